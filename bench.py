@@ -1,0 +1,376 @@
+#!/usr/bin/env python3
+"""Benchmark of the GP-MPPI rollout (one "step" = one mppi_step: every
+sample's rollout, costs, weights and the control update) on the K=4096, T=50,
+N=500, 16-obstacle figure-eight workload.
+
+Prints ONE JSON line (rank 0).  Metric: rollout sample-steps/s (K*T per
+mppi_step) with the p50 mppi_step latency alongside.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (launched by torchrun) every rank runs an independent replica of
+the controller with its own seed (the method has no exchange step between
+controllers); value = all ranks' sample-steps / the slowest rank's time.
+--impl reference times the FP64 oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "rollout sample-steps/s and p50 mppi_step latency vs plain FP32 GPU path"
+WORKLOAD = "cfg2"
+L2_FLUSH_BYTES = 512 << 20
+ROLLOUT_SRC = os.path.join(ROOT, "paper_2411_03289_gb300", "csrc", "rollout_fp32.cu")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "rollout_fp32_cfg2_ncu.md")
+
+
+def rollout_flops_per_sample_step(N, O, S):
+    """Algorithmic FP32 flops of one sample-step (exps counted separately):
+    triangular quadratic form N(N+1) (N(N+1)/2 multiply-adds), 16N for the
+    kernel row (4 differences, 4 squares-and-adds), the two means and the
+    sum of squares, 15 per obstacle, 10 per lane segment, 150 for the
+    dynamics, covariance and stage cost."""
+    return N * (N + 1) + 16 * N + 15 * O + 10 * S + 150
+
+
+def fp32_peak_tflops(sm_mhz=2070.0, n_sm=152):
+    """FP32 FMA pipe: 128 lanes per SM, 2 flops per FMA."""
+    return n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def describe(sc):
+    P = sc.params
+    return {"workload": f"{sc.name}: K={P.K} T={P.T} N={sc.N} obstacles={sc.obstacles.shape[0]} "
+                        f"path={sc.meta.get('path')} ({sc.path.shape[0]} vertices), FP32",
+            "K": P.K, "T": P.T, "N": sc.N, "obstacles": int(sc.obstacles.shape[0]),
+            "path_vertices": int(sc.path.shape[0]), "precision": "fp32",
+            "variance_mode": "per_sample",
+            "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)"}
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing
+# ---------------------------------------------------------------------------
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            import tempfile
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# measured DRAM traffic of the rollout kernel (from the committed ncu summary)
+# ---------------------------------------------------------------------------
+
+def committed_traffic():
+    """Bytes per launch from the ncu summary, if it was taken on the current
+    kernel source (the summary records the source's sha256)."""
+    try:
+        txt = open(TRAFFIC_FILE).read()
+        sha = hashlib.sha256(open(ROLLOUT_SRC, "rb").read()).hexdigest()
+    except OSError:
+        return None
+    m_sha = re.search(r"rollout_fp32\.cu sha256:\s*([0-9a-f]{64})", txt)
+    m_tr = re.search(r"dram bytes per launch \(full workload\):\s*([0-9.eE+]+)", txt)
+    if not m_sha or not m_tr or m_sha.group(1) != sha:
+        return None
+    return float(m_tr.group(1))
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle as it stands, in a spawned process
+# ---------------------------------------------------------------------------
+
+CPU_SAMPLE_ROWS = 256
+
+
+def _cpu_child(rows, reps):
+    import numpy as np  # noqa: F401
+    import oracle as O
+    import scenarios as S
+    sc = S.scenario(WORKLOAD)
+    fits = O.gp_fit(sc.X, sc.Y, sc.hyper)
+    samples = list(range(rows))
+    t0 = time.perf_counter()
+    for r in range(reps):
+        O.rollout(sc, fits, sc.x0, sc.U0, r, samples=samples)
+    dt = time.perf_counter() - t0
+    print(json.dumps({"seconds": dt, "sample_steps": rows * sc.params.T * reps}))
+
+
+def cpu_baseline(rows=CPU_SAMPLE_ROWS, reps=4):
+    cores = os.cpu_count() or 1
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = str(cores)
+    env.pop("CUDA_VISIBLE_DEVICES", None)
+    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-child", str(rows), str(reps)]
+    out = subprocess.run(cmd, capture_output=True, text=True, env=env, cwd=ROOT, timeout=900)
+    line = [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
+    if out.returncode != 0 or not line:
+        return {"value": None, "unit": "sample-steps/s", "cores": cores, "kind": "oracle",
+                "sample": f"failed: {out.stderr.strip()[-200:]}"}
+    d = json.loads(line[-1])
+    return {"value": d["sample_steps"] / d["seconds"], "unit": "sample-steps/s", "cores": cores,
+            "kind": "oracle",
+            "sample": f"FP64 numpy oracle, {rows} of the K samples x T={50} steps x {reps} iterations "
+                      f"({d['seconds']:.1f} s), BLAS threads = {cores}"}
+
+
+# ---------------------------------------------------------------------------
+# the reference arm: the oracle, timed as it stands
+# ---------------------------------------------------------------------------
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle as O
+    import scenarios as S
+    sc = S.scenario(WORKLOAD)
+    fits = O.gp_fit(sc.X, sc.Y, sc.hyper)
+    rows = list(range(args.ref_rows))
+    for w in range(args.warmup):
+        O.rollout(sc, fits, sc.x0, sc.U0, w, samples=rows)
+    times = []
+    for s in range(args.steps):
+        t0 = time.perf_counter()
+        ro = O.rollout(sc, fits, sc.x0, sc.U0, args.warmup + s, samples=rows)
+        O.mppi_update(sc.U0, ro["u_tilde"], O.mppi_weights(ro["costs"], sc.params.lam))
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    value = args.ref_rows * sc.params.T * args.steps / tot
+    cores = os.cpu_count() or 1
+    cfg = describe(sc)
+    line = {"metric": METRIC, "value": value, "unit": "sample-steps/s", "impl": "reference",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * tot / args.steps, "p50_ms": 1e3 * statistics.median(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": cfg,
+            "cpu_baseline": {"value": value, "unit": "sample-steps/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{args.ref_rows} of K={sc.params.K} samples per step, full T and N"},
+            "e2e": {"value": value, "unit": "sample-steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_2411_03289_gb300 as gp
+    import scenarios as S
+    from paper_2411_03289_gb300 import build as B
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    B.build()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    sc = S.scenario(WORKLOAD, seed=1 + rank)
+    P = sc.params
+    g = gp.gp_fit(sc.X, sc.Y, sc.hyper)
+    ctrl = gp.mppi_create(P, sc.obstacles, sc.path, g)
+    U = torch.tensor(sc.U0, dtype=torch.float32, device=dev)
+    U_new = torch.empty_like(U)
+    w = torch.empty(P.K, dtype=torch.float32, device=dev)
+    c = torch.empty_like(w)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    x0 = sc.x0.astype(np.float32)
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+
+    gp.mppi_set_profiling(ctrl, True)
+    for _ in range(args.warmup):
+        gp.mppi_step(ctrl, x0, U, U_new, w, c)
+        flush.fill_(1.0)
+    torch.cuda.synchronize()
+
+    # ---- device-timed region: inputs resident, L2 flushed between steps ----
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    rollout_ms, update_ms = [], []
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter()
+    for i in range(args.steps):
+        starts[i].record(stream)
+        gp.mppi_step(ctrl, x0, U, U_new, w, c)
+        ends[i].record(stream)
+        r_ms, u_ms = gp.mppi_last_profile(ctrl)
+        rollout_ms.append(r_ms)
+        update_ms.append(u_ms)
+        flush.fill_(float(i))
+    torch.cuda.synchronize()
+    barrier()
+    t_wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    tot_ms = sum(step_ms)
+    if ws > 1:
+        t = torch.tensor([tot_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    gp.mppi_set_profiling(ctrl, False)
+
+    # ---- end to end through the ABI with host buffers -----------------------
+    U_host = torch.tensor(sc.U0, dtype=torch.float32).pin_memory()
+    out_host = torch.empty_like(U_host).pin_memory()
+    for _ in range(3):
+        U.copy_(U_host, non_blocking=True)
+        gp.mppi_step(ctrl, x0, U, U_new, w, c)
+        out_host.copy_(U_new, non_blocking=True)
+        torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        U.copy_(U_host, non_blocking=True)
+        gp.mppi_step(ctrl, x0, U, U_new, w, c)
+        out_host.copy_(U_new, non_blocking=True)
+        torch.cuda.synchronize()             # the controller needs U_new[0] on the host
+    e2e_s = time.perf_counter() - t0
+    if ws > 1:
+        t = torch.tensor([e2e_s], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    h2d = U_host.numel() * 4 + 5 * 4
+    d2h = out_host.numel() * 4
+
+    units = P.K * P.T * args.steps * ws
+    value = units / (tot_ms / 1e3)
+    S_seg = max(sc.path.shape[0] - 1, 1)
+    flops = rollout_flops_per_sample_step(sc.N, sc.obstacles.shape[0], S_seg) * P.K * P.T
+    r_avg = sum(rollout_ms) / len(rollout_ms)
+    sm_max = (clk or {}).get("sm_max_mhz") or 2070.0
+    peak = fp32_peak_tflops(2070.0)
+    achieved = flops / (r_avg / 1e3) / 1e12
+    traffic = committed_traffic()
+    if rank != 0:
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": "sample-steps/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_ms / args.steps,
+        "p50_ms": statistics.median(step_ms), "p90_ms": sorted(step_ms)[int(0.9 * (len(step_ms) - 1))],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded GP training set, obstacles and figure-eight path)",
+        "config": describe(sc),
+        "gpu_launches": 2 * args.steps,
+        "kernel_ms": {"rollout_avg": r_avg, "update_avg": sum(update_ms) / len(update_ms)},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "k_rollout_fp32",
+                     "peak_note": "FP32 FMA pipe 152 SM x 128 lanes x 2 flops x 2070 MHz (derived)"},
+        "cpu_baseline": cpu_baseline() if (rank == 0 and ws == 1 and not args.no_cpu) else None,
+        "e2e": {"value": units / e2e_s, "unit": "sample-steps/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "clocks": clk,
+        "wall_s_timed_region": t_wall,
+    }
+    del sm_max
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    if len(sys.argv) >= 2 and sys.argv[1] == "--cpu-child":
+        _cpu_child(int(sys.argv[2]), int(sys.argv[3]))
+        return
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--ref-rows", type=int, default=128,
+                    help="samples per reference (oracle) step")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline leg")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

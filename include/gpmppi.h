@@ -1,0 +1,205 @@
+/*
+ * gpmppi.h -- C ABI of the GB300 chance-constrained GP-MPPI rollout library.
+ *
+ * The library implements the data-parallel hot path of the chance-constrained
+ * GP-MPPI controller of Trivedi et al. (Sec. IV, Alg. 1): K sampled control
+ * sequences are propagated over a horizon of T steps through the dynamic
+ * unicycle plus a GP residual mean (Eq. 1-3, Eq. 6, Eq. 10), the GP variance is
+ * propagated into the state covariance (Eq. 10), every trajectory is scored
+ * against lane and obstacle chance constraints tightened by that covariance
+ * (Eq. 11-16), and the nominal control is updated by a log-sum-exp stabilised
+ * softmax-weighted sum of the sampled controls (Alg. 1, Step 1).
+ *
+ * Conventions shared by every entry point
+ *  - Every function returns an int status: GPMPPI_OK (0) or a negative error
+ *    code; gpmppi_last_error() returns a thread-local message for the last
+ *    failure on the calling thread.  No C++ exception crosses the ABI.
+ *  - The caller owns every array argument.  Arrays documented as "device" must
+ *    be CUDA device (or managed) memory of the current device; the library
+ *    checks the pointer kind and returns GPMPPI_ERR_INVALID_ARG for host
+ *    pointers, but it cannot check a device array's length: the caller must
+ *    provide at least the documented number of elements.
+ *  - Arrays documented as "host" are read or written synchronously before the
+ *    function returns (gp_fit, mppi_create, gp_factors, state vectors).
+ *  - "stream" is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Device work is enqueued on it and the call returns without
+ *    synchronising, except where noted.
+ *  - A failed call leaves its outputs unspecified and the handles usable.
+ *  - Row-major layouts throughout; float is IEEE binary32, double binary64.
+ */
+#ifndef GPMPPI_H
+#define GPMPPI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define GPMPPI_OK 0
+#define GPMPPI_ERR_INVALID_ARG (-1)   /* bad shape, value, pointer kind or handle */
+#define GPMPPI_ERR_NOT_PD (-2)        /* K_XX + noise I not positive definite     */
+#define GPMPPI_ERR_CUDA (-3)          /* a CUDA runtime call failed               */
+#define GPMPPI_ERR_OOM (-4)           /* device allocation failed                 */
+#define GPMPPI_ERR_TIMEOUT (-5)       /* a bounded device wait gave up            */
+#define GPMPPI_ERR_NONFINITE (-6)     /* NaN or Inf in an input                   */
+#define GPMPPI_ERR_UNSUPPORTED (-7)   /* valid request this build does not serve  */
+
+/* variance modes (where the tightening covariance comes from) */
+#define GPMPPI_VAR_PER_SAMPLE 0   /* each sample's own propagated Sigma (Eq. 10)     */
+#define GPMPPI_VAR_NOMINAL 1      /* Alg. 1 Step 2: Sigma along the previous update */
+
+/* arithmetic of the GP variance contraction */
+#define GPMPPI_FP32 0
+#define GPMPPI_BF16_SPLIT 1
+
+/* limits of this build */
+#define GPMPPI_MAX_N 4096         /* GP training points      */
+#define GPMPPI_MAX_T 1024         /* horizon                 */
+#define GPMPPI_MAX_K (1 << 24)    /* samples                 */
+#define GPMPPI_MAX_OBSTACLES 4096
+#define GPMPPI_MAX_PATH 65536     /* polyline vertices       */
+
+typedef struct gpmppi_gp_s* gpmppi_gp;       /* opaque, owned by the library */
+typedef struct gpmppi_ctrl_s* gpmppi_ctrl;   /* opaque, owned by the library */
+
+/* SE-ARD hyper-parameters of one GP output (Sec. III-A; Sec. V-A trains
+ * them with GPyTorch, here they are supplied):
+ * k(a,b) = signal_var * exp(-1/2 sum_d (a_d - b_d)^2 / lengthscale_d^2),
+ * observation noise variance noise_var. */
+typedef struct gpmppi_hyper {
+    double lengthscale[4];
+    double signal_var;
+    double noise_var;
+} gpmppi_hyper;
+
+/* Controller parameters (Alg. 1 inputs; Eq. 5-9, Eq. 11-16). */
+typedef struct gpmppi_params {
+    int32_t K;               /* samples per iteration (S in Alg. 1), >= 1           */
+    int32_t T;               /* horizon (N in Eq. 5), >= 1                          */
+    float dt;                /* Euler step [s]                                      */
+    float tau_v, tau_w;      /* first-order lag time constants of f_v, f_omega      */
+    float sigma[2];          /* std of the control noise Sigma_sim (v, omega), >= 0 */
+    float lambda;            /* MPPI temperature, > 0                               */
+    float p_x;               /* chance level of Eq. 7, in (0, 1)                    */
+    float u_min[2], u_max[2];/* control box of Eq. 8                                */
+    float alpha[5];          /* Eq. 11 weights; alpha[2] (slip) must be 0           */
+    float beta[4];           /* Eq. 12 weights; beta[2], beta[3] (goal) must be 0   */
+    float P_lane, P_coll;    /* penalties multiplying the two indicators            */
+    float lane_half_width;   /* r of Eq. 13, > 0                                    */
+    float v_desired;         /* v_desired of Eq. 11                                 */
+    uint64_t seed;           /* Philox key                                          */
+    int32_t variance_mode;   /* GPMPPI_VAR_*                                        */
+    int32_t precision;       /* GPMPPI_FP32 or GPMPPI_BF16_SPLIT                    */
+} gpmppi_params;
+
+/* Fit the two residual GPs of Sec. III-A (outputs delta_v and delta_omega)
+ * on the current CUDA device, in FP64: K_j = k_j(X,X) + noise_var_j I,
+ * L_j = chol(K_j), alpha_j = K_j^-1 Y[:,j], and L_j^-1; the rollout uses
+ * FP32 copies of alpha_j and L_j^-1 (and BF16 hi/lo parts when requested).
+ *   X     host, N x 4 doubles (v, omega, v_cmd, omega_cmd) per row
+ *   Y     host, N x 2 doubles (delta_v, delta_omega)
+ *   N     0 <= N <= GPMPPI_MAX_N (N = 0 gives the prior: mean 0, var signal_var)
+ *   hyper host, two entries (output 0 = delta_v, output 1 = delta_omega)
+ *   out   receives the new handle (owned by the library; free with gp_destroy)
+ * Blocking: returns after the factorisation finished.
+ * Errors: INVALID_ARG, NONFINITE, NOT_PD (Cholesky pivot <= 0), OOM, CUDA. */
+int gp_fit(const double* X, const double* Y, int32_t N, const gpmppi_hyper hyper[2],
+           gpmppi_gp* out);
+
+/* Release a GP handle.  A controller created from it must be destroyed first. */
+int gp_destroy(gpmppi_gp gp);
+
+/* Copy the FP64 factors of output j (0 or 1) to the host:
+ *   Linv  host, N x N doubles, lower triangular L_j^-1 (upper part zero); may be NULL
+ *   alpha host, N doubles, K_j^-1 Y[:,j]; may be NULL
+ * Blocking. */
+int gp_factors(gpmppi_gp gp, int32_t j, double* Linv, double* alpha);
+
+/* GP posterior of the latent residual at M query points (Eq. 3 with one
+ * terrain): mean_j = k_j(z,X) alpha_j, var_j = max(0, sf2_j - |L_j^-1 k_j(X,z)|^2).
+ *   Z     device, M x 4 floats
+ *   mean  device, M x 2 floats (output)
+ *   var   device, M x 2 floats (output)
+ * FP32 arithmetic on the FP32 factors. */
+int gp_predict(gpmppi_gp gp, const float* Z, int32_t M, float* mean, float* var, void* stream);
+
+/* Create a controller for one robot.
+ *   p          host, parameters (validated; copied)
+ *   obstacles  host, O x 3 floats (centre x, centre y, radius > 0); NULL if O = 0
+ *   path       host, P x 2 floats, lane-centre polyline (P >= 1); copied
+ *   gp         fitted GP on the current device; must outlive the controller.
+ *              Both outputs must share their hyper-parameters (the rollout
+ *              evaluates one kernel row and one variance per query).
+ * Allocates the controller's device buffers on the current device.
+ * Errors: INVALID_ARG, NONFINITE, UNSUPPORTED, OOM, CUDA. */
+int mppi_create(const gpmppi_params* p, const float* obstacles, int32_t O, const float* path,
+                int32_t P, gpmppi_gp gp, gpmppi_ctrl* out);
+
+/* One MPPI iteration (Alg. 1 Step 1, plus Step 2 in GPMPPI_VAR_NOMINAL mode):
+ * sample K perturbed control sequences with Philox4x32-10 (key = seed,
+ * counter = (k, s, it_lo, it_hi)), roll each out for T steps with the GP
+ * mean and variance, score it, and return the softmax-weighted update.
+ *   state    host, 5 floats (X, Y, theta, v, omega): mu_x(0); Sigma_x(0) = 0
+ *   U_nom    device, T x 2 floats: nominal controls u(0..T-1)
+ *   U_new    device, T x 2 floats (output): U + sum_s w_s (u~_s - U)
+ *   weights  device, K floats (output) or NULL
+ *   costs    device, K floats (output) or NULL
+ * The iteration counter advances by one per successful call.  Calls on one
+ * controller must not overlap on the GPU (they share its scratch buffers). */
+int mppi_step(gpmppi_ctrl c, const float state[5], const float* U_nom, float* U_new,
+              float* weights, float* costs, void* stream);
+
+/* The rollout of mppi_step for the current iteration, recording every
+ * sample's trajectory (does not update U and does not advance the counter):
+ *   mu      device, K x T x 5 floats: state after step k (mu(k+1)), or NULL
+ *   sigma   device, K x T x 15 floats: upper triangle of Sigma(k+1), row by row
+ *           (00,01,02,03,04,11,12,13,14,22,23,24,33,34,44), or NULL
+ *   stage   device, K x T floats: stage cost of step k, or NULL
+ *   margins device, K x T x 2 floats: (e - r_bar, min_j d_bar_j); the lane
+ *           indicator fires when the first is > 0, the collision indicator
+ *           when the second is <= 0 (+inf without obstacles), or NULL
+ *   costs   device, K floats: summed costs, or NULL */
+int mppi_rollout_trace(gpmppi_ctrl c, const float state[5], const float* U_nom, float* mu,
+                       float* sigma, float* stage, float* margins, float* costs, void* stream);
+
+/* Set / read the MPPI iteration counter (Philox counter words 2 and 3). */
+int mppi_set_iteration(gpmppi_ctrl c, uint64_t it);
+int mppi_get_iteration(gpmppi_ctrl c, uint64_t* it);
+
+/* GPMPPI_VAR_NOMINAL: the tightening covariance carried to the next call
+ * (Alg. 1 Step 2), T x 3 floats (Sxx, Sxy, Syy) of Sigma_XY(k+1), device. */
+int mppi_nominal_sxy(gpmppi_ctrl c, float* sxy, void* stream);
+
+/* Per-kernel timing of mppi_step.  When enabled, mppi_step records CUDA
+ * events on its stream around the rollout kernel and around the update
+ * kernel(s); mppi_last_profile waits for the last step's events and returns
+ * the two durations in milliseconds (host floats).  Off by default. */
+int mppi_set_profiling(gpmppi_ctrl c, int32_t on);
+int mppi_last_profile(gpmppi_ctrl c, float* rollout_ms, float* update_ms);
+
+/* Release a controller and its device buffers (synchronises its device). */
+int mppi_destroy(gpmppi_ctrl c);
+
+/* Raw Philox4x32-10 blocks as the kernels draw them (Salmon et al., SC'11):
+ *   ctr  device, M x 4 uint32 counters; out device, M x 4 uint32 words. */
+int gpmppi_philox(uint64_t seed, const uint32_t* ctr, int32_t M, uint32_t* out, void* stream);
+
+/* The control perturbations eps (K x T x 2 floats, device) of one iteration,
+ * as the rollout draws them before clamping (Alg. 1 "Sample eps^s"). */
+int gpmppi_control_noise(uint64_t seed, int32_t K, int32_t T, uint64_t it, const float sigma[2],
+                         float* eps, void* stream);
+
+/* Thread-local message describing the last failed call ("" if none). */
+const char* gpmppi_last_error(void);
+
+/* Library version (major * 10000 + minor * 100 + patch). */
+int gpmppi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GPMPPI_H */

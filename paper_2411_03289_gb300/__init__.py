@@ -1,0 +1,308 @@
+"""Python binding of libgpmppi, the GB300 chance-constrained GP-MPPI rollout.
+
+Argument marshalling only: every step of the rollout, the GP fit and the
+MPPI update runs in the CUDA kernels behind the C ABI of include/gpmppi.h.
+The functions carry the C names; device arrays are torch CUDA tensors (their
+data pointers are passed through), host arrays are numpy arrays, and
+``stream`` defaults to torch's current CUDA stream.  There is no CPU path: if
+the shared library has not been built, ``load()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+LIB_PATH = _build.LIB_PATH
+
+GPMPPI_OK = 0
+GPMPPI_ERR_INVALID_ARG = -1
+GPMPPI_ERR_NOT_PD = -2
+GPMPPI_ERR_CUDA = -3
+GPMPPI_ERR_OOM = -4
+GPMPPI_ERR_TIMEOUT = -5
+GPMPPI_ERR_NONFINITE = -6
+GPMPPI_ERR_UNSUPPORTED = -7
+GPMPPI_VAR_PER_SAMPLE = 0
+GPMPPI_VAR_NOMINAL = 1
+GPMPPI_FP32 = 0
+GPMPPI_BF16_SPLIT = 1
+
+# names every build of the library exports (checked by the CPU test suite)
+EXPORTS = ("gp_fit", "gp_destroy", "gp_factors", "gp_predict", "mppi_create", "mppi_step",
+           "mppi_rollout_trace", "mppi_set_iteration", "mppi_get_iteration", "mppi_nominal_sxy",
+           "mppi_destroy", "mppi_set_profiling", "mppi_last_profile", "gpmppi_philox", "gpmppi_control_noise", "gpmppi_last_error",
+           "gpmppi_version")
+
+
+class GpmppiError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+class Hyper(ctypes.Structure):
+    _fields_ = [("lengthscale", ctypes.c_double * 4), ("signal_var", ctypes.c_double),
+                ("noise_var", ctypes.c_double)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("K", ctypes.c_int32), ("T", ctypes.c_int32), ("dt", ctypes.c_float),
+                ("tau_v", ctypes.c_float), ("tau_w", ctypes.c_float),
+                ("sigma", ctypes.c_float * 2), ("lambda_", ctypes.c_float),
+                ("p_x", ctypes.c_float), ("u_min", ctypes.c_float * 2),
+                ("u_max", ctypes.c_float * 2), ("alpha", ctypes.c_float * 5),
+                ("beta", ctypes.c_float * 4), ("P_lane", ctypes.c_float),
+                ("P_coll", ctypes.c_float), ("lane_half_width", ctypes.c_float),
+                ("v_desired", ctypes.c_float), ("seed", ctypes.c_uint64),
+                ("variance_mode", ctypes.c_int32), ("precision", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def load():
+    """Load the shared library (it must have been built with build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libgpmppi is not built ({LIB_PATH} missing): "
+                           "run `python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i32, u64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint64
+    sig = {
+        "gp_fit": [vp, vp, i32, vp, ctypes.POINTER(vp)],
+        "gp_destroy": [vp],
+        "gp_factors": [vp, i32, vp, vp],
+        "gp_predict": [vp, vp, i32, vp, vp, vp],
+        "mppi_create": [vp, vp, i32, vp, i32, vp, ctypes.POINTER(vp)],
+        "mppi_step": [vp, vp, vp, vp, vp, vp, vp],
+        "mppi_rollout_trace": [vp, vp, vp, vp, vp, vp, vp, vp, vp],
+        "mppi_set_iteration": [vp, u64],
+        "mppi_get_iteration": [vp, ctypes.POINTER(u64)],
+        "mppi_nominal_sxy": [vp, vp, vp],
+        "mppi_destroy": [vp],
+        "mppi_set_profiling": [vp, i32],
+        "mppi_last_profile": [vp, vp, vp],
+        "gpmppi_philox": [u64, vp, i32, vp, vp],
+        "gpmppi_control_noise": [u64, i32, i32, u64, vp, vp, vp],
+        "gpmppi_version": [],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    lib.gpmppi_last_error.argtypes = []
+    lib.gpmppi_last_error.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def gpmppi_last_error() -> str:
+    return load().gpmppi_last_error().decode()
+
+
+def gpmppi_version() -> int:
+    return load().gpmppi_version()
+
+
+def _check(rc):
+    if rc != GPMPPI_OK:
+        raise GpmppiError(rc, gpmppi_last_error())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dptr(t, dtype=None, numel=None, name="array"):
+    """Data pointer of a contiguous CUDA tensor (None -> NULL)."""
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name} must have dtype {dtype}")
+    if numel is not None and t.numel() < numel:
+        raise ValueError(f"{name} needs at least {numel} elements")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _f32(x):
+    return np.ascontiguousarray(np.asarray(x, dtype=np.float32))
+
+
+def make_hyper(h) -> Hyper:
+    out = Hyper()
+    out.lengthscale[:] = [float(v) for v in h.lengthscale]
+    out.signal_var = float(h.signal_var)
+    out.noise_var = float(h.noise_var)
+    return out
+
+
+def make_params(p) -> Params:
+    """Params from any object with the field names of gpmppi_params (``lam`` or
+    ``lambda_`` for the temperature)."""
+    out = Params()
+    out.K, out.T = int(p.K), int(p.T)
+    out.dt, out.tau_v, out.tau_w = float(p.dt), float(p.tau_v), float(p.tau_w)
+    out.sigma[:] = [float(v) for v in p.sigma]
+    out.lambda_ = float(getattr(p, "lam", getattr(p, "lambda_", 1.0)))
+    out.p_x = float(p.p_x)
+    out.u_min[:] = [float(v) for v in p.u_min]
+    out.u_max[:] = [float(v) for v in p.u_max]
+    out.alpha[:] = [float(v) for v in p.alpha]
+    out.beta[:] = [float(v) for v in p.beta]
+    out.P_lane, out.P_coll = float(p.P_lane), float(p.P_coll)
+    out.lane_half_width, out.v_desired = float(p.lane_half_width), float(p.v_desired)
+    out.seed = int(p.seed) & 0xFFFFFFFFFFFFFFFF
+    out.variance_mode = int(p.variance_mode)
+    out.precision = int(p.precision)
+    return out
+
+
+class GP:
+    """Owning wrapper of a gpmppi_gp handle."""
+
+    def __init__(self, handle, N):
+        self.handle, self.N = handle, N
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.gp_destroy(self.handle)
+            self.handle = None
+
+
+class Ctrl:
+    """Owning wrapper of a gpmppi_ctrl handle (keeps its GP alive)."""
+
+    def __init__(self, handle, gp, K, T):
+        self.handle, self.gp, self.K, self.T = handle, gp, K, T
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.mppi_destroy(self.handle)
+            self.handle = None
+
+
+def gp_fit(X, Y, hyper) -> GP:
+    lib = load()
+    X = np.ascontiguousarray(np.asarray(X, dtype=np.float64).reshape(-1, 4))
+    Y = np.ascontiguousarray(np.asarray(Y, dtype=np.float64).reshape(-1, 2))
+    if X.shape[0] != Y.shape[0]:
+        raise ValueError("X and Y row counts differ")
+    hy = (Hyper * 2)(make_hyper(hyper[0]), make_hyper(hyper[1]))
+    h = ctypes.c_void_p()
+    _check(lib.gp_fit(X.ctypes.data_as(ctypes.c_void_p), Y.ctypes.data_as(ctypes.c_void_p),
+                      X.shape[0], ctypes.cast(hy, ctypes.c_void_p), ctypes.byref(h)))
+    return GP(h.value, X.shape[0])
+
+
+def gp_destroy(gp: GP):
+    if gp.handle:
+        _check(load().gp_destroy(gp.handle))
+        gp.handle = None
+
+
+def gp_factors(gp: GP, j: int):
+    """(Linv (N,N), alpha (N,)) in float64 copied from the device."""
+    N = gp.N
+    Linv = np.zeros((N, N))
+    alpha = np.zeros(N)
+    _check(load().gp_factors(gp.handle, j, Linv.ctypes.data_as(ctypes.c_void_p),
+                             alpha.ctypes.data_as(ctypes.c_void_p)))
+    return Linv, alpha
+
+
+def gp_predict(gp: GP, Z, mean, var, stream=None):
+    M = Z.shape[0]
+    _check(load().gp_predict(gp.handle, _dptr(Z, numel=4 * M, name="Z"), M,
+                             _dptr(mean, numel=2 * M, name="mean"),
+                             _dptr(var, numel=2 * M, name="var"), _stream(stream)))
+
+
+def mppi_create(params, obstacles, path, gp: GP) -> Ctrl:
+    lib = load()
+    p = make_params(params)
+    obst = _f32(obstacles).reshape(-1, 3)
+    pth = _f32(path).reshape(-1, 2)
+    h = ctypes.c_void_p()
+    _check(lib.mppi_create(ctypes.byref(p), obst.ctypes.data_as(ctypes.c_void_p) if obst.size else None,
+                           obst.shape[0], pth.ctypes.data_as(ctypes.c_void_p), pth.shape[0],
+                           gp.handle, ctypes.byref(h)))
+    return Ctrl(h.value, gp, p.K, p.T)
+
+
+def mppi_step(ctrl: Ctrl, state, U_nom, U_new, weights=None, costs=None, stream=None):
+    st = _f32(state).reshape(5)
+    _check(load().mppi_step(ctrl.handle, st.ctypes.data_as(ctypes.c_void_p),
+                            _dptr(U_nom, numel=2 * ctrl.T, name="U_nom"),
+                            _dptr(U_new, numel=2 * ctrl.T, name="U_new"),
+                            _dptr(weights, numel=ctrl.K, name="weights"),
+                            _dptr(costs, numel=ctrl.K, name="costs"), _stream(stream)))
+
+
+def mppi_rollout_trace(ctrl: Ctrl, state, U_nom, mu=None, sigma=None, stage=None, margins=None,
+                       costs=None, stream=None):
+    st = _f32(state).reshape(5)
+    KT = ctrl.K * ctrl.T
+    _check(load().mppi_rollout_trace(ctrl.handle, st.ctypes.data_as(ctypes.c_void_p),
+                                     _dptr(U_nom, numel=2 * ctrl.T, name="U_nom"),
+                                     _dptr(mu, numel=5 * KT, name="mu"),
+                                     _dptr(sigma, numel=15 * KT, name="sigma"),
+                                     _dptr(stage, numel=KT, name="stage"),
+                                     _dptr(margins, numel=2 * KT, name="margins"),
+                                     _dptr(costs, numel=ctrl.K, name="costs"), _stream(stream)))
+
+
+def mppi_set_iteration(ctrl: Ctrl, it: int):
+    _check(load().mppi_set_iteration(ctrl.handle, int(it)))
+
+
+def mppi_get_iteration(ctrl: Ctrl) -> int:
+    v = ctypes.c_uint64()
+    _check(load().mppi_get_iteration(ctrl.handle, ctypes.byref(v)))
+    return v.value
+
+
+def mppi_nominal_sxy(ctrl: Ctrl, out, stream=None):
+    _check(load().mppi_nominal_sxy(ctrl.handle, _dptr(out, numel=3 * ctrl.T, name="sxy"),
+                                   _stream(stream)))
+
+
+def mppi_set_profiling(ctrl: Ctrl, on: bool):
+    _check(load().mppi_set_profiling(ctrl.handle, 1 if on else 0))
+
+
+def mppi_last_profile(ctrl: Ctrl):
+    """(rollout_ms, update_ms) of the last profiled mppi_step (waits for it)."""
+    a, b = ctypes.c_float(), ctypes.c_float()
+    _check(load().mppi_last_profile(ctrl.handle, ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
+def mppi_destroy(ctrl: Ctrl):
+    if ctrl.handle:
+        _check(load().mppi_destroy(ctrl.handle))
+        ctrl.handle = None
+
+
+def gpmppi_philox(seed: int, ctr, out, stream=None):
+    M = ctr.numel() // 4
+    _check(load().gpmppi_philox(int(seed) & 0xFFFFFFFFFFFFFFFF, _dptr(ctr, name="ctr"), M,
+                                _dptr(out, numel=4 * M, name="out"), _stream(stream)))
+
+
+def gpmppi_control_noise(seed: int, K: int, T: int, it: int, sigma, eps, stream=None):
+    sg = (ctypes.c_float * 2)(float(sigma[0]), float(sigma[1]))
+    _check(load().gpmppi_control_noise(int(seed) & 0xFFFFFFFFFFFFFFFF, K, T, int(it), sg,
+                                       _dptr(eps, numel=2 * K * T, name="eps"), _stream(stream)))

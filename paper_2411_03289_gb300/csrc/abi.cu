@@ -1,0 +1,577 @@
+// Host implementation of the C ABI declared in include/gpmppi.h.
+//
+// Every entry point validates its arguments (shapes, finiteness, pointer
+// kinds, handle tags) before touching the GPU, so that bad input becomes an
+// error code instead of a device fault, and converts every CUDA error into a
+// status code with a thread-local message.
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+namespace gpm {
+
+static thread_local std::string g_err;
+
+void set_error(const std::string& msg) { g_err = msg; }
+
+int fail(int code, const std::string& msg) {
+    g_err = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+    g_err = std::string(what) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? GPMPPI_ERR_OOM : GPMPPI_ERR_CUDA;
+}
+
+}  // namespace gpm
+
+using namespace gpm;
+
+namespace {
+
+constexpr uint32_t kGpMagic = 0x47504d31u;     // "GPM1"
+constexpr uint32_t kCtrlMagic = 0x4d505031u;   // "MPP1"
+
+bool is_finite(double v) { return std::isfinite(v); }
+
+// Quantile of a chi-squared variable with 2 degrees of freedom (Eq. 14):
+// that distribution is exponential with mean 2, so chi2_2(p) = -2 ln(1 - p).
+double chi2_2_quantile(double p) { return -2.0 * std::log1p(-p); }
+
+// Standard normal quantile (Eq. 16) by bisection on the upper tail
+// erfc(x / sqrt 2) / 2 = 1 - p (p > 1/2) or on Phi(x) = p.
+double normal_quantile(double p) {
+    double lo = -40.0, hi = 40.0;
+    const double q = 1.0 - p;
+    for (int i = 0; i < 400; ++i) {
+        const double mid = 0.5 * (lo + hi);
+        if (mid == lo || mid == hi) break;
+        const bool below = (p > 0.5) ? (0.5 * std::erfc(mid / std::sqrt(2.0)) > q)
+                                     : (0.5 * std::erfc(-mid / std::sqrt(2.0)) < p);
+        if (below) lo = mid; else hi = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
+// Device (or managed) memory of the current device?
+int check_dev_ptr(const void* p, const char* name, bool nullable) {
+    if (p == nullptr) {
+        if (nullable) return GPMPPI_OK;
+        return fail(GPMPPI_ERR_INVALID_ARG, std::string(name) + " must not be NULL");
+    }
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(GPMPPI_ERR_INVALID_ARG, std::string(name) + " is not a CUDA pointer");
+    }
+    if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)
+        return fail(GPMPPI_ERR_INVALID_ARG, std::string(name) + " must be device memory");
+    int dev = 0;
+    GPM_CUDA(cudaGetDevice(&dev));
+    if (at.type == cudaMemoryTypeDevice && at.device != dev)
+        return fail(GPMPPI_ERR_INVALID_ARG, std::string(name) + " lives on another device");
+    return GPMPPI_OK;
+}
+
+}  // namespace
+
+struct gpmppi_gp_s {
+    uint32_t magic = kGpMagic;
+    GpDevice g;
+};
+
+struct gpmppi_ctrl_s {
+    uint32_t magic = kCtrlMagic;
+    gpmppi_params p{};
+    gpmppi_gp gp = nullptr;
+    int device = 0;
+    int O = 0, P = 0, S = 0;
+    int mt = 1, n_upd = 1;
+    uint64_t it = 0;
+    double sq_chi2 = 0.0, phi_inv = 0.0;
+    float* obst = nullptr;
+    float4* seg = nullptr;
+    float* seg_il2 = nullptr;
+    float* costs = nullptr;       // K, used when the caller passes no costs array
+    float2* u_tilde = nullptr;    // T x K
+    float* partial = nullptr;     // n_upd x T x 2
+    unsigned int* counter = nullptr;
+    float* nom_sxy = nullptr;     // T x 3
+    bool profiling = false;
+    bool profiled = false;
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+};
+
+namespace {
+
+void free_gp(gpmppi_gp h) {
+    if (!h) return;
+    GpDevice& g = h->g;
+    cudaFree(g.alpha);
+    cudaFree(g.Xs[0]);
+    cudaFree(g.W[0]);
+    cudaFree(g.Linv64[0]);
+    cudaFree(g.alpha64[0]);
+    cudaFree(g.alpha64[1]);
+    if (!g.shared) {
+        cudaFree(g.Xs[1]);
+        cudaFree(g.W[1]);
+        cudaFree(g.Linv64[1]);
+    }
+    h->magic = 0;
+    delete h;
+}
+
+void free_ctrl(gpmppi_ctrl c) {
+    if (!c) return;
+    cudaFree(c->obst);
+    cudaFree(c->seg);
+    cudaFree(c->seg_il2);
+    cudaFree(c->costs);
+    cudaFree(c->u_tilde);
+    cudaFree(c->partial);
+    cudaFree(c->counter);
+    cudaFree(c->nom_sxy);
+    for (cudaEvent_t e : c->ev)
+        if (e) cudaEventDestroy(e);
+    if (c->gp && c->gp->magic == kGpMagic) c->gp->g.n_controllers--;
+    c->magic = 0;
+    delete c;
+}
+
+bool valid_gp(gpmppi_gp h) { return h && h->magic == kGpMagic; }
+bool valid_ctrl(gpmppi_ctrl c) { return c && c->magic == kCtrlMagic && valid_gp(c->gp); }
+
+int validate_params(const gpmppi_params& p) {
+    auto bad = [](const char* what) { return fail(GPMPPI_ERR_INVALID_ARG, std::string("params: ") + what); };
+    if (p.K < 1 || p.K > GPMPPI_MAX_K) return bad("K out of range");
+    if (p.T < 1 || p.T > GPMPPI_MAX_T) return bad("T out of range");
+    const float fs[] = {p.dt, p.tau_v, p.tau_w, p.sigma[0], p.sigma[1], p.lambda, p.p_x,
+                        p.u_min[0], p.u_min[1], p.u_max[0], p.u_max[1], p.alpha[0], p.alpha[1],
+                        p.alpha[2], p.alpha[3], p.alpha[4], p.beta[0], p.beta[1], p.beta[2],
+                        p.beta[3], p.P_lane, p.P_coll, p.lane_half_width, p.v_desired};
+    for (float f : fs)
+        if (!is_finite(f)) return fail(GPMPPI_ERR_NONFINITE, "params: non-finite value");
+    if (!(p.dt > 0.0f) || !(p.tau_v > 0.0f) || !(p.tau_w > 0.0f)) return bad("dt, tau_v, tau_w must be > 0");
+    if (p.sigma[0] < 0.0f || p.sigma[1] < 0.0f) return bad("sigma must be >= 0");
+    if (!(p.lambda > 0.0f)) return bad("lambda must be > 0");
+    if (!(p.p_x > 0.0f && p.p_x < 1.0f)) return bad("p_x must lie in (0, 1)");
+    if (p.u_min[0] > p.u_max[0] || p.u_min[1] > p.u_max[1]) return bad("u_min > u_max");
+    if (!(p.lane_half_width > 0.0f)) return bad("lane_half_width must be > 0");
+    if (p.alpha[2] != 0.0f)
+        return fail(GPMPPI_ERR_UNSUPPORTED, "params: the slip term (alpha[2]) is not modelled");
+    if (p.beta[2] != 0.0f || p.beta[3] != 0.0f)
+        return fail(GPMPPI_ERR_UNSUPPORTED, "params: goal terms (beta[2], beta[3]) are not modelled");
+    if (p.variance_mode != GPMPPI_VAR_PER_SAMPLE && p.variance_mode != GPMPPI_VAR_NOMINAL)
+        return bad("unknown variance_mode");
+    if (p.precision != GPMPPI_FP32 && p.precision != GPMPPI_BF16_SPLIT) return bad("unknown precision");
+    return GPMPPI_OK;
+}
+
+int current_device(int* dev) {
+    GPM_CUDA(cudaGetDevice(dev));
+    return GPMPPI_OK;
+}
+
+int check_state(const float* state) {
+    if (!state) return fail(GPMPPI_ERR_INVALID_ARG, "state must not be NULL");
+    for (int i = 0; i < 5; ++i)
+        if (!std::isfinite(state[i])) return fail(GPMPPI_ERR_NONFINITE, "state: non-finite value");
+    return GPMPPI_OK;
+}
+
+RolloutArgs make_rollout_args(gpmppi_ctrl c, const float* state, const float* U) {
+    const gpmppi_params& p = c->p;
+    const GpDevice& g = c->gp->g;
+    RolloutArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.Xs = g.Xs[0];
+    a.alpha = g.alpha;
+    a.W = g.W[0];
+    a.obst = c->obst;
+    a.seg = c->seg;
+    a.seg_il2 = c->seg_il2;
+    a.U = U;
+    a.nom_sxy = (p.variance_mode == GPMPPI_VAR_NOMINAL) ? c->nom_sxy : nullptr;
+    a.costs = c->costs;
+    a.u_tilde = c->u_tilde;
+    a.K = p.K;
+    a.T = p.T;
+    a.N = g.N;
+    a.Np = g.Np;
+    a.O = c->O;
+    a.S = c->S;
+    a.mt = c->mt;
+    a.sf2 = g.sf2[0];
+    for (int i = 0; i < 5; ++i) a.x0[i] = state[i];
+    for (int d = 0; d < 4; ++d) a.zscale[d] = g.zscale[0][d];
+    a.dt = p.dt;
+    a.kv = (float)((double)p.dt / p.tau_v);
+    a.kw = (float)((double)p.dt / p.tau_w);
+    a.av = (float)(1.0 - (double)p.dt / p.tau_v);
+    a.aw = (float)(1.0 - (double)p.dt / p.tau_w);
+    a.sig_v = p.sigma[0];
+    a.sig_w = p.sigma[1];
+    a.umin0 = p.u_min[0];
+    a.umin1 = p.u_min[1];
+    a.umax0 = p.u_max[0];
+    a.umax1 = p.u_max[1];
+    a.c_var = p.alpha[0] + p.beta[0];
+    a.c_dev = (float)((double)p.alpha[1] / p.lane_half_width);
+    a.c_lane = p.alpha[3] * p.P_lane;
+    a.c_speed = p.alpha[4];
+    a.c_coll = p.beta[1] * p.P_coll;
+    a.r = p.lane_half_width;
+    a.v_des = p.v_desired;
+    a.sq_chi2 = (float)c->sq_chi2;
+    a.phi_inv = (float)c->phi_inv;
+    a.key0 = (uint32_t)p.seed;
+    a.key1 = (uint32_t)(p.seed >> 32);
+    a.it0 = (uint32_t)c->it;
+    a.it1 = (uint32_t)(c->it >> 32);
+    return a;
+}
+
+int check_ctrl_device(gpmppi_ctrl c) {
+    int dev = 0;
+    int rc = current_device(&dev);
+    if (rc) return rc;
+    if (dev != c->device) return fail(GPMPPI_ERR_INVALID_ARG, "controller belongs to another device");
+    return GPMPPI_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* gpmppi_last_error(void) { return g_err.c_str(); }
+
+int gpmppi_version(void) { return 100; }
+
+int gp_fit(const double* X, const double* Y, int32_t N, const gpmppi_hyper hyper[2], gpmppi_gp* out) {
+    try {
+        if (!out) return fail(GPMPPI_ERR_INVALID_ARG, "gp_fit: out must not be NULL");
+        *out = nullptr;
+        if (!hyper) return fail(GPMPPI_ERR_INVALID_ARG, "gp_fit: hyper must not be NULL");
+        if (N < 0 || N > GPMPPI_MAX_N) return fail(GPMPPI_ERR_INVALID_ARG, "gp_fit: N out of range");
+        if (N > 0 && (!X || !Y)) return fail(GPMPPI_ERR_INVALID_ARG, "gp_fit: X and Y must not be NULL");
+        for (int i = 0; i < 4 * N; ++i)
+            if (!is_finite(X[i])) return fail(GPMPPI_ERR_NONFINITE, "gp_fit: non-finite X");
+        for (int i = 0; i < 2 * N; ++i)
+            if (!is_finite(Y[i])) return fail(GPMPPI_ERR_NONFINITE, "gp_fit: non-finite Y");
+        for (int o = 0; o < 2; ++o) {
+            const gpmppi_hyper& h = hyper[o];
+            for (int d = 0; d < 4; ++d)
+                if (!is_finite(h.lengthscale[d]) || !(h.lengthscale[d] > 0.0))
+                    return fail(GPMPPI_ERR_INVALID_ARG, "gp_fit: lengthscales must be finite and > 0");
+            if (!is_finite(h.signal_var) || !(h.signal_var > 0.0))
+                return fail(GPMPPI_ERR_INVALID_ARG, "gp_fit: signal_var must be finite and > 0");
+            if (!is_finite(h.noise_var) || h.noise_var < 0.0)
+                return fail(GPMPPI_ERR_INVALID_ARG, "gp_fit: noise_var must be finite and >= 0");
+        }
+        gpmppi_gp h = new (std::nothrow) gpmppi_gp_s;
+        if (!h) return fail(GPMPPI_ERR_OOM, "gp_fit: host allocation failed");
+        h->g.hyper[0] = hyper[0];
+        h->g.hyper[1] = hyper[1];
+        h->g.shared = std::memcmp(hyper[0].lengthscale, hyper[1].lengthscale, sizeof(double) * 4) == 0 &&
+                      hyper[0].signal_var == hyper[1].signal_var &&
+                      hyper[0].noise_var == hyper[1].noise_var;
+        int rc = current_device(&h->g.device);
+        if (rc) {
+            delete h;
+            return rc;
+        }
+        cudaStream_t st = nullptr;
+        cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            delete h;
+            return cuda_fail(e, "gp_fit: stream");
+        }
+        rc = gp_fit_device(h->g, X, Y, N, st);
+        cudaStreamDestroy(st);
+        if (rc) {
+            free_gp(h);
+            return rc;
+        }
+        *out = h;
+        return GPMPPI_OK;
+    } catch (...) {
+        return fail(GPMPPI_ERR_CUDA, "gp_fit: unexpected exception");
+    }
+}
+
+int gp_destroy(gpmppi_gp gp) {
+    if (!valid_gp(gp)) return fail(GPMPPI_ERR_INVALID_ARG, "gp_destroy: invalid handle");
+    if (gp->g.n_controllers > 0)
+        return fail(GPMPPI_ERR_INVALID_ARG, "gp_destroy: controllers still use this GP");
+    free_gp(gp);
+    return GPMPPI_OK;
+}
+
+int gp_factors(gpmppi_gp gp, int32_t j, double* Linv, double* alpha) {
+    if (!valid_gp(gp)) return fail(GPMPPI_ERR_INVALID_ARG, "gp_factors: invalid handle");
+    if (j != 0 && j != 1) return fail(GPMPPI_ERR_INVALID_ARG, "gp_factors: output must be 0 or 1");
+    const int N = gp->g.N;
+    if (N == 0) return GPMPPI_OK;
+    if (Linv)
+        GPM_CUDA(cudaMemcpy(Linv, gp->g.Linv64[j], sizeof(double) * (size_t)N * N, cudaMemcpyDeviceToHost));
+    if (alpha) GPM_CUDA(cudaMemcpy(alpha, gp->g.alpha64[j], sizeof(double) * N, cudaMemcpyDeviceToHost));
+    return GPMPPI_OK;
+}
+
+int gp_predict(gpmppi_gp gp, const float* Z, int32_t M, float* mean, float* var, void* stream) {
+    if (!valid_gp(gp)) return fail(GPMPPI_ERR_INVALID_ARG, "gp_predict: invalid handle");
+    if (M < 0) return fail(GPMPPI_ERR_INVALID_ARG, "gp_predict: M must be >= 0");
+    if (M == 0) return GPMPPI_OK;
+    int rc;
+    if ((rc = check_dev_ptr(Z, "gp_predict: Z", false))) return rc;
+    if ((rc = check_dev_ptr(mean, "gp_predict: mean", false))) return rc;
+    if ((rc = check_dev_ptr(var, "gp_predict: var", false))) return rc;
+    return launch_gp_predict(gp->g, Z, M, mean, var, (cudaStream_t)stream);
+}
+
+int mppi_create(const gpmppi_params* p, const float* obstacles, int32_t O, const float* path,
+                int32_t P, gpmppi_gp gp, gpmppi_ctrl* out) {
+    try {
+        if (!out) return fail(GPMPPI_ERR_INVALID_ARG, "mppi_create: out must not be NULL");
+        *out = nullptr;
+        if (!p) return fail(GPMPPI_ERR_INVALID_ARG, "mppi_create: params must not be NULL");
+        if (!valid_gp(gp)) return fail(GPMPPI_ERR_INVALID_ARG, "mppi_create: invalid GP handle");
+        int rc = validate_params(*p);
+        if (rc) return rc;
+        if (p->precision == GPMPPI_BF16_SPLIT)
+            return fail(GPMPPI_ERR_UNSUPPORTED, "mppi_create: BF16 split precision is not built");
+        if (!gp->g.shared)
+            return fail(GPMPPI_ERR_UNSUPPORTED,
+                        "mppi_create: the two GP outputs must share hyper-parameters");
+        if (O < 0 || O > GPMPPI_MAX_OBSTACLES) return fail(GPMPPI_ERR_INVALID_ARG, "mppi_create: O out of range");
+        if (O > 0 && !obstacles) return fail(GPMPPI_ERR_INVALID_ARG, "mppi_create: obstacles is NULL");
+        if (P < 1 || P > GPMPPI_MAX_PATH) return fail(GPMPPI_ERR_INVALID_ARG, "mppi_create: P out of range");
+        if (!path) return fail(GPMPPI_ERR_INVALID_ARG, "mppi_create: path is NULL");
+        for (int i = 0; i < 3 * O; ++i)
+            if (!is_finite(obstacles[i])) return fail(GPMPPI_ERR_NONFINITE, "mppi_create: non-finite obstacle");
+        for (int i = 0; i < O; ++i)
+            if (!(obstacles[3 * i + 2] > 0.0f)) return fail(GPMPPI_ERR_INVALID_ARG, "mppi_create: radius <= 0");
+        for (int i = 0; i < 2 * P; ++i)
+            if (!is_finite(path[i])) return fail(GPMPPI_ERR_NONFINITE, "mppi_create: non-finite path");
+        int dev = 0;
+        if ((rc = current_device(&dev))) return rc;
+        if (dev != gp->g.device) return fail(GPMPPI_ERR_INVALID_ARG, "mppi_create: GP lives on another device");
+
+        // launch geometry
+        const int mtp = rollout_fp32_mtp(gp->g.Np);
+        int nsm = 0, smem_optin = 0;
+        GPM_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        GPM_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+        if (rollout_fp32_smem_bytes(gp->g.Np, mtp) > smem_optin)
+            return fail(GPMPPI_ERR_UNSUPPORTED, "mppi_create: GP too large for shared memory");
+
+        gpmppi_ctrl c = new (std::nothrow) gpmppi_ctrl_s;
+        if (!c) return fail(GPMPPI_ERR_OOM, "mppi_create: host allocation failed");
+        c->p = *p;
+        c->gp = gp;
+        c->device = dev;
+        c->O = O;
+        c->P = P;
+        c->S = (P > 1) ? (P - 1) : 1;
+        int mt = (p->K + nsm - 1) / nsm;
+        if (const char* env = std::getenv("GPMPPI_SAMPLES_PER_CTA")) mt = std::atoi(env);
+        c->mt = mt < 1 ? 1 : (mt > mtp ? mtp : mt);
+        c->n_upd = (p->K + 255) / 256;
+        c->sq_chi2 = std::sqrt(chi2_2_quantile(p->p_x));
+        c->phi_inv = normal_quantile(p->p_x);
+        gp->g.n_controllers++;
+
+        std::vector<float4> seg(c->S);
+        std::vector<float> il2(c->S);
+        if (P == 1) {
+            seg[0] = make_float4(path[0], path[1], 0.0f, 0.0f);
+            il2[0] = 0.0f;
+        } else {
+            for (int i = 0; i < P - 1; ++i) {
+                const double ax = path[2 * i], ay = path[2 * i + 1];
+                const double dx = (double)path[2 * i + 2] - ax, dy = (double)path[2 * i + 3] - ay;
+                const double l2 = dx * dx + dy * dy;
+                seg[i] = make_float4((float)ax, (float)ay, (float)dx, (float)dy);
+                il2[i] = l2 > 0.0 ? (float)(1.0 / l2) : 0.0f;
+            }
+        }
+        const size_t K = (size_t)p->K, T = (size_t)p->T;
+        auto alloc = [&](void** ptr, size_t bytes) -> int {
+            cudaError_t e = cudaMalloc(ptr, bytes > 0 ? bytes : 16);
+            if (e != cudaSuccess) return cuda_fail(e, "mppi_create: cudaMalloc");
+            return GPMPPI_OK;
+        };
+        if ((rc = alloc((void**)&c->obst, sizeof(float) * 3 * O)) ||
+            (rc = alloc((void**)&c->seg, sizeof(float4) * c->S)) ||
+            (rc = alloc((void**)&c->seg_il2, sizeof(float) * c->S)) ||
+            (rc = alloc((void**)&c->costs, sizeof(float) * K)) ||
+            (rc = alloc((void**)&c->u_tilde, sizeof(float2) * K * T)) ||
+            (rc = alloc((void**)&c->partial, sizeof(float) * 2 * T * c->n_upd)) ||
+            (rc = alloc((void**)&c->counter, sizeof(unsigned int))) ||
+            (rc = alloc((void**)&c->nom_sxy, sizeof(float) * 3 * T))) {
+            free_ctrl(c);
+            return rc;
+        }
+        cudaError_t e = cudaSuccess;
+        if (O > 0 && e == cudaSuccess)
+            e = cudaMemcpy(c->obst, obstacles, sizeof(float) * 3 * O, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(c->seg, seg.data(), sizeof(float4) * c->S, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(c->seg_il2, il2.data(), sizeof(float) * c->S, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemset(c->counter, 0, sizeof(unsigned int));
+        if (e == cudaSuccess) e = cudaMemset(c->nom_sxy, 0, sizeof(float) * 3 * T);
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) {
+            free_ctrl(c);
+            return cuda_fail(e, "mppi_create: upload");
+        }
+        *out = c;
+        return GPMPPI_OK;
+    } catch (...) {
+        return fail(GPMPPI_ERR_CUDA, "mppi_create: unexpected exception");
+    }
+}
+
+int mppi_step(gpmppi_ctrl c, const float state[5], const float* U_nom, float* U_new,
+              float* weights, float* costs, void* stream) {
+    if (!valid_ctrl(c)) return fail(GPMPPI_ERR_INVALID_ARG, "mppi_step: invalid handle");
+    int rc;
+    if ((rc = check_ctrl_device(c))) return rc;
+    if ((rc = check_state(state))) return rc;
+    if ((rc = check_dev_ptr(U_nom, "mppi_step: U_nom", false))) return rc;
+    if ((rc = check_dev_ptr(U_new, "mppi_step: U_new", false))) return rc;
+    if ((rc = check_dev_ptr(weights, "mppi_step: weights", true))) return rc;
+    if ((rc = check_dev_ptr(costs, "mppi_step: costs", true))) return rc;
+    if (U_nom == U_new) return fail(GPMPPI_ERR_INVALID_ARG, "mppi_step: U_new must not alias U_nom");
+    cudaStream_t st = (cudaStream_t)stream;
+    RolloutArgs a = make_rollout_args(c, state, U_nom);
+    if (costs) a.costs = costs;
+    if (c->profiling) GPM_CUDA(cudaEventRecord(c->ev[0], st));
+    if ((rc = launch_rollout_fp32(a, false, st))) return rc;
+    if (c->profiling) GPM_CUDA(cudaEventRecord(c->ev[1], st));
+    UpdateArgs u;
+    u.costs = a.costs;
+    u.u_tilde = c->u_tilde;
+    u.U = U_nom;
+    u.U_new = U_new;
+    u.weights = weights;
+    u.partial = c->partial;
+    u.counter = c->counter;
+    u.K = c->p.K;
+    u.T = c->p.T;
+    u.per_cta = 256;
+    u.inv_lambda = 1.0f / c->p.lambda;
+    if ((rc = launch_update(u, c->n_upd, st))) return rc;
+    if (c->p.variance_mode == GPMPPI_VAR_NOMINAL) {
+        RolloutArgs n = make_rollout_args(c, state, U_new);
+        if ((rc = launch_nominal(n, c->nom_sxy, st))) return rc;
+    }
+    if (c->profiling) {
+        GPM_CUDA(cudaEventRecord(c->ev[2], st));
+        c->profiled = true;
+    }
+    c->it++;
+    return GPMPPI_OK;
+}
+
+int mppi_rollout_trace(gpmppi_ctrl c, const float state[5], const float* U_nom, float* mu,
+                       float* sigma, float* stage, float* margins, float* costs, void* stream) {
+    if (!valid_ctrl(c)) return fail(GPMPPI_ERR_INVALID_ARG, "mppi_rollout_trace: invalid handle");
+    int rc;
+    if ((rc = check_ctrl_device(c))) return rc;
+    if ((rc = check_state(state))) return rc;
+    if ((rc = check_dev_ptr(U_nom, "mppi_rollout_trace: U_nom", false))) return rc;
+    if ((rc = check_dev_ptr(mu, "mppi_rollout_trace: mu", true))) return rc;
+    if ((rc = check_dev_ptr(sigma, "mppi_rollout_trace: sigma", true))) return rc;
+    if ((rc = check_dev_ptr(stage, "mppi_rollout_trace: stage", true))) return rc;
+    if ((rc = check_dev_ptr(margins, "mppi_rollout_trace: margins", true))) return rc;
+    if ((rc = check_dev_ptr(costs, "mppi_rollout_trace: costs", true))) return rc;
+    RolloutArgs a = make_rollout_args(c, state, U_nom);
+    if (costs) a.costs = costs;
+    a.tr_mu = mu;
+    a.tr_sig = sigma;
+    a.tr_stage = stage;
+    a.tr_margin = margins;
+    return launch_rollout_fp32(a, true, (cudaStream_t)stream);
+}
+
+int mppi_set_iteration(gpmppi_ctrl c, uint64_t it) {
+    if (!valid_ctrl(c)) return fail(GPMPPI_ERR_INVALID_ARG, "mppi_set_iteration: invalid handle");
+    c->it = it;
+    return GPMPPI_OK;
+}
+
+int mppi_get_iteration(gpmppi_ctrl c, uint64_t* it) {
+    if (!valid_ctrl(c)) return fail(GPMPPI_ERR_INVALID_ARG, "mppi_get_iteration: invalid handle");
+    if (!it) return fail(GPMPPI_ERR_INVALID_ARG, "mppi_get_iteration: it must not be NULL");
+    *it = c->it;
+    return GPMPPI_OK;
+}
+
+int mppi_nominal_sxy(gpmppi_ctrl c, float* sxy, void* stream) {
+    if (!valid_ctrl(c)) return fail(GPMPPI_ERR_INVALID_ARG, "mppi_nominal_sxy: invalid handle");
+    int rc;
+    if ((rc = check_dev_ptr(sxy, "mppi_nominal_sxy: sxy", false))) return rc;
+    GPM_CUDA(cudaMemcpyAsync(sxy, c->nom_sxy, sizeof(float) * 3 * c->p.T, cudaMemcpyDeviceToDevice,
+                             (cudaStream_t)stream));
+    return GPMPPI_OK;
+}
+
+int mppi_set_profiling(gpmppi_ctrl c, int32_t on) {
+    if (!valid_ctrl(c)) return fail(GPMPPI_ERR_INVALID_ARG, "mppi_set_profiling: invalid handle");
+    if (on && !c->ev[0])
+        for (cudaEvent_t& e : c->ev) GPM_CUDA(cudaEventCreate(&e));
+    c->profiling = on != 0;
+    c->profiled = false;
+    return GPMPPI_OK;
+}
+
+int mppi_last_profile(gpmppi_ctrl c, float* rollout_ms, float* update_ms) {
+    if (!valid_ctrl(c)) return fail(GPMPPI_ERR_INVALID_ARG, "mppi_last_profile: invalid handle");
+    if (!c->profiled) return fail(GPMPPI_ERR_INVALID_ARG, "mppi_last_profile: no profiled step");
+    GPM_CUDA(cudaEventSynchronize(c->ev[2]));
+    float a = 0.0f, b = 0.0f;
+    GPM_CUDA(cudaEventElapsedTime(&a, c->ev[0], c->ev[1]));
+    GPM_CUDA(cudaEventElapsedTime(&b, c->ev[1], c->ev[2]));
+    if (rollout_ms) *rollout_ms = a;
+    if (update_ms) *update_ms = b;
+    return GPMPPI_OK;
+}
+
+int mppi_destroy(gpmppi_ctrl c) {
+    if (!c || c->magic != kCtrlMagic) return fail(GPMPPI_ERR_INVALID_ARG, "mppi_destroy: invalid handle");
+    cudaDeviceSynchronize();
+    free_ctrl(c);
+    return GPMPPI_OK;
+}
+
+int gpmppi_philox(uint64_t seed, const uint32_t* ctr, int32_t M, uint32_t* out, void* stream) {
+    if (M < 0) return fail(GPMPPI_ERR_INVALID_ARG, "gpmppi_philox: M must be >= 0");
+    if (M == 0) return GPMPPI_OK;
+    int rc;
+    if ((rc = check_dev_ptr(ctr, "gpmppi_philox: ctr", false))) return rc;
+    if ((rc = check_dev_ptr(out, "gpmppi_philox: out", false))) return rc;
+    if ((reinterpret_cast<uintptr_t>(ctr) | reinterpret_cast<uintptr_t>(out)) & 15u)
+        return fail(GPMPPI_ERR_INVALID_ARG, "gpmppi_philox: arrays must be 16-byte aligned");
+    return launch_philox(seed, ctr, M, out, (cudaStream_t)stream);
+}
+
+int gpmppi_control_noise(uint64_t seed, int32_t K, int32_t T, uint64_t it, const float sigma[2],
+                         float* eps, void* stream) {
+    if (K < 0 || T < 0 || !sigma) return fail(GPMPPI_ERR_INVALID_ARG, "gpmppi_control_noise: bad arguments");
+    if ((size_t)K * T == 0) return GPMPPI_OK;
+    int rc;
+    if ((rc = check_dev_ptr(eps, "gpmppi_control_noise: eps", false))) return rc;
+    if (reinterpret_cast<uintptr_t>(eps) & 7u)
+        return fail(GPMPPI_ERR_INVALID_ARG, "gpmppi_control_noise: eps must be 8-byte aligned");
+    return launch_noise(seed, K, T, it, sigma[0], sigma[1], eps, (cudaStream_t)stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,170 @@
+// Internal declarations shared by the CUDA translation units of libgpmppi.
+//
+// Nothing here is part of the C ABI (include/gpmppi.h is).  The device
+// helpers below are used by every kernel that draws control noise, so the
+// rollout, the update and the debug entry points see bit-identical draws.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "gpmppi.h"
+
+namespace gpm {
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11).  Round function on the
+// counter words (c0,c1,c2,c3) with key (k0,k1):
+//   c0' = hi(M1 c2) ^ c1 ^ k0,  c1' = lo(M1 c2),
+//   c2' = hi(M0 c0) ^ c3 ^ k1,  c3' = lo(M0 c0),
+// and the Weyl key schedule k += (W0, W1) between rounds.
+// ---------------------------------------------------------------------------
+constexpr uint32_t kPhiloxM0 = 0xD2511F53u;
+constexpr uint32_t kPhiloxM1 = 0xCD9E8D57u;
+constexpr uint32_t kPhiloxW0 = 0x9E3779B9u;
+constexpr uint32_t kPhiloxW1 = 0xBB67AE85u;
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k0 += kPhiloxW0;
+            k1 += kPhiloxW1;
+        }
+        const uint32_t lo0 = kPhiloxM0 * c.x;
+        const uint32_t hi0 = __umulhi(kPhiloxM0, c.x);
+        const uint32_t lo1 = kPhiloxM1 * c.z;
+        const uint32_t hi1 = __umulhi(kPhiloxM1, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    }
+    return c;
+}
+
+// Standard normal pair from two Philox words by Box-Muller with the
+// uniforms u = (w + 1/2) 2^-32 in (0,1).  -2 ln u0 is evaluated through
+// log1p(-(1 - u0)) when u0 >= 1/2, where 1 - u0 = (~w0 + 1/2) 2^-32 is formed
+// without cancellation; the angle 2 pi u1 goes through sincospi.
+__device__ __forceinline__ float2 box_muller(uint32_t w0, uint32_t w1) {
+    float r2;
+    if (w0 >= 0x80000000u) {
+        const float t = (__uint2float_rn(~w0) + 0.5f) * 0x1p-32f;
+        r2 = -2.0f * log1pf(-t);
+    } else {
+        const float u0 = (__uint2float_rn(w0) + 0.5f) * 0x1p-32f;
+        r2 = -2.0f * logf(u0);
+    }
+    const float rad = sqrtf(r2);
+    const float u1 = (__uint2float_rn(w1) + 0.5f) * 0x1p-32f;
+    float s, c;
+    sincospif(2.0f * u1, &s, &c);
+    return make_float2(rad * c, rad * s);
+}
+
+// Control perturbation of sample s at step k, iteration (it0 = low word,
+// it1 = high word): counter (k, s, it0, it1), key (seed_lo, seed_hi).
+__device__ __forceinline__ float2 control_eps(uint32_t k, uint32_t s, uint32_t it0, uint32_t it1,
+                                              uint32_t key0, uint32_t key1, float sig_v, float sig_w) {
+    const uint4 w = philox4x32_10(make_uint4(k, s, it0, it1), key0, key1);
+    const float2 z = box_muller(w.x, w.y);
+    return make_float2(sig_v * z.x, sig_w * z.y);
+}
+
+// ---------------------------------------------------------------------------
+// error plumbing (host)
+// ---------------------------------------------------------------------------
+void set_error(const std::string& msg);
+int fail(int code, const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what);
+
+#define GPM_CUDA(call)                                      \
+    do {                                                    \
+        cudaError_t e_ = (call);                            \
+        if (e_ != cudaSuccess) return ::gpm::cuda_fail(e_, #call); \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// device-side layout of a fitted GP
+// ---------------------------------------------------------------------------
+struct GpDevice {
+    int N = 0;        // training points
+    int Np = 0;       // N rounded up to a multiple of 16 (W is Np x Np)
+    int device = 0;
+    bool shared = true;          // both outputs share their hyper-parameters
+    float sf2[2] = {0, 0};       // signal variances
+    // per output o: Xs[o] = N x 4 floats, X scaled by sqrt(log2(e)/2)/l_d so
+    // that k = sf2 * exp2(-|xs - zs|^2); W[o] = Np x Np floats, W[j][i] =
+    // (L^-1)[i][j] for i >= j, zero elsewhere (row j of L^-T).
+    float* Xs[2] = {nullptr, nullptr};
+    float* W[2] = {nullptr, nullptr};
+    float* alpha = nullptr;      // N x 2 floats (alpha_v, alpha_w) per point
+    float zscale[2][4] = {};     // the per-input scale applied to queries
+    // FP64 factors kept for export: Linv64[o] N x N, alpha64[o] N
+    double* Linv64[2] = {nullptr, nullptr};
+    double* alpha64[2] = {nullptr, nullptr};
+    gpmppi_hyper hyper[2];
+    int n_controllers = 0;
+};
+
+// Everything one rollout launch needs (passed by value as a kernel argument).
+struct RolloutArgs {
+    const float* Xs;        // N x 4 scaled GP inputs
+    const float* alpha;     // N x 2
+    const float* W;         // Np x Np
+    const float* obst;      // O x 3 (cx, cy, r)
+    const float4* seg;      // S segments: (ax, ay, bx - ax, by - ay)
+    const float* seg_il2;   // S: 1 / |b - a|^2, or 0 for a degenerate segment
+    const float* U;         // T x 2 nominal controls
+    const float* nom_sxy;   // T x 3 tightening covariance (nominal mode) or null
+    float* costs;           // K
+    float2* u_tilde;        // T x K clamped sampled controls (for the update)
+    // optional per-(s,k) records
+    float* tr_mu;           // K x T x 5
+    float* tr_sig;          // K x T x 15
+    float* tr_stage;        // K x T
+    float* tr_margin;       // K x T x 2
+    int K, T, N, Np, O, S;
+    int mt;                 // samples per CTA
+    float sf2;
+    float x0[5];
+    float zscale[4];
+    float dt, kv, kw, av, aw;   // kv = dt/tau_v, av = 1 - kv (same for omega)
+    float sig_v, sig_w;
+    float umin0, umin1, umax0, umax1;
+    float c_var;            // (alpha_0 + beta_0): weight of trace(C)
+    float c_dev;            // alpha_1 / r
+    float c_lane;           // alpha_3 * P_lane
+    float c_speed;          // alpha_4
+    float c_coll;           // beta_1 * P_coll
+    float r, v_des, sq_chi2, phi_inv;
+    uint32_t key0, key1, it0, it1;
+};
+
+struct UpdateArgs {
+    const float* costs;     // K
+    const float2* u_tilde;  // T x K
+    const float* U;         // T x 2
+    float* U_new;           // T x 2
+    float* weights;         // K or null
+    float* partial;         // n_cta x T x 2 scratch
+    unsigned int* counter;  // one scratch word, zero between launches
+    int K, T;
+    int per_cta;            // samples per CTA
+    float inv_lambda;
+};
+
+// launchers (defined in the .cu files)
+int launch_rollout_fp32(const RolloutArgs& a, bool trace, cudaStream_t st);
+int launch_update(const UpdateArgs& a, int n_cta, cudaStream_t st);
+int launch_gp_predict(const GpDevice& g, const float* Z, int M, float* mean, float* var,
+                      cudaStream_t st);
+int gp_fit_device(GpDevice& g, const double* X, const double* Y, int N, cudaStream_t st);
+int launch_philox(uint64_t seed, const uint32_t* ctr, int M, uint32_t* out, cudaStream_t st);
+int launch_noise(uint64_t seed, int K, int T, uint64_t it, float sv, float sw, float* eps,
+                 cudaStream_t st);
+int launch_nominal(const RolloutArgs& a, float* sxy_out, cudaStream_t st);
+int rollout_fp32_smem_bytes(int Np, int mtp);
+int rollout_fp32_mtp(int Np);
+
+}  // namespace gpm
