@@ -183,6 +183,31 @@ int mppi_last_profile(gpmppi_ctrl c, float* rollout_ms, float* update_ms);
 /* Release a controller and its device buffers (synchronises its device). */
 int mppi_destroy(gpmppi_ctrl c);
 
+/* Allocation-free weights-and-update step (the paper has no counterpart;
+ * this is a deployment aid).  Some callers cannot allocate device memory
+ * once running: a controller in a real-time loop whose memory is fixed at
+ * start-up (cudaMalloc may synchronise the device and has no latency bound),
+ * or a framework that owns all device memory and forbids plug-ins from
+ * allocating.  This call runs the same softmax weights and control update as
+ * mppi_step's second kernel, with its scratch (per-CTA partial sums and a
+ * completion ticket) in a fixed static device array of 512 KiB that every
+ * GPU loading the library holds until the process exits.  It allocates
+ * nothing.
+ *   costs    device, K floats: the samples' total costs S_s
+ *   u_tilde  device, T x K x 2 floats, step-major: the clamped sampled
+ *            controls u~ of sample s at step k at [(k*K + s)*2 + {0,1}]
+ *   U_nom    device, T x 2 floats; U_new device, T x 2 floats (output,
+ *            U_nom + sum_s w_s (u~_s - U_nom)); weights device, K floats or NULL
+ *   lambda   temperature > 0
+ * Limit: ceil(K / 256) * T <= 65536 (and T <= GPMPPI_MAX_T); larger sizes
+ * return GPMPPI_ERR_INVALID_ARG.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress); make that first call before
+ * any stream capture.  All calls share the one array, so calls that overlap
+ * on the GPU (other streams, other host threads) race: serialise them. */
+int mppi_update_noalloc(const float* costs, const float* u_tilde, const float* U_nom,
+                        float* U_new, float* weights, int32_t K, int32_t T, float lambda,
+                        void* stream);
+
 /* Raw Philox4x32-10 blocks as the kernels draw them (Salmon et al., SC'11):
  *   ctr  device, M x 4 uint32 counters; out device, M x 4 uint32 words. */
 int gpmppi_philox(uint64_t seed, const uint32_t* ctr, int32_t M, uint32_t* out, void* stream);

@@ -34,7 +34,7 @@ GPMPPI_BF16_SPLIT = 1
 # names every build of the library exports (checked by the CPU test suite)
 EXPORTS = ("gp_fit", "gp_destroy", "gp_factors", "gp_predict", "mppi_create", "mppi_step",
            "mppi_rollout_trace", "mppi_set_iteration", "mppi_get_iteration", "mppi_nominal_sxy",
-           "mppi_destroy", "mppi_set_profiling", "mppi_last_profile", "gpmppi_philox", "gpmppi_control_noise", "gpmppi_last_error",
+           "mppi_destroy", "mppi_set_profiling", "mppi_last_profile", "mppi_update_noalloc", "gpmppi_philox", "gpmppi_control_noise", "gpmppi_last_error",
            "gpmppi_version")
 
 
@@ -88,6 +88,7 @@ def load():
         "mppi_destroy": [vp],
         "mppi_set_profiling": [vp, i32],
         "mppi_last_profile": [vp, vp, vp],
+        "mppi_update_noalloc": [vp, vp, vp, vp, vp, i32, i32, ctypes.c_float, vp],
         "gpmppi_philox": [u64, vp, i32, vp, vp],
         "gpmppi_control_noise": [u64, i32, i32, u64, vp, vp, vp],
         "gpmppi_version": [],
@@ -294,6 +295,18 @@ def mppi_destroy(ctrl: Ctrl):
     if ctrl.handle:
         _check(load().mppi_destroy(ctrl.handle))
         ctrl.handle = None
+
+
+def mppi_update_noalloc(costs, u_tilde, U_nom, U_new, weights, K: int, T: int, lam: float,
+                        stream=None):
+    """Weights and control update with no device allocation (for callers that
+    cannot allocate once running); u_tilde is (T, K, 2), step-major."""
+    _check(load().mppi_update_noalloc(_dptr(costs, numel=K, name="costs"),
+                                      _dptr(u_tilde, numel=2 * K * T, name="u_tilde"),
+                                      _dptr(U_nom, numel=2 * T, name="U_nom"),
+                                      _dptr(U_new, numel=2 * T, name="U_new"),
+                                      _dptr(weights, numel=K, name="weights"), K, T, float(lam),
+                                      _stream(stream)))
 
 
 def gpmppi_philox(seed: int, ctr, out, stream=None):
