@@ -50,12 +50,27 @@ def fp32_peak_tflops(sm_mhz=2070.0, n_sm=152):
     return n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
+PRECISIONS = {"fp32": 0, "bf16split": 1, "fp16split": 2}
+
+
+def measured_tensor_peak():
+    """Dense 16-bit tensor peak: the measured BF16 burst figure (FP16 has the
+    same nominal rate), else the recipe's fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            v = float(json.load(fh)["bf16_tflops"])
+        return v, "measured BF16 dense burst (cuBLAS), same nominal rate for FP16"
+    except (OSError, KeyError, ValueError):
+        return 1900.0, "fallback 1.9 PFLOP/s BF16 dense"
+
+
 def describe(sc):
     P = sc.params
+    prec = {v: k for k, v in PRECISIONS.items()}[P.precision]
     return {"workload": f"{sc.name}: K={P.K} T={P.T} N={sc.N} obstacles={sc.obstacles.shape[0]} "
-                        f"path={sc.meta.get('path')} ({sc.path.shape[0]} vertices), FP32",
+                        f"path={sc.meta.get('path')} ({sc.path.shape[0]} vertices), {prec}",
             "K": P.K, "T": P.T, "N": sc.N, "obstacles": int(sc.obstacles.shape[0]),
-            "path_vertices": int(sc.path.shape[0]), "precision": "fp32",
+            "path_vertices": int(sc.path.shape[0]), "precision": prec,
             "variance_mode": "per_sample",
             "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)"}
 
@@ -239,7 +254,7 @@ def run_ours(args):
         torch.cuda.set_device(0)
     B.build()
     dev = torch.device("cuda", torch.cuda.current_device())
-    sc = S.scenario(WORKLOAD, seed=1 + rank)
+    sc = S.scenario(args.workload, seed=1 + rank, precision=PRECISIONS[args.precision])
     P = sc.params
     g = gp.gp_fit(sc.X, sc.Y, sc.hyper)
     ctrl = gp.mppi_create(P, sc.obstacles, sc.path, g)
@@ -321,10 +336,17 @@ def run_ours(args):
     S_seg = max(sc.path.shape[0] - 1, 1)
     flops = rollout_flops_per_sample_step(sc.N, sc.obstacles.shape[0], S_seg) * P.K * P.T
     r_avg = sum(rollout_ms) / len(rollout_ms)
-    sm_max = (clk or {}).get("sm_max_mhz") or 2070.0
-    peak = fp32_peak_tflops(2070.0)
     achieved = flops / (r_avg / 1e3) / 1e12
-    traffic = committed_traffic()
+    traffic = committed_traffic() if P.precision == 0 else None
+    if P.precision == 0:
+        roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak_tflops(2070.0), "unit": "TFLOP/s",
+                "traffic": traffic, "kernel": "k_rollout_fp32",
+                "peak_note": "FP32 FMA pipe 152 SM x 128 lanes x 2 flops x 2070 MHz (derived)"}
+    else:
+        peak, note = measured_tensor_peak()
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "traffic": traffic, "kernel": "k_rollout_mma", "peak_note": note}
+    roof["frac"] = roof["achieved"] / roof["peak"]
     if rank != 0:
         if ws > 1:
             torch.distributed.destroy_process_group()
@@ -338,17 +360,13 @@ def run_ours(args):
         "config": describe(sc),
         "gpu_launches": 2 * args.steps,
         "kernel_ms": {"rollout_avg": r_avg, "update_avg": sum(update_ms) / len(update_ms)},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": traffic,
-                     "kernel": "k_rollout_fp32",
-                     "peak_note": "FP32 FMA pipe 152 SM x 128 lanes x 2 flops x 2070 MHz (derived)"},
+        "roofline": roof,
         "cpu_baseline": cpu_baseline() if (rank == 0 and ws == 1 and not args.no_cpu) else None,
         "e2e": {"value": units / e2e_s, "unit": "sample-steps/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "clocks": clk,
         "wall_s_timed_region": t_wall,
     }
-    del sm_max
     print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
@@ -366,6 +384,8 @@ def main():
     ap.add_argument("--ref-rows", type=int, default=128,
                     help="samples per reference (oracle) step")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline leg")
+    ap.add_argument("--workload", default=WORKLOAD, help="scenario name (cfg2 is the reported workload)")
+    ap.add_argument("--precision", default="fp32", choices=sorted(PRECISIONS))
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -51,9 +51,10 @@ extern "C" {
 #define GPMPPI_VAR_PER_SAMPLE 0   /* each sample's own propagated Sigma (Eq. 10)     */
 #define GPMPPI_VAR_NOMINAL 1      /* Alg. 1 Step 2: Sigma along the previous update */
 
-/* arithmetic of the GP variance contraction */
-#define GPMPPI_FP32 0
-#define GPMPPI_BF16_SPLIT 1
+/* arithmetic of the GP variance contraction |L^-1 k*|^2 */
+#define GPMPPI_FP32 0         /* FP32 on the CUDA cores                                   */
+#define GPMPPI_BF16_SPLIT 1   /* tensor cores: BF16 hi/lo operands, 3 products, FP32 sums */
+#define GPMPPI_FP16_SPLIT 2   /* tensor cores: FP16 hi/lo operands, 3 products, FP32 sums */
 
 /* limits of this build */
 #define GPMPPI_MAX_N 4096         /* GP training points      */
@@ -92,7 +93,7 @@ typedef struct gpmppi_params {
     float v_desired;         /* v_desired of Eq. 11                                 */
     uint64_t seed;           /* Philox key                                          */
     int32_t variance_mode;   /* GPMPPI_VAR_*                                        */
-    int32_t precision;       /* GPMPPI_FP32 or GPMPPI_BF16_SPLIT                    */
+    int32_t precision;       /* GPMPPI_FP32, GPMPPI_BF16_SPLIT or GPMPPI_FP16_SPLIT */
 } gpmppi_params;
 
 /* Fit the two residual GPs of Sec. III-A (outputs delta_v and delta_omega)
@@ -180,6 +181,12 @@ int mppi_nominal_sxy(gpmppi_ctrl c, float* sxy, void* stream);
 int mppi_set_profiling(gpmppi_ctrl c, int32_t on);
 int mppi_last_profile(gpmppi_ctrl c, float* rollout_ms, float* update_ms);
 
+/* Device-side status of the controller's kernels since the last check:
+ * GPMPPI_OK, or GPMPPI_ERR_TIMEOUT when a rollout kernel gave up a bounded
+ * wait for one of its shared-memory tile copies (its outputs are then
+ * invalid).  Synchronises the device; clears the status. */
+int mppi_device_status(gpmppi_ctrl c);
+
 /* Release a controller and its device buffers (synchronises its device). */
 int mppi_destroy(gpmppi_ctrl c);
 
@@ -216,6 +223,18 @@ int gpmppi_philox(uint64_t seed, const uint32_t* ctr, int32_t M, uint32_t* out, 
  * as the rollout draws them before clamping (Alg. 1 "Sample eps^s"). */
 int gpmppi_control_noise(uint64_t seed, int32_t K, int32_t T, uint64_t it, const float sigma[2],
                          float* eps, void* stream);
+
+/* Tensor-core self-test (diagnostic): D = A B^T on one CTA with the
+ * library's tcgen05 operand layout, descriptors and TMEM path.
+ *   fmt      0 = FP16, 1 = BF16 (A and B share it)
+ *   N        64, 128 or 256 (rows of B, columns of D); K 16, 32, 48 or 64
+ *   variant  0 = the library's descriptor convention; 1 = leading and stride
+ *            byte offsets exchanged (N <= 128), to show which one the
+ *            hardware expects
+ *   A device 128 x K, B device N x K (16-bit, row-major), D device 128 x N floats
+ * Blocking; GPMPPI_ERR_TIMEOUT if the MMA completion did not arrive. */
+int gpmppi_mma_selftest(int32_t fmt, int32_t N, int32_t K, int32_t variant, const uint16_t* A,
+                        const uint16_t* B, float* D);
 
 /* Thread-local message describing the last failed call ("" if none). */
 const char* gpmppi_last_error(void);

@@ -30,11 +30,12 @@ GPMPPI_VAR_PER_SAMPLE = 0
 GPMPPI_VAR_NOMINAL = 1
 GPMPPI_FP32 = 0
 GPMPPI_BF16_SPLIT = 1
+GPMPPI_FP16_SPLIT = 2
 
 # names every build of the library exports (checked by the CPU test suite)
 EXPORTS = ("gp_fit", "gp_destroy", "gp_factors", "gp_predict", "mppi_create", "mppi_step",
            "mppi_rollout_trace", "mppi_set_iteration", "mppi_get_iteration", "mppi_nominal_sxy",
-           "mppi_destroy", "mppi_set_profiling", "mppi_last_profile", "mppi_update_noalloc", "gpmppi_philox", "gpmppi_control_noise", "gpmppi_last_error",
+           "mppi_destroy", "mppi_set_profiling", "mppi_last_profile", "mppi_device_status", "mppi_update_noalloc", "gpmppi_philox", "gpmppi_control_noise", "gpmppi_mma_selftest", "gpmppi_last_error",
            "gpmppi_version")
 
 
@@ -88,9 +89,11 @@ def load():
         "mppi_destroy": [vp],
         "mppi_set_profiling": [vp, i32],
         "mppi_last_profile": [vp, vp, vp],
+        "mppi_device_status": [vp],
         "mppi_update_noalloc": [vp, vp, vp, vp, vp, i32, i32, ctypes.c_float, vp],
         "gpmppi_philox": [u64, vp, i32, vp, vp],
         "gpmppi_control_noise": [u64, i32, i32, u64, vp, vp, vp],
+        "gpmppi_mma_selftest": [i32, i32, i32, i32, vp, vp, vp],
         "gpmppi_version": [],
     }
     for name, args in sig.items():
@@ -291,6 +294,11 @@ def mppi_last_profile(ctrl: Ctrl):
     return a.value, b.value
 
 
+def mppi_device_status(ctrl: Ctrl):
+    """Raise if a rollout kernel reported a device-side failure (synchronises)."""
+    _check(load().mppi_device_status(ctrl.handle))
+
+
 def mppi_destroy(ctrl: Ctrl):
     if ctrl.handle:
         _check(load().mppi_destroy(ctrl.handle))
@@ -319,3 +327,11 @@ def gpmppi_control_noise(seed: int, K: int, T: int, it: int, sigma, eps, stream=
     sg = (ctypes.c_float * 2)(float(sigma[0]), float(sigma[1]))
     _check(load().gpmppi_control_noise(int(seed) & 0xFFFFFFFFFFFFFFFF, K, T, int(it), sg,
                                        _dptr(eps, numel=2 * K * T, name="eps"), _stream(stream)))
+
+
+def gpmppi_mma_selftest(fmt: int, A, B, D, variant: int = 0):
+    """D = A B^T through the library's tcgen05 path (A: 128 x K, B: N x K 16-bit
+    tensors viewed as int16/uint16, D: 128 x N float32)."""
+    N, K = B.shape
+    _check(load().gpmppi_mma_selftest(fmt, N, K, variant, _dptr(A, name="A"), _dptr(B, name="B"),
+                                      _dptr(D, numel=128 * N, name="D")))

@@ -104,6 +104,11 @@ struct gpmppi_ctrl_s {
     float* partial = nullptr;     // n_upd x T x 2
     unsigned int* counter = nullptr;
     float* nom_sxy = nullptr;     // T x 3
+    unsigned int* err = nullptr;  // device status word written by the rollout
+    int stages = 2;               // per-warp TMA pipeline depth
+    CUtensorMap tmW;              // TMA map over the GP's W
+    MmaArgs mm{};                 // tensor-core tiles (split precisions)
+    int fmt = -1;                 // 0 = FP16, 1 = BF16 split, -1 = FP32 path
     bool profiling = false;
     bool profiled = false;
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
@@ -120,6 +125,10 @@ void free_gp(gpmppi_gp h) {
     cudaFree(g.Linv64[0]);
     cudaFree(g.alpha64[0]);
     cudaFree(g.alpha64[1]);
+    for (int f = 0; f < 2; ++f) {
+        cudaFree(g.mma_hi[f]);
+        cudaFree(g.mma_lo[f]);
+    }
     if (!g.shared) {
         cudaFree(g.Xs[1]);
         cudaFree(g.W[1]);
@@ -139,6 +148,7 @@ void free_ctrl(gpmppi_ctrl c) {
     cudaFree(c->partial);
     cudaFree(c->counter);
     cudaFree(c->nom_sxy);
+    cudaFree(c->err);
     for (cudaEvent_t e : c->ev)
         if (e) cudaEventDestroy(e);
     if (c->gp && c->gp->magic == kGpMagic) c->gp->g.n_controllers--;
@@ -171,7 +181,8 @@ int validate_params(const gpmppi_params& p) {
         return fail(GPMPPI_ERR_UNSUPPORTED, "params: goal terms (beta[2], beta[3]) are not modelled");
     if (p.variance_mode != GPMPPI_VAR_PER_SAMPLE && p.variance_mode != GPMPPI_VAR_NOMINAL)
         return bad("unknown variance_mode");
-    if (p.precision != GPMPPI_FP32 && p.precision != GPMPPI_BF16_SPLIT) return bad("unknown precision");
+    if (p.precision != GPMPPI_FP32 && p.precision != GPMPPI_BF16_SPLIT && p.precision != GPMPPI_FP16_SPLIT)
+        return bad("unknown precision");
     return GPMPPI_OK;
 }
 
@@ -209,6 +220,8 @@ RolloutArgs make_rollout_args(gpmppi_ctrl c, const float* state, const float* U)
     a.O = c->O;
     a.S = c->S;
     a.mt = c->mt;
+    a.stages = c->stages;
+    a.err = c->err;
     a.sf2 = g.sf2[0];
     for (int i = 0; i < 5; ++i) a.x0[i] = state[i];
     for (int d = 0; d < 4; ++d) a.zscale[d] = g.zscale[0][d];
@@ -346,8 +359,6 @@ int mppi_create(const gpmppi_params* p, const float* obstacles, int32_t O, const
         if (!valid_gp(gp)) return fail(GPMPPI_ERR_INVALID_ARG, "mppi_create: invalid GP handle");
         int rc = validate_params(*p);
         if (rc) return rc;
-        if (p->precision == GPMPPI_BF16_SPLIT)
-            return fail(GPMPPI_ERR_UNSUPPORTED, "mppi_create: BF16 split precision is not built");
         if (!gp->g.shared)
             return fail(GPMPPI_ERR_UNSUPPORTED,
                         "mppi_create: the two GP outputs must share hyper-parameters");
@@ -370,8 +381,8 @@ int mppi_create(const gpmppi_params* p, const float* obstacles, int32_t O, const
         int nsm = 0, smem_optin = 0;
         GPM_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
         GPM_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-        if (rollout_fp32_smem_bytes(gp->g.Np, mtp) > smem_optin)
-            return fail(GPMPPI_ERR_UNSUPPORTED, "mppi_create: GP too large for shared memory");
+        const int stages = rollout_fp32_stages(gp->g.Np, smem_optin);
+        if (stages == 0) return fail(GPMPPI_ERR_UNSUPPORTED, "mppi_create: GP too large for shared memory");
 
         gpmppi_ctrl c = new (std::nothrow) gpmppi_ctrl_s;
         if (!c) return fail(GPMPPI_ERR_OOM, "mppi_create: host allocation failed");
@@ -380,6 +391,8 @@ int mppi_create(const gpmppi_params* p, const float* obstacles, int32_t O, const
         c->device = dev;
         c->O = O;
         c->P = P;
+        c->stages = stages;
+        std::memset(&c->tmW, 0, sizeof(c->tmW));
         c->S = (P > 1) ? (P - 1) : 1;
         int mt = (p->K + nsm - 1) / nsm;
         if (const char* env = std::getenv("GPMPPI_SAMPLES_PER_CTA")) mt = std::atoi(env);
@@ -416,7 +429,8 @@ int mppi_create(const gpmppi_params* p, const float* obstacles, int32_t O, const
             (rc = alloc((void**)&c->u_tilde, sizeof(float2) * K * T)) ||
             (rc = alloc((void**)&c->partial, sizeof(float) * 2 * T * c->n_upd)) ||
             (rc = alloc((void**)&c->counter, sizeof(unsigned int))) ||
-            (rc = alloc((void**)&c->nom_sxy, sizeof(float) * 3 * T))) {
+            (rc = alloc((void**)&c->nom_sxy, sizeof(float) * 3 * T)) ||
+            (rc = alloc((void**)&c->err, sizeof(unsigned int)))) {
             free_ctrl(c);
             return rc;
         }
@@ -427,10 +441,33 @@ int mppi_create(const gpmppi_params* p, const float* obstacles, int32_t O, const
         if (e == cudaSuccess) e = cudaMemcpy(c->seg_il2, il2.data(), sizeof(float) * c->S, cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemset(c->counter, 0, sizeof(unsigned int));
         if (e == cudaSuccess) e = cudaMemset(c->nom_sxy, 0, sizeof(float) * 3 * T);
+        if (e == cudaSuccess) e = cudaMemset(c->err, 0, sizeof(unsigned int));
         if (e == cudaSuccess) e = cudaDeviceSynchronize();
         if (e != cudaSuccess) {
             free_ctrl(c);
             return cuda_fail(e, "mppi_create: upload");
+        }
+        if (gp->g.Np > 0 && (rc = make_w_tensor_map(&c->tmW, gp->g.W[0], gp->g.Np))) {
+            free_ctrl(c);
+            return rc;
+        }
+        if (p->precision != GPMPPI_FP32) {
+            c->fmt = (p->precision == GPMPPI_FP16_SPLIT) ? 0 : 1;
+            if (rollout_mma_smem_bytes() > smem_optin) {
+                free_ctrl(c);
+                return fail(GPMPPI_ERR_UNSUPPORTED, "mppi_create: tensor-core rollout does not fit shared memory");
+            }
+            if ((rc = build_mma_tiles(gp->g, c->fmt))) {
+                free_ctrl(c);
+                return rc;
+            }
+            const GpDevice& g = gp->g;
+            c->mm.Bhi = g.mma_hi[c->fmt];
+            c->mm.Blo = g.mma_lo[c->fmt];
+            c->mm.nblocks = g.NpM / 64;
+            c->mm.nchunks = g.NpM / 32;
+            const double r = (double)g.sf2[0] / (g.mma_cB > 0.0f ? (double)g.mma_cB : 1.0);
+            c->mm.qscale = (float)(r * r);
         }
         *out = c;
         return GPMPPI_OK;
@@ -454,7 +491,9 @@ int mppi_step(gpmppi_ctrl c, const float state[5], const float* U_nom, float* U_
     RolloutArgs a = make_rollout_args(c, state, U_nom);
     if (costs) a.costs = costs;
     if (c->profiling) GPM_CUDA(cudaEventRecord(c->ev[0], st));
-    if ((rc = launch_rollout_fp32(a, false, st))) return rc;
+    rc = (c->fmt < 0) ? launch_rollout_fp32(a, &c->tmW, false, st)
+                      : launch_rollout_mma(a, c->mm, c->fmt, false, st);
+    if (rc) return rc;
     if (c->profiling) GPM_CUDA(cudaEventRecord(c->ev[1], st));
     UpdateArgs u;
     u.costs = a.costs;
@@ -499,7 +538,8 @@ int mppi_rollout_trace(gpmppi_ctrl c, const float state[5], const float* U_nom, 
     a.tr_sig = sigma;
     a.tr_stage = stage;
     a.tr_margin = margins;
-    return launch_rollout_fp32(a, true, (cudaStream_t)stream);
+    if (c->fmt >= 0) return launch_rollout_mma(a, c->mm, c->fmt, true, (cudaStream_t)stream);
+    return launch_rollout_fp32(a, &c->tmW, true, (cudaStream_t)stream);
 }
 
 int mppi_set_iteration(gpmppi_ctrl c, uint64_t it) {
@@ -545,6 +585,18 @@ int mppi_last_profile(gpmppi_ctrl c, float* rollout_ms, float* update_ms) {
     return GPMPPI_OK;
 }
 
+int mppi_device_status(gpmppi_ctrl c) {
+    if (!valid_ctrl(c)) return fail(GPMPPI_ERR_INVALID_ARG, "mppi_device_status: invalid handle");
+    int rc;
+    if ((rc = check_ctrl_device(c))) return rc;
+    GPM_CUDA(cudaDeviceSynchronize());
+    unsigned int word = 0;
+    GPM_CUDA(cudaMemcpy(&word, c->err, sizeof(word), cudaMemcpyDeviceToHost));
+    if (word == 0) return GPMPPI_OK;
+    GPM_CUDA(cudaMemset(c->err, 0, sizeof(unsigned int)));
+    return fail(GPMPPI_ERR_TIMEOUT, "a rollout kernel gave up waiting for a tile copy");
+}
+
 int mppi_destroy(gpmppi_ctrl c) {
     if (!c || c->magic != kCtrlMagic) return fail(GPMPPI_ERR_INVALID_ARG, "mppi_destroy: invalid handle");
     cudaDeviceSynchronize();
@@ -572,6 +624,38 @@ int gpmppi_control_noise(uint64_t seed, int32_t K, int32_t T, uint64_t it, const
     if (reinterpret_cast<uintptr_t>(eps) & 7u)
         return fail(GPMPPI_ERR_INVALID_ARG, "gpmppi_control_noise: eps must be 8-byte aligned");
     return launch_noise(seed, K, T, it, sigma[0], sigma[1], eps, (cudaStream_t)stream);
+}
+
+int gpmppi_mma_selftest(int32_t fmt, int32_t N, int32_t K, int32_t variant, const uint16_t* A,
+                        const uint16_t* B, float* D) {
+    if (fmt != 0 && fmt != 1) return fail(GPMPPI_ERR_INVALID_ARG, "gpmppi_mma_selftest: fmt must be 0 or 1");
+    if (N != 64 && N != 128 && N != 256) return fail(GPMPPI_ERR_INVALID_ARG, "gpmppi_mma_selftest: N must be 64, 128 or 256");
+    if (K != 16 && K != 32 && K != 48 && K != 64) return fail(GPMPPI_ERR_INVALID_ARG, "gpmppi_mma_selftest: K must be 16, 32, 48 or 64");
+    if (variant != 0 && variant != 1) return fail(GPMPPI_ERR_INVALID_ARG, "gpmppi_mma_selftest: variant must be 0 or 1");
+    if (variant == 1 && N > 128) return fail(GPMPPI_ERR_INVALID_ARG, "gpmppi_mma_selftest: variant 1 needs N <= 128");
+    int rc;
+    if ((rc = check_dev_ptr(A, "gpmppi_mma_selftest: A", false))) return rc;
+    if ((rc = check_dev_ptr(B, "gpmppi_mma_selftest: B", false))) return rc;
+    if ((rc = check_dev_ptr(D, "gpmppi_mma_selftest: D", false))) return rc;
+    if ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B)) & 15u)
+        return fail(GPMPPI_ERR_INVALID_ARG, "gpmppi_mma_selftest: A and B must be 16-byte aligned");
+    unsigned int* err = nullptr;
+    GPM_CUDA(cudaMalloc(&err, sizeof(unsigned int)));
+    cudaError_t e = cudaMemset(err, 0, sizeof(unsigned int));
+    if (e == cudaSuccess) {
+        rc = launch_mma_selftest(fmt, N, K, variant, A, B, D, err, nullptr);
+        if (rc) {
+            cudaFree(err);
+            return rc;
+        }
+        e = cudaDeviceSynchronize();
+    }
+    unsigned int word = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&word, err, sizeof(word), cudaMemcpyDeviceToHost);
+    cudaFree(err);
+    if (e != cudaSuccess) return cuda_fail(e, "gpmppi_mma_selftest");
+    if (word) return fail(GPMPPI_ERR_TIMEOUT, "gpmppi_mma_selftest: MMA completion did not arrive");
+    return GPMPPI_OK;
 }
 
 }  // extern "C"

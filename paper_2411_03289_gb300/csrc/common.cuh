@@ -5,6 +5,7 @@
 // rollout, the update and the debug entry points see bit-identical draws.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -71,6 +72,15 @@ __device__ __forceinline__ float2 control_eps(uint32_t k, uint32_t s, uint32_t i
     return make_float2(sig_v * z.x, sig_w * z.y);
 }
 
+// Compensated (Neumaier) accumulation s += x with running correction c: the
+// GP mean is a long sum of terms k*_j alpha_j of both signs that largely
+// cancel, where plain FP32 accumulation loses digits with the length of the sum.
+__device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
+    const float t = s + x;
+    c += (fabsf(s) >= fabsf(x)) ? ((s - t) + x) : ((x - t) + s);
+    s = t;
+}
+
 // ---------------------------------------------------------------------------
 // error plumbing (host)
 // ---------------------------------------------------------------------------
@@ -89,7 +99,7 @@ int cuda_fail(cudaError_t e, const char* what);
 // ---------------------------------------------------------------------------
 struct GpDevice {
     int N = 0;        // training points
-    int Np = 0;       // N rounded up to a multiple of 16 (W is Np x Np)
+    int Np = 0;       // N rounded up to a multiple of 16, at least 64 (W is Np x Np)
     int device = 0;
     bool shared = true;          // both outputs share their hyper-parameters
     float sf2[2] = {0, 0};       // signal variances
@@ -103,6 +113,12 @@ struct GpDevice {
     // FP64 factors kept for export: Linv64[o] N x N, alpha64[o] N
     double* Linv64[2] = {nullptr, nullptr};
     double* alpha64[2] = {nullptr, nullptr};
+    // tensor-core tiles of L^-T per 16-bit format (0 = FP16, 1 = BF16), built
+    // on first use by a controller; NpM = N rounded up to 64
+    uint16_t* mma_hi[2] = {nullptr, nullptr};
+    uint16_t* mma_lo[2] = {nullptr, nullptr};
+    float mma_cB = 0.0f;
+    int NpM = 0;
     gpmppi_hyper hyper[2];
     int n_controllers = 0;
 };
@@ -126,6 +142,8 @@ struct RolloutArgs {
     float* tr_margin;       // K x T x 2
     int K, T, N, Np, O, S;
     int mt;                 // samples per CTA
+    int stages;             // per-warp TMA pipeline depth for the L^-T tiles
+    unsigned int* err;      // device status word (bit 0: a bounded wait gave up)
     float sf2;
     float x0[5];
     float zscale[4];
@@ -139,6 +157,18 @@ struct RolloutArgs {
     float c_coll;           // beta_1 * P_coll
     float r, v_des, sq_chi2, phi_inv;
     uint32_t key0, key1, it0, it1;
+};
+
+// Tensor-core variance contraction: L^-T (scaled by cB, a power of two) split
+// into hi and lo 16-bit parts, stored as 4 KiB tiles of 64 output columns x
+// 32 training points in the slab-major operand layout (tile (b, c) at element
+// offset (b * nchunks + c) * 2048).
+struct MmaArgs {
+    const uint16_t* Bhi;
+    const uint16_t* Blo;
+    int nblocks;            // NpM / 64
+    int nchunks;            // NpM / 32
+    float qscale;           // (sf2 / cB)^2: |L^-1 k*|^2 = qscale * |V'|^2
 };
 
 struct UpdateArgs {
@@ -155,7 +185,12 @@ struct UpdateArgs {
 };
 
 // launchers (defined in the .cu files)
-int launch_rollout_fp32(const RolloutArgs& a, bool trace, cudaStream_t st);
+int launch_rollout_fp32(const RolloutArgs& a, const CUtensorMap* tmap_w, bool trace,
+                        cudaStream_t st);
+// TMA tensor map over W (Np x Np floats) with the box the FP32 rollout reads
+int make_w_tensor_map(CUtensorMap* out, const float* W, int Np);
+// pipeline depth that fits shared memory (0 if none fits)
+int rollout_fp32_stages(int Np, int smem_optin);
 int launch_update(const UpdateArgs& a, int n_cta, cudaStream_t st);
 int launch_gp_predict(const GpDevice& g, const float* Z, int M, float* mean, float* var,
                       cudaStream_t st);
@@ -164,7 +199,12 @@ int launch_philox(uint64_t seed, const uint32_t* ctr, int M, uint32_t* out, cuda
 int launch_noise(uint64_t seed, int K, int T, uint64_t it, float sv, float sw, float* eps,
                  cudaStream_t st);
 int launch_nominal(const RolloutArgs& a, float* sxy_out, cudaStream_t st);
-int rollout_fp32_smem_bytes(int Np, int mtp);
+int rollout_fp32_smem_bytes(int Np, int mtp, int stages);
+int launch_rollout_mma(const RolloutArgs& a, const MmaArgs& mm, int fmt, bool trace, cudaStream_t st);
+int rollout_mma_smem_bytes();
+int build_mma_tiles(GpDevice& g, int fmt);
+int launch_mma_selftest(int fmt, int N, int K, int variant, const uint16_t* A, const uint16_t* B,
+                        float* D, unsigned int* err, cudaStream_t st);
 int rollout_fp32_mtp(int Np);
 
 }  // namespace gpm

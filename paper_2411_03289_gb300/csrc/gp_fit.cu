@@ -7,8 +7,13 @@
 // panel solve, trailing update), followed by a column-block triangular
 // inverse and two matrix-vector products for alpha.  Results are then
 // converted to the FP32 layouts the rollout reads.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include <cmath>
 #include <vector>
+
+#include <cstring>
 
 #include "common.cuh"
 
@@ -264,7 +269,72 @@ __global__ void k_gp_predict(PredArgs p, const float* __restrict__ Z, int M, flo
     }
 }
 
+// max |L^-1| over the lower triangle (positive doubles order like their bits)
+__global__ void k_absmax(const double* __restrict__ Xm, size_t n, unsigned long long* out) {
+    double m = 0.0;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        m = fmax(m, fabs(Xm[i]));
+    atomicMax(out, (unsigned long long)__double_as_longlong(m));
+}
+
+// Tensor-core tiles: element (i = 64 b + r, j = 32 c + 8 sl + e) of cB L^-1 goes
+// to tile (b, c) at sl * 512 + r * 8 + e; hi = round(v), lo = round(v - hi).
+__global__ void k_pack_mma(const double* __restrict__ Xm, int N, int NpM, int fmt, double cB,
+                           uint16_t* __restrict__ hi, uint16_t* __restrict__ lo) {
+    const size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    const size_t total = (size_t)NpM * NpM;
+    if (idx >= total) return;
+    const int nch = NpM / 32;
+    const size_t tile = idx / 2048;
+    const int w = (int)(idx % 2048);
+    const int b = (int)(tile / nch), c = (int)(tile % nch);
+    const int sl = w / 512, r = (w / 8) % 64, e = w % 8;
+    const int i = 64 * b + r, j = 32 * c + 8 * sl + e;
+    double v = 0.0;
+    if (i < N && j < N && j <= i) v = cB * Xm[(size_t)i * N + j];
+    if (fmt == 0) {
+        const __half h = __double2half(v);
+        hi[idx] = __half_as_ushort(h);
+        lo[idx] = __half_as_ushort(__double2half(v - (double)__half2float(h)));
+    } else {
+        const __nv_bfloat16 h = __double2bfloat16(v);
+        hi[idx] = __bfloat16_as_ushort(h);
+        lo[idx] = __bfloat16_as_ushort(__double2bfloat16(v - (double)__bfloat162float(h)));
+    }
+}
+
 }  // namespace
+
+int build_mma_tiles(GpDevice& g, int fmt) {
+    if (g.mma_hi[fmt] || g.N == 0) return GPMPPI_OK;
+    const int N = g.N;
+    g.NpM = ((N + 63) / 64) * 64;
+    if (g.mma_cB == 0.0f) {
+        unsigned long long* d = nullptr;
+        GPM_CUDA(cudaMalloc(&d, sizeof(unsigned long long)));
+        cudaError_t e = cudaMemset(d, 0, sizeof(unsigned long long));
+        if (e == cudaSuccess) {
+            k_absmax<<<256, 256>>>(g.Linv64[0], (size_t)N * N, d);
+            e = cudaGetLastError();
+        }
+        unsigned long long bits = 0;
+        if (e == cudaSuccess) e = cudaMemcpy(&bits, d, sizeof(bits), cudaMemcpyDeviceToHost);
+        cudaFree(d);
+        if (e != cudaSuccess) return cuda_fail(e, "build_mma_tiles: absmax");
+        double mx = 0.0;
+        std::memcpy(&mx, &bits, sizeof(mx));
+        // largest power of two with cB * max|L^-1| <= 2^14 (16-bit range, room for the sums)
+        g.mma_cB = (float)std::ldexp(1.0, (int)std::floor(std::log2(16384.0 / (mx > 0 ? mx : 1.0))));
+    }
+    const size_t n = (size_t)g.NpM * g.NpM;
+    GPM_CUDA(cudaMalloc(&g.mma_hi[fmt], n * sizeof(uint16_t)));
+    GPM_CUDA(cudaMalloc(&g.mma_lo[fmt], n * sizeof(uint16_t)));
+    k_pack_mma<<<(unsigned)((n + 255) / 256), 256>>>(g.Linv64[0], N, g.NpM, fmt, (double)g.mma_cB,
+                                                      g.mma_hi[fmt], g.mma_lo[fmt]);
+    GPM_CUDA(cudaGetLastError());
+    GPM_CUDA(cudaDeviceSynchronize());
+    return GPMPPI_OK;
+}
 
 int launch_gp_predict(const GpDevice& g, const float* Z, int M, float* mean, float* var,
                       cudaStream_t st) {
@@ -291,7 +361,10 @@ int launch_gp_predict(const GpDevice& g, const float* Z, int M, float* mean, flo
 // Fit both outputs.  X (N x 4) and Y (N x 2) are host arrays; g.hyper is set.
 int gp_fit_device(GpDevice& g, const double* X, const double* Y, int N, cudaStream_t st) {
     g.N = N;
-    g.Np = ((N + 15) / 16) * 16;
+    // rows of W padded to a multiple of 16, at least 64 so that every TMA box
+    // of the rollout fits inside the tensor; N = 0 has no W at all
+    g.Np = (N > 0) ? ((N + 15) / 16) * 16 : 0;
+    if (g.Np > 0 && g.Np < 64) g.Np = 64;
     const double log2e = 1.4426950408889634;
     for (int o = 0; o < 2; ++o) {
         g.sf2[o] = (float)g.hyper[o].signal_var;

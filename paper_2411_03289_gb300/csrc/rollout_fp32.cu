@@ -6,13 +6,19 @@
 //   P2  (all)  k*_j = sf2 exp(-|z - x_j|^2 / 2l^2) into shared memory, and the
 //              mean partials k* . alpha (Eq. 3)
 //   P3  (all)  V = K* L^-T as a register-tiled triangular product; each thread
-//              squares and sums its tile, giving partial |L^-1 k*|^2
+//              squares and sums its tile, giving partial |L^-1 k*|^2.  Every
+//              warp streams the two column tiles of L^-T it needs through its
+//              own ring of shared-memory stages filled by TMA tensor copies
+//              (cp.async.bulk.tensor, completion on an mbarrier), so the FMA
+//              loop reads shared memory while later rows are in flight
 //   P4  (warp 0) GP mean / variance, mean dynamics (Eq. 6, 10), covariance
 //              A Sigma A^T + diag(0,0,0,s,s) (Eq. 10), obstacle chance
 //              constraint (Eq. 15-16), variance and speed terms (Eq. 11-12)
 //   P5  (all)  distance to the lane polyline, split over segments
 //   P6  (warp 0) lane deviation and tightened lane indicator (Eq. 11, 13-14)
 // The triangular product dominates: N(N+1)/2 FMAs per sample-step.
+#include <cudaTypedefs.h>
+
 #include <cfloat>
 
 #include "common.cuh"
@@ -27,6 +33,85 @@ __device__ __forceinline__ float4 ldg4(const float* p) {
     return __ldg(reinterpret_cast<const float4*>(p));
 }
 
+// ---- TMA / mbarrier primitives (PTX) ---------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for a phase with a time limit; on expiry record the error and report
+// failure (the caller then stops waiting for further copies).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint64_t limit_ns,
+                                                  unsigned int* err) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    while (!mbar_try_wait(bar, parity)) {
+        if (global_ns() - t0 > limit_ns) {
+            atomicOr(err, 1u);
+            return false;
+        }
+    }
+    return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* tm, int x, int y,
+                                            uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+constexpr uint64_t kWaitLimitNs = 2000000000ull;   // 2 s per copy: only a broken copy waits this long
+
+// Geometry of the L^-T tiles: a warp owns 32 consecutive (sample-group, pair)
+// items, i.e. PPW = 32 / NMG pairs; its A tile covers columns [8 p0, 8 p0 + 8 PPW)
+// and its B tile columns [Np - 8 (p0 + PPW), Np - 8 p0), R rows per stage.
+template <int MTP>
+struct Tile {
+    static constexpr int NMG = MTP / 4;
+    static constexpr int PPW = 32 / NMG;
+    static constexpr int TW = 8 * PPW;                 // tile width (floats)
+    static constexpr int R = (MTP == 8) ? 4 : 8;       // rows per stage
+    static constexpr int BYTES = TW * R * 4;           // one tile
+};
+
 template <int MTP>
 struct Smem {
     // byte offsets inside the dynamic shared buffer
@@ -36,11 +121,17 @@ struct Smem {
     static __host__ __device__ int epart(int Np) { return mpart(Np) + THREADS * 8; }
     static __host__ __device__ int zq(int Np) { return epart(Np) + THREADS * 4; }
     static __host__ __device__ int pos(int Np) { return zq(Np) + MTP * 16; }
-    static __host__ __device__ int total(int Np) { return pos(Np) + MTP * 8; }
+    static __host__ __device__ int tiles(int Np) { return ((pos(Np) + MTP * 8 + 1023) / 1024) * 1024; }
+    // per warp and stage: the A tile then the B tile
+    static __host__ __device__ int bars(int Np, int stages) {
+        return tiles(Np) + WARPS * stages * 2 * Tile<MTP>::BYTES;
+    }
+    static __host__ __device__ int total(int Np, int stages) { return bars(Np, stages) + WARPS * stages * 8; }
 };
 
 template <int MTP, bool TRACE>
-__global__ void __launch_bounds__(THREADS, 1) k_rollout_fp32(const RolloutArgs a) {
+__global__ void __launch_bounds__(THREADS, 1)
+    k_rollout_fp32(const RolloutArgs a, const __grid_constant__ CUtensorMap tmW) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int Np = a.Np;
     float* Ks = reinterpret_cast<float*>(smem_raw + Smem<MTP>::ks(Np));
@@ -49,6 +140,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_fp32(const RolloutArgs a
     float* epart = reinterpret_cast<float*>(smem_raw + Smem<MTP>::epart(Np));
     float4* zq = reinterpret_cast<float4*>(smem_raw + Smem<MTP>::zq(Np));
     float2* pos = reinterpret_cast<float2*>(smem_raw + Smem<MTP>::pos(Np));
+    unsigned char* tiles = smem_raw + Smem<MTP>::tiles(Np);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + Smem<MTP>::bars(Np, a.stages));
 
     constexpr int SUB = 32 / MTP;          // lanes sharing one sample in P2 / P5
     constexpr int NMG = MTP / 4;           // 4-sample groups in P3
@@ -69,6 +162,19 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_fp32(const RolloutArgs a
     float cost = 0.0f, disc = 1.0f, stage = 0.0f, rbar = 0.0f, omargin = FLT_MAX;
     float2 ut = make_float2(0.f, 0.f);
 
+    // per-warp tile pipeline: S stages, one full-barrier each
+    using TL = Tile<MTP>;
+    const int S = a.stages;
+    uint64_t* wbar = bars + warp * S;
+    unsigned char* wtile = tiles + (size_t)warp * S * 2 * TL::BYTES;
+    if (lane == 0)
+        for (int st = 0; st < S; ++st) mbar_init(wbar + st, 1);
+    fence_mbar_init();
+    __syncthreads();
+    uint32_t nrun = 0;          // tile stages consumed by this warp so far
+    uint32_t nissued = 0;       // tile stages requested by this warp (lane 0)
+    bool tma_ok = true;         // warp-uniform; false once a copy failed to arrive in time
+
     for (int k = 0; k < a.T; ++k) {
         // ---------------- P1: noise, clamp, query --------------------------
         if (owner) {
@@ -86,7 +192,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_fp32(const RolloutArgs a
         {
             const int m = lane % MTP;
             const float4 z = zq[m];
-            float mv = 0.0f, mw = 0.0f;
+            float mv = 0.0f, mw = 0.0f, cv = 0.0f, cw = 0.0f;
             for (int j = warp * SUB + lane / MTP; j < Np; j += THREADS / MTP) {
                 float kv = 0.0f;
                 if (j < a.N) {
@@ -94,25 +200,40 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_fp32(const RolloutArgs a
                     const float e0 = z.x - x.x, e1 = z.y - x.y, e2 = z.z - x.z, e3 = z.w - x.w;
                     kv = a.sf2 * exp2f(-(e0 * e0 + e1 * e1 + e2 * e2 + e3 * e3));
                     const float2 al = __ldg(reinterpret_cast<const float2*>(a.alpha) + j);
-                    mv = fmaf(kv, al.x, mv);
-                    mw = fmaf(kv, al.y, mw);
+                    kahan_add(mv, cv, kv * al.x);
+                    kahan_add(mw, cw, kv * al.y);
                 }
                 Ks[j * MTP + m] = kv;
             }
-            mpart[tid] = make_float2(mv, mw);
+            mpart[tid] = make_float2(mv + cv, mw + cw);
         }
         __syncthreads();
 
         // ---------------- P3: |L^-1 k*|^2 by a triangular product ----------
-        for (int it = tid; it < items; it += THREADS) {
-            const int mg = it % NMG;
-            const int p = it / NMG;
-            const int colA = 8 * p;
-            const int colB = Np - 8 - 8 * p;
-            // warp-uniform trip counts: extra rows of W are zero (upper part)
-            const unsigned am = __activemask();
-            const int endA = __reduce_max_sync(am, colA + 8);
-            const int endB = __reduce_max_sync(am, colB + 8);
+        for (int g = warp; g * 32 < items; g += WARPS) {
+            const int mg = lane % NMG;
+            const int pl = lane / NMG;
+            const int p0 = g * TL::PPW;
+            const int p = p0 + pl;
+            const int last = min(TL::PPW, npairs - p0);    // pairs in this group
+            const int endA = 8 * (p0 + last);                // rows holding A coefficients
+            const int endB = Np - 8 * p0;                    // rows holding B coefficients
+            const int xA = 8 * p0;
+            const int xB = Np - 8 * (p0 + TL::PPW);          // may be < 0 for tiny N: zero fill
+            const int nchA = endA / TL::R;                   // endA, endB are multiples of 8
+            const int nch = endB / TL::R;
+            auto issue = [&](int c) {
+                const uint32_t n = nrun + (uint32_t)c;
+                const int st = (int)(n % (uint32_t)S);
+                unsigned char* base = wtile + (size_t)st * 2 * TL::BYTES;
+                const bool withA = c < nchA;
+                ++nissued;
+                mbar_expect_tx(wbar + st, (withA ? 2u : 1u) * (uint32_t)TL::BYTES);
+                if (withA) tma_load_2d(base, &tmW, xA, c * TL::R, wbar + st);
+                tma_load_2d(base + TL::BYTES, &tmW, xB, c * TL::R, wbar + st);
+            };
+            if (lane == 0 && tma_ok)
+                for (int c = 0; c < min(S, nch); ++c) issue(c);
             float accA[4][8], accB[4][8];
 #pragma unroll
             for (int r = 0; r < 4; ++r)
@@ -122,44 +243,69 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_fp32(const RolloutArgs a
                     accB[r][c] = 0.0f;
                 }
             const float* kp = Ks + 4 * mg;
-            const float* wA = a.W + colA;
-            const float* wB = a.W + colB;
-#pragma unroll 2
-            for (int j = 0; j < endA; ++j) {
-                const float4 kv = *reinterpret_cast<const float4*>(kp + j * MTP);
-                const float4 a0 = ldg4(wA + (size_t)j * Np), a1 = ldg4(wA + (size_t)j * Np + 4);
-                const float4 b0 = ldg4(wB + (size_t)j * Np), b1 = ldg4(wB + (size_t)j * Np + 4);
-                const float kr[4] = {kv.x, kv.y, kv.z, kv.w};
-                const float wa[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-                const float wb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+            const int offA = 8 * pl;
+            const int offB = 8 * (TL::PPW - 1 - pl);
+            for (int c = 0; c < nch; ++c) {
+                const uint32_t n = nrun + (uint32_t)c;
+                const int st = (int)(n % (uint32_t)S);
+                bool ok = tma_ok;
+                if (ok) ok = mbar_wait_bounded(wbar + st, (n / (uint32_t)S) & 1u, kWaitLimitNs, a.err);
+                tma_ok = __all_sync(0xffffffffu, ok);
+                const float* tA = reinterpret_cast<const float*>(wtile + (size_t)st * 2 * TL::BYTES);
+                const float* tB = tA + TL::TW * TL::R;
+                const int j0 = c * TL::R;
+                if (c < nchA) {
 #pragma unroll
-                for (int r = 0; r < 4; ++r)
+                    for (int r = 0; r < TL::R; ++r) {
+                        const float4 kv = *reinterpret_cast<const float4*>(kp + (j0 + r) * MTP);
+                        const float4 a0 = *reinterpret_cast<const float4*>(tA + r * TL::TW + offA);
+                        const float4 a1 = *reinterpret_cast<const float4*>(tA + r * TL::TW + offA + 4);
+                        const float4 b0 = *reinterpret_cast<const float4*>(tB + r * TL::TW + offB);
+                        const float4 b1 = *reinterpret_cast<const float4*>(tB + r * TL::TW + offB + 4);
+                        const float kr[4] = {kv.x, kv.y, kv.z, kv.w};
+                        const float wa[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+                        const float wb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+                        for (int rr = 0; rr < 4; ++rr)
+#pragma unroll
+                            for (int cc = 0; cc < 8; ++cc) {
+                                accA[rr][cc] = fmaf(kr[rr], wa[cc], accA[rr][cc]);
+                                accB[rr][cc] = fmaf(kr[rr], wb[cc], accB[rr][cc]);
+                            }
+                    }
+                } else {
+#pragma unroll
+                    for (int r = 0; r < TL::R; ++r) {
+                        const float4 kv = *reinterpret_cast<const float4*>(kp + (j0 + r) * MTP);
+                        const float4 b0 = *reinterpret_cast<const float4*>(tB + r * TL::TW + offB);
+                        const float4 b1 = *reinterpret_cast<const float4*>(tB + r * TL::TW + offB + 4);
+                        const float kr[4] = {kv.x, kv.y, kv.z, kv.w};
+                        const float wb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+                        for (int rr = 0; rr < 4; ++rr)
+#pragma unroll
+                            for (int cc = 0; cc < 8; ++cc)
+                                accB[rr][cc] = fmaf(kr[rr], wb[cc], accB[rr][cc]);
+                    }
+                }
+                __syncwarp();
+                if (lane == 0 && tma_ok && c + S < nch) {
+                    fence_proxy_async_smem();     // our reads of this stage precede the refill
+                    issue(c + S);
+                }
+            }
+            nrun += (uint32_t)nch;
+            if (p < npairs) {
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    float q = 0.0f;
 #pragma unroll
                     for (int c = 0; c < 8; ++c) {
-                        accA[r][c] = fmaf(kr[r], wa[c], accA[r][c]);
-                        accB[r][c] = fmaf(kr[r], wb[c], accB[r][c]);
+                        q = fmaf(accA[r][c], accA[r][c], q);
+                        q = fmaf(accB[r][c], accB[r][c], q);
                     }
-            }
-#pragma unroll 4
-            for (int j = endA; j < endB; ++j) {
-                const float4 kv = *reinterpret_cast<const float4*>(kp + j * MTP);
-                const float4 b0 = ldg4(wB + (size_t)j * Np), b1 = ldg4(wB + (size_t)j * Np + 4);
-                const float kr[4] = {kv.x, kv.y, kv.z, kv.w};
-                const float wb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
-#pragma unroll
-                for (int r = 0; r < 4; ++r)
-#pragma unroll
-                    for (int c = 0; c < 8; ++c) accB[r][c] = fmaf(kr[r], wb[c], accB[r][c]);
-            }
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                float q = 0.0f;
-#pragma unroll
-                for (int c = 0; c < 8; ++c) {
-                    q = fmaf(accA[r][c], accA[r][c], q);
-                    q = fmaf(accB[r][c], accB[r][c], q);
+                    qpart[p * MTP + 4 * mg + r] = q;
                 }
-                qpart[p * MTP + 4 * mg + r] = q;
             }
         }
         __syncthreads();
@@ -167,14 +313,16 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_fp32(const RolloutArgs a
         // ---------------- P4: dynamics, covariance, obstacles --------------
         if (owner) {
             const int m = lane;
-            float mv = 0.0f, mw = 0.0f;
+            float mv = 0.0f, mw = 0.0f, cv = 0.0f, cw = 0.0f;
             for (int w = 0; w < WARPS; ++w)
 #pragma unroll
                 for (int u = 0; u < SUB; ++u) {
                     const float2 pm = mpart[w * 32 + u * MTP + m];
-                    mv += pm.x;
-                    mw += pm.y;
+                    kahan_add(mv, cv, pm.x);
+                    kahan_add(mw, cw, pm.y);
                 }
+            mv += cv;
+            mw += cw;
             float q = 0.0f;
             for (int p = 0; p < npairs; ++p) q += qpart[p * MTP + m];
             const float s = fmaxf(0.0f, a.sf2 - q);
@@ -300,16 +448,32 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_fp32(const RolloutArgs a
         }
     }
     if (active && a.costs) a.costs[s_me] = cost;
+    // after a failed copy, give the copies still in flight a bounded time to
+    // land before the CTA's shared memory is released
+    if (!tma_ok && lane == 0) {
+        const uint64_t t0 = global_ns();
+        for (uint32_t n = (nissued > (uint32_t)S ? nissued - (uint32_t)S : 0u); n < nissued; ++n)
+            while (!mbar_try_wait(wbar + n % (uint32_t)S, (n / (uint32_t)S) & 1u) &&
+                   global_ns() - t0 < 200000000ull) {
+            }
+    }
 }
 
 template <int MTP, bool TRACE>
-int launch_t(const RolloutArgs& a, cudaStream_t st) {
-    const int smem = Smem<MTP>::total(a.Np);
+int launch_t(const RolloutArgs& a, const CUtensorMap* tm, cudaStream_t st) {
+    const int smem = Smem<MTP>::total(a.Np, a.stages);
     auto kern = k_rollout_fp32<MTP, TRACE>;
     GPM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     const int grid = (a.K + a.mt - 1) / a.mt;
-    kern<<<grid, THREADS, smem, st>>>(a);
+    kern<<<grid, THREADS, smem, st>>>(a, *tm);
     GPM_CUDA(cudaGetLastError());
+    return GPMPPI_OK;
+}
+
+template <int MTP>
+int tile_box(int* w, int* h) {
+    *w = Tile<MTP>::TW;
+    *h = Tile<MTP>::R;
     return GPMPPI_OK;
 }
 
@@ -321,28 +485,64 @@ int rollout_fp32_mtp(int Np) {
     return 8;
 }
 
-int rollout_fp32_smem_bytes(int Np, int mtp) {
+int rollout_fp32_smem_bytes(int Np, int mtp, int stages) {
     switch (mtp) {
-        case 32: return Smem<32>::total(Np);
-        case 16: return Smem<16>::total(Np);
-        default: return Smem<8>::total(Np);
+        case 32: return Smem<32>::total(Np, stages);
+        case 16: return Smem<16>::total(Np, stages);
+        default: return Smem<8>::total(Np, stages);
     }
 }
 
-int launch_rollout_fp32(const RolloutArgs& a, bool trace, cudaStream_t st) {
+int rollout_fp32_stages(int Np, int smem_optin) {
+    const int mtp = rollout_fp32_mtp(Np);
+    for (int s = 4; s >= 2; --s)
+        if (rollout_fp32_smem_bytes(Np, mtp, s) <= smem_optin) return s;
+    return 0;
+}
+
+int make_w_tensor_map(CUtensorMap* out, const float* W, int Np) {
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        GPM_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                  cudaEnableDefault, &q));
+        if (q != cudaDriverEntryPointSuccess || !fn)
+            return fail(GPMPPI_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    int bw = 0, bh = 0;
+    switch (rollout_fp32_mtp(Np)) {
+        case 32: tile_box<32>(&bw, &bh); break;
+        case 16: tile_box<16>(&bw, &bh); break;
+        default: tile_box<8>(&bw, &bh); break;
+    }
+    const cuuint64_t dims[2] = {(cuuint64_t)Np, (cuuint64_t)Np};
+    const cuuint64_t strides[1] = {(cuuint64_t)Np * sizeof(float)};
+    const cuuint32_t box[2] = {(cuuint32_t)bw, (cuuint32_t)bh};
+    const cuuint32_t estr[2] = {1, 1};
+    CUresult r = encode(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(W), dims, strides,
+                        box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(GPMPPI_ERR_CUDA, "cuTensorMapEncodeTiled failed for L^-T");
+    return GPMPPI_OK;
+}
+
+int launch_rollout_fp32(const RolloutArgs& a, const CUtensorMap* tm, bool trace, cudaStream_t st) {
     const int mtp = rollout_fp32_mtp(a.Np);
     if (a.mt < 1 || a.mt > mtp) return fail(GPMPPI_ERR_INVALID_ARG, "rollout: bad samples per CTA");
+    if (a.stages < 2 || a.stages > 4) return fail(GPMPPI_ERR_INVALID_ARG, "rollout: bad pipeline depth");
     if (trace) {
         switch (mtp) {
-            case 32: return launch_t<32, true>(a, st);
-            case 16: return launch_t<16, true>(a, st);
-            default: return launch_t<8, true>(a, st);
+            case 32: return launch_t<32, true>(a, tm, st);
+            case 16: return launch_t<16, true>(a, tm, st);
+            default: return launch_t<8, true>(a, tm, st);
         }
     }
     switch (mtp) {
-        case 32: return launch_t<32, false>(a, st);
-        case 16: return launch_t<16, false>(a, st);
-        default: return launch_t<8, false>(a, st);
+        case 32: return launch_t<32, false>(a, tm, st);
+        case 16: return launch_t<16, false>(a, tm, st);
+        default: return launch_t<8, false>(a, tm, st);
     }
 }
 

@@ -28,6 +28,12 @@ TOL_TRAJ = 1e-4
 TOL_COST = 1e-4
 TOL_U = 1e-4
 TOL_W = 1e-4
+# Margins e - r + sqrt(chi2) sqrt(lambda_max(Sigma_XY)) pass covariance errors
+# through a square root: d sqrt(lambda) = d lambda / (2 sqrt(lambda)), a factor
+# of up to ~10 at the covariance scales of these workloads, so margin values
+# are held to 10x the trajectory tolerance; what they decide (indicator bits)
+# is checked exactly outside MARGIN_WINDOW.
+TOL_MARGIN = 1e-3
 MARGIN_WINDOW = 2e-3      # metres
 MAX_FLIPS = 12
 
@@ -51,7 +57,7 @@ def gpu_step(gp, ctrl, sc, state, U, it=None):
     w = torch.empty(sc.params.K, dtype=torch.float32, device=dev)
     c = torch.empty_like(w)
     gp.mppi_step(ctrl, state, Ud, U_new, w, c)
-    torch.cuda.synchronize()
+    gp.mppi_device_status(ctrl)        # no kernel gave up a bounded wait
     return to_np(U_new), to_np(w), to_np(c)
 
 
@@ -68,7 +74,7 @@ def gpu_trace(gp, ctrl, sc, state, U, it=None):
     mg = torch.empty(K, T, 2, device=dev)
     c = torch.empty(K, device=dev)
     gp.mppi_rollout_trace(ctrl, state, Ud, mu, sig, st, mg, c)
-    torch.cuda.synchronize()
+    gp.mppi_device_status(ctrl)
     return dict(mu=to_np(mu), sigma=to_np(sig), stage=to_np(st), margins=to_np(mg), costs=to_np(c))
 
 
@@ -163,19 +169,34 @@ def check_trace(sc, ro, tr, rows=None):
     assert_close(tr["sigma"][rows], sig_ref, TOL_TRAJ, floor=sf2 * P.T * P.dt, what="covariances")
     # margins: continuous quantities
     mg = tr["margins"][rows]
-    assert_close(mg[..., 0], ro["lane_margin"], TOL_TRAJ, what="lane margins")
+    assert_close(mg[..., 0], ro["lane_margin"], TOL_MARGIN, what="lane margins")
     om = ro["obs_margin"]
     if np.all(np.isinf(om)):
         assert np.all(np.isinf(mg[..., 1]))
     else:
-        assert_close(mg[..., 1], om, TOL_TRAJ, what="obstacle margins")
+        assert_close(mg[..., 1], om, TOL_MARGIN, what="obstacle margins")
     # indicator bits agree wherever the oracle's margin is clear of the boundary
     clear_l = np.abs(ro["lane_margin"]) >= MARGIN_WINDOW
     assert np.array_equal((mg[..., 0] > 0)[clear_l], (ro["lane_margin"] > 0)[clear_l])
     clear_o = np.isfinite(om) & (np.abs(om) >= MARGIN_WINDOW)
     assert np.array_equal((mg[..., 1] <= 0)[clear_o], (om <= 0)[clear_o])
     n_amb = int(np.sum(~clear_l) + np.sum(np.isfinite(om) & ~clear_o))
-    return dict(n_ambiguous_stages=n_amb,
+    lm_err = float(np.max(np.abs(mg[..., 0] - ro["lane_margin"]) / (np.abs(ro["lane_margin"]) + 1)))
+    return dict(n_ambiguous_stages=n_amb, err_lane_margin=lm_err,
                 err_mu=float(np.max(np.abs(mu_g - ro["mu"]) / (np.abs(ro["mu"]) + 1))),
                 err_sigma=float(np.max(np.abs(tr["sigma"][rows] - sig_ref)
                                        / (np.abs(sig_ref) + sf2 * P.T * P.dt))))
+
+
+def trace_errors(sc, ro, tr, rows=None):
+    """Max scaled errors per quantity (no assertion): means, covariances,
+    lane margins (with the floors of the parity tolerances)."""
+    rows = np.arange(ro["costs"].shape[0]) if rows is None else np.asarray(rows)
+    sf2 = sc.hyper[0].signal_var
+    P = sc.params
+    sig_ref = sigma_upper(ro["Sigma"])
+    mg = tr["margins"][rows]
+    return dict(
+        err_mu=float(np.max(np.abs(tr["mu"][rows] - ro["mu"]) / (np.abs(ro["mu"]) + 1))),
+        err_sigma=float(np.max(np.abs(tr["sigma"][rows] - sig_ref) / (np.abs(sig_ref) + sf2 * P.T * P.dt))),
+        err_lane_margin=float(np.max(np.abs(mg[..., 0] - ro["lane_margin"]) / (np.abs(ro["lane_margin"]) + 1))))
