@@ -32,8 +32,8 @@ if ROOT not in sys.path:
 METRIC = "rollout sample-steps/s and p50 mppi_step latency vs plain FP32 GPU path"
 WORKLOAD = "cfg2"
 L2_FLUSH_BYTES = 512 << 20
-ROLLOUT_SRC = os.path.join(ROOT, "paper_2411_03289_gb300", "csrc", "rollout_fp32.cu")
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "rollout_fp32_cfg2_ncu.md")
+CSRC = os.path.join(ROOT, "paper_2411_03289_gb300", "csrc")
+PROFILES = os.path.join(ROOT, "profiles")
 
 
 def rollout_flops_per_sample_step(N, O, S):
@@ -141,15 +141,16 @@ class ClockSampler:
 # measured DRAM traffic of the rollout kernel (from the committed ncu summary)
 # ---------------------------------------------------------------------------
 
-def committed_traffic():
-    """Bytes per launch from the ncu summary, if it was taken on the current
-    kernel source (the summary records the source's sha256)."""
+def committed_traffic(kernel="rollout_fp32", workload=WORKLOAD):
+    """DRAM bytes per launch from the committed ncu summary of this kernel and
+    workload, if it was taken on the current kernel source (the summary
+    records the source's sha256); else None."""
     try:
-        txt = open(TRAFFIC_FILE).read()
-        sha = hashlib.sha256(open(ROLLOUT_SRC, "rb").read()).hexdigest()
+        txt = open(os.path.join(PROFILES, f"{kernel}_{workload}_ncu.md")).read()
+        sha = hashlib.sha256(open(os.path.join(CSRC, f"{kernel}.cu"), "rb").read()).hexdigest()
     except OSError:
         return None
-    m_sha = re.search(r"rollout_fp32\.cu sha256:\s*([0-9a-f]{64})", txt)
+    m_sha = re.search(rf"{kernel}\.cu sha256:\s*([0-9a-f]{{64}})", txt)
     m_tr = re.search(r"dram bytes per launch \(full workload\):\s*([0-9.eE+]+)", txt)
     if not m_sha or not m_tr or m_sha.group(1) != sha:
         return None
@@ -237,6 +238,66 @@ def run_reference(args):
 # our arm
 # ---------------------------------------------------------------------------
 
+def timed_steps(gp, ctrl, x0, U, U_new, w, c, flush, stream, steps, warmup, barrier, clocks=None):
+    """W warm-up steps, then `steps` mppi_steps each bracketed by CUDA events on
+    the launch stream, with an L2 flush (untimed) between them."""
+    import torch
+    for _ in range(warmup):
+        gp.mppi_step(ctrl, x0, U, U_new, w, c)
+        flush.fill_(1.0)
+    torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    rollout_ms, update_ms = [], []
+    if clocks is not None:
+        clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter()
+    for i in range(steps):
+        starts[i].record(stream)
+        gp.mppi_step(ctrl, x0, U, U_new, w, c)
+        ends[i].record(stream)
+        r_ms, u_ms = gp.mppi_last_profile(ctrl)
+        rollout_ms.append(r_ms)
+        update_ms.append(u_ms)
+        flush.fill_(float(i))
+    torch.cuda.synchronize()
+    barrier()
+    t_wall = time.perf_counter() - t_wall
+    clk = clocks.stop() if clocks is not None else None
+    gp.mppi_device_status(ctrl)
+    step_ms = [s_.elapsed_time(e_) for s_, e_ in zip(starts, ends)]
+    return step_ms, rollout_ms, update_ms, t_wall, clk
+
+
+def fp32_path(args, gp, S, dev, flush, stream, barrier):
+    """The plain FP32 CUDA-core path on the same workload, for comparison."""
+    import numpy as np
+    import torch
+    sc = S.scenario(args.workload, seed=1, precision=0)
+    g = gp.gp_fit(sc.X, sc.Y, sc.hyper)
+    ctrl = gp.mppi_create(sc.params, sc.obstacles, sc.path, g)
+    U = torch.tensor(sc.U0, dtype=torch.float32, device=dev)
+    U_new = torch.empty_like(U)
+    w = torch.empty(sc.params.K, dtype=torch.float32, device=dev)
+    c = torch.empty_like(w)
+    gp.mppi_set_profiling(ctrl, True)
+    steps = max(10, args.steps // 4)
+    step_ms, rollout_ms, _, _, _ = timed_steps(gp, ctrl, sc.x0.astype(np.float32), U, U_new, w, c, flush,
+                                               stream, steps, args.warmup, barrier)
+    P = sc.params
+    S_seg = max(sc.path.shape[0] - 1, 1)
+    flops = rollout_flops_per_sample_step(sc.N, sc.obstacles.shape[0], S_seg) * P.K * P.T
+    r_avg = sum(rollout_ms) / len(rollout_ms)
+    ach = flops / (r_avg / 1e3) / 1e12
+    return {"value": P.K * P.T * steps / (sum(step_ms) / 1e3), "unit": "sample-steps/s",
+            "p50_ms": statistics.median(step_ms), "steps": steps, "rollout_ms": r_avg,
+            "roofline": {"bound": "alu", "achieved": ach, "peak": fp32_peak_tflops(2070.0),
+                         "unit": "TFLOP/s", "frac": ach / fp32_peak_tflops(2070.0),
+                         "kernel": "k_rollout_fp32", "traffic": committed_traffic("rollout_fp32", args.workload)}}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -271,33 +332,9 @@ def run_ours(args):
             torch.distributed.barrier()
 
     gp.mppi_set_profiling(ctrl, True)
-    for _ in range(args.warmup):
-        gp.mppi_step(ctrl, x0, U, U_new, w, c)
-        flush.fill_(1.0)
-    torch.cuda.synchronize()
-
-    # ---- device-timed region: inputs resident, L2 flushed between steps ----
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    rollout_ms, update_ms = [], []
     clocks = ClockSampler(torch.cuda.current_device())
-    clocks.start()
-    barrier()
-    torch.cuda.synchronize()
-    t_wall = time.perf_counter()
-    for i in range(args.steps):
-        starts[i].record(stream)
-        gp.mppi_step(ctrl, x0, U, U_new, w, c)
-        ends[i].record(stream)
-        r_ms, u_ms = gp.mppi_last_profile(ctrl)
-        rollout_ms.append(r_ms)
-        update_ms.append(u_ms)
-        flush.fill_(float(i))
-    torch.cuda.synchronize()
-    barrier()
-    t_wall = time.perf_counter() - t_wall
-    clk = clocks.stop()
-    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    step_ms, rollout_ms, update_ms, t_wall, clk = timed_steps(gp, ctrl, x0, U, U_new, w, c, flush, stream,
+                                                             args.steps, args.warmup, barrier, clocks)
     tot_ms = sum(step_ms)
     if ws > 1:
         t = torch.tensor([tot_ms], device=dev)
@@ -337,7 +374,7 @@ def run_ours(args):
     flops = rollout_flops_per_sample_step(sc.N, sc.obstacles.shape[0], S_seg) * P.K * P.T
     r_avg = sum(rollout_ms) / len(rollout_ms)
     achieved = flops / (r_avg / 1e3) / 1e12
-    traffic = committed_traffic() if P.precision == 0 else None
+    traffic = committed_traffic("rollout_fp32" if P.precision == 0 else "rollout_mma", args.workload)
     if P.precision == 0:
         roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak_tflops(2070.0), "unit": "TFLOP/s",
                 "traffic": traffic, "kernel": "k_rollout_fp32",
@@ -347,6 +384,9 @@ def run_ours(args):
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "traffic": traffic, "kernel": "k_rollout_mma", "peak_note": note}
     roof["frac"] = roof["achieved"] / roof["peak"]
+    fp32 = None
+    if P.precision != 0 and not args.no_fp32_path:
+        fp32 = fp32_path(args, gp, S, dev, flush, stream, barrier)
     if rank != 0:
         if ws > 1:
             torch.distributed.destroy_process_group()
@@ -355,7 +395,8 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": "sample-steps/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_ms / args.steps,
         "p50_ms": statistics.median(step_ms), "p90_ms": sorted(step_ms)[int(0.9 * (len(step_ms) - 1))],
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {0: "f32", 1: "f32+bf16split", 2: "f32+f16split"}[P.precision],
         "data": "synthetic (seeded GP training set, obstacles and figure-eight path)",
         "config": describe(sc),
         "gpu_launches": 2 * args.steps,
@@ -365,6 +406,8 @@ def run_ours(args):
         "e2e": {"value": units / e2e_s, "unit": "sample-steps/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "clocks": clk,
+        "fp32_path": fp32,
+        "vs_plain_fp32_path": (value / (fp32["value"] * ws)) if fp32 else None,
         "wall_s_timed_region": t_wall,
     }
     print(json.dumps(line), flush=True)
@@ -385,7 +428,9 @@ def main():
                     help="samples per reference (oracle) step")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline leg")
     ap.add_argument("--workload", default=WORKLOAD, help="scenario name (cfg2 is the reported workload)")
-    ap.add_argument("--precision", default="fp32", choices=sorted(PRECISIONS))
+    ap.add_argument("--precision", default="fp16split", choices=sorted(PRECISIONS))
+    ap.add_argument("--no-fp32-path", action="store_true",
+                    help="skip timing the plain FP32 CUDA-core path beside the headline path")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -453,10 +453,6 @@ int mppi_create(const gpmppi_params* p, const float* obstacles, int32_t O, const
         }
         if (p->precision != GPMPPI_FP32) {
             c->fmt = (p->precision == GPMPPI_FP16_SPLIT) ? 0 : 1;
-            if (rollout_mma_smem_bytes() > smem_optin) {
-                free_ctrl(c);
-                return fail(GPMPPI_ERR_UNSUPPORTED, "mppi_create: tensor-core rollout does not fit shared memory");
-            }
             if ((rc = build_mma_tiles(gp->g, c->fmt))) {
                 free_ctrl(c);
                 return rc;
@@ -464,10 +460,21 @@ int mppi_create(const gpmppi_params* p, const float* obstacles, int32_t O, const
             const GpDevice& g = gp->g;
             c->mm.Bhi = g.mma_hi[c->fmt];
             c->mm.Blo = g.mma_lo[c->fmt];
-            c->mm.nblocks = g.NpM / 64;
-            c->mm.nchunks = g.NpM / 32;
+            c->mm.nblocks = g.NpM / 128;
+            c->mm.nchunks = g.NpM / 16;
             const double r = (double)g.sf2[0] / (g.mma_cB > 0.0f ? (double)g.mma_cB : 1.0);
             c->mm.qscale = (float)(r * r);
+            c->mm.stages = rollout_mma_stages(g.NpM, smem_optin);
+            // fewest threads per sample (largest sample tile) that still
+            // gives every SM a CTA; small K falls back to 32 samples per CTA
+            c->mm.rps = 8;
+            if ((p->K + 127) / 128 >= nsm * 4 / 5) c->mm.rps = 2;
+            else if ((p->K + 63) / 64 >= nsm * 4 / 5) c->mm.rps = 4;
+            if (const char* env = std::getenv("GPMPPI_MMA_THREADS_PER_SAMPLE")) c->mm.rps = std::atoi(env);
+            if (c->mm.stages == 0) {
+                free_ctrl(c);
+                return fail(GPMPPI_ERR_UNSUPPORTED, "mppi_create: tensor-core rollout does not fit shared memory");
+            }
         }
         *out = c;
         return GPMPPI_OK;

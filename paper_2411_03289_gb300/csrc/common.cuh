@@ -114,7 +114,7 @@ struct GpDevice {
     double* Linv64[2] = {nullptr, nullptr};
     double* alpha64[2] = {nullptr, nullptr};
     // tensor-core tiles of L^-T per 16-bit format (0 = FP16, 1 = BF16), built
-    // on first use by a controller; NpM = N rounded up to 64
+    // on first use by a controller; NpM = N rounded up to 128
     uint16_t* mma_hi[2] = {nullptr, nullptr};
     uint16_t* mma_lo[2] = {nullptr, nullptr};
     float mma_cB = 0.0f;
@@ -160,15 +160,17 @@ struct RolloutArgs {
 };
 
 // Tensor-core variance contraction: L^-T (scaled by cB, a power of two) split
-// into hi and lo 16-bit parts, stored as 4 KiB tiles of 64 output columns x
-// 32 training points in the slab-major operand layout (tile (b, c) at element
-// offset (b * nchunks + c) * 2048).
+// into hi and lo 16-bit parts, stored as 4 KiB pieces of 128 output columns x
+// 16 training points in the slab-major operand layout, piece (chunk c, block
+// b) at element offset (c * nblocks + b) * 2048.
 struct MmaArgs {
     const uint16_t* Bhi;
     const uint16_t* Blo;
-    int nblocks;            // NpM / 64
-    int nchunks;            // NpM / 32
+    int nblocks;            // NpM / 128
+    int nchunks;            // NpM / 16
     float qscale;           // (sf2 / cB)^2: |L^-1 k*|^2 = qscale * |V'|^2
+    int stages;             // shared-memory pipeline depth (2..4)
+    int rps;                // producer threads per sample (2, 4, 8): 128, 64, 32 samples per CTA
 };
 
 struct UpdateArgs {
@@ -201,7 +203,7 @@ int launch_noise(uint64_t seed, int K, int T, uint64_t it, float sv, float sw, f
 int launch_nominal(const RolloutArgs& a, float* sxy_out, cudaStream_t st);
 int rollout_fp32_smem_bytes(int Np, int mtp, int stages);
 int launch_rollout_mma(const RolloutArgs& a, const MmaArgs& mm, int fmt, bool trace, cudaStream_t st);
-int rollout_mma_smem_bytes();
+int rollout_mma_stages(int NpM, int smem_optin);
 int build_mma_tiles(GpDevice& g, int fmt);
 int launch_mma_selftest(int fmt, int N, int K, int variant, const uint16_t* A, const uint16_t* B,
                         float* D, unsigned int* err, cudaStream_t st);

@@ -277,19 +277,21 @@ __global__ void k_absmax(const double* __restrict__ Xm, size_t n, unsigned long 
     atomicMax(out, (unsigned long long)__double_as_longlong(m));
 }
 
-// Tensor-core tiles: element (i = 64 b + r, j = 32 c + 8 sl + e) of cB L^-1 goes
-// to tile (b, c) at sl * 512 + r * 8 + e; hi = round(v), lo = round(v - hi).
+// Tensor-core tiles: element (i = 128 b + r, j = 16 c + 8 sl + e) of cB L^-1 goes
+// to piece (c, b) at ((c * NB + b) * 2 + sl) * 1024 + r * 8 + e, so one 16-point
+// chunk holds the 4 KiB pieces of all blocks contiguously; hi = round(v),
+// lo = round(v - hi).
 __global__ void k_pack_mma(const double* __restrict__ Xm, int N, int NpM, int fmt, double cB,
                            uint16_t* __restrict__ hi, uint16_t* __restrict__ lo) {
     const size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     const size_t total = (size_t)NpM * NpM;
     if (idx >= total) return;
-    const int nch = NpM / 32;
-    const size_t tile = idx / 2048;
+    const int NB = NpM / 128;
+    const size_t piece = idx / 2048;
     const int w = (int)(idx % 2048);
-    const int b = (int)(tile / nch), c = (int)(tile % nch);
-    const int sl = w / 512, r = (w / 8) % 64, e = w % 8;
-    const int i = 64 * b + r, j = 32 * c + 8 * sl + e;
+    const int c = (int)(piece / NB), b = (int)(piece % NB);
+    const int sl = w / 1024, r = (w / 8) % 128, e = w % 8;
+    const int i = 128 * b + r, j = 16 * c + 8 * sl + e;
     double v = 0.0;
     if (i < N && j < N && j <= i) v = cB * Xm[(size_t)i * N + j];
     if (fmt == 0) {
@@ -308,7 +310,7 @@ __global__ void k_pack_mma(const double* __restrict__ Xm, int N, int NpM, int fm
 int build_mma_tiles(GpDevice& g, int fmt) {
     if (g.mma_hi[fmt] || g.N == 0) return GPMPPI_OK;
     const int N = g.N;
-    g.NpM = ((N + 63) / 64) * 64;
+    g.NpM = ((N + 127) / 128) * 128;
     if (g.mma_cB == 0.0f) {
         unsigned long long* d = nullptr;
         GPM_CUDA(cudaMalloc(&d, sizeof(unsigned long long)));

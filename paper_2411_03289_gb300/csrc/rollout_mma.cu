@@ -30,26 +30,44 @@
 namespace gpm {
 namespace {
 
-constexpr int MT = 128;               // samples per CTA
-constexpr int THREADS = 256;
-constexpr int KC = 32;                // training points per chunk
-constexpr int BLK = 64;               // output columns per MMA block
-constexpr int BLOCKS_PER_PASS = 8;    // 512 TMEM columns
-constexpr int A_PART = MT * KC * 2;                         // 8 KiB
-constexpr int B_TILE = BLK * KC * 2;                        // 4 KiB
-constexpr int STAGE = 2 * A_PART + BLOCKS_PER_PASS * 2 * B_TILE;   // 80 KiB
+constexpr int MT = 128;               // samples per CTA (the MMA M)
+constexpr int NPROD = 256;            // producer threads (warps 0-7): two per sample
+constexpr int THREADS = NPROD + 64;   // + warp 8 (MMA issuer) + warp 9 (tile loader)
+constexpr int KC = 16;                // training points per chunk (one MMA K-step)
+constexpr int BLK = 128;              // output columns per MMA block (MMA N)
+constexpr int BLOCKS_PER_PASS = 4;    // 512 TMEM columns
+constexpr int NSTAGE = 4;             // maximum pipeline depth (3 when the training set is large)
+constexpr int A_PART = MT * KC * 2;                         // 4 KiB
+constexpr int B_PART = BLK * KC * 2;                        // 4 KiB
+constexpr int STAGE = 2 * A_PART + BLOCKS_PER_PASS * 2 * B_PART;   // 40 KiB
 constexpr uint64_t kWaitNs = 2000000000ull;
 
-struct SmemM {
-    static constexpr int bars = 2 * STAGE;              // mma_done[2], bfull[2]
-    static constexpr int tslot = bars + 32;
-    static constexpr int flag = tslot + 4;
-    static constexpr int qh = bars + 64;                // 2 x 128 floats
-    static constexpr int mh = qh + 2 * MT * 4;          // 2 x 128 float2
-    static constexpr int ep = mh + 2 * MT * 8;          // 2 x 128 floats
-    static constexpr int om = ep + 2 * MT * 4;          // 2 x 128 floats
-    static constexpr int total = om + 2 * MT * 4;
+// Shared-memory layout for a given pipeline depth and padded training-set size.
+struct MLayout {
+    int bars, tslot, abort_flag, qh, mh, ep, om, xs, al, total;
 };
+
+__host__ __device__ inline MLayout mma_layout(int nstage, int NpM) {
+    MLayout L;
+    L.bars = nstage * STAGE;                     // a_full, b_full, empty [NSTAGE] + pass_done, tmem_free
+    L.tslot = L.bars + 8 * (3 * NSTAGE + 2);
+    L.abort_flag = L.tslot + 4;
+    L.qh = ((L.abort_flag + 4 + 15) / 16) * 16;  // 2 x 128 floats
+    L.mh = L.qh + 2 * MT * 4;                    // 2 x 128 float2
+    L.ep = L.mh + 2 * MT * 8;                    // 2 x 128 floats
+    L.om = L.ep + 2 * MT * 4;                    // 2 x 128 floats
+    L.xs = ((L.om + 2 * MT * 4 + 127) / 128) * 128;   // NpM float4: scaled training inputs
+    L.al = L.xs + NpM * 16;                      // NpM float2: alpha
+    L.total = L.al + NpM * 8;
+    return L;
+}
+
+// deepest pipeline that fits (0 if none)
+inline int mma_stages(int NpM, int optin) {
+    for (int s = NSTAGE; s >= 2; --s)
+        if (mma_layout(s, NpM).total <= optin) return s;
+    return 0;
+}
 
 __device__ __forceinline__ void bulk_copy(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
     asm volatile(
@@ -59,71 +77,179 @@ __device__ __forceinline__ void bulk_copy(void* dst, const void* src, uint32_t b
         : "memory");
 }
 
+// hi/lo split of two values into packed 16-bit pairs (element a in the low half)
 template <int FMT>
-__device__ __forceinline__ uint32_t pack2(float a, float b, float* ra, float* rb) {
-    // hi parts of two values packed in one 32-bit word; returns the residuals
+__device__ __forceinline__ void split2(float a, float b, uint32_t* hi, uint32_t* lo) {
     if (FMT == 0) {
-        const __half ha = __float2half_rn(a), hb = __float2half_rn(b);
-        *ra = a - __half2float(ha);
-        *rb = b - __half2float(hb);
-        return (uint32_t)__half_as_ushort(ha) | ((uint32_t)__half_as_ushort(hb) << 16);
+        const __half2 h = __floats2half2_rn(a, b);
+        const float2 hf = __half22float2(h);
+        const __half2 l = __floats2half2_rn(a - hf.x, b - hf.y);
+        *hi = *reinterpret_cast<const uint32_t*>(&h);
+        *lo = *reinterpret_cast<const uint32_t*>(&l);
     } else {
-        const __nv_bfloat16 ha = __float2bfloat16_rn(a), hb = __float2bfloat16_rn(b);
-        *ra = a - __bfloat162float(ha);
-        *rb = b - __bfloat162float(hb);
-        return (uint32_t)__bfloat16_as_ushort(ha) | ((uint32_t)__bfloat16_as_ushort(hb) << 16);
+        const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+        const float2 hf = __bfloat1622float2(h);
+        const __nv_bfloat162 l = __floats2bfloat162_rn(a - hf.x, b - hf.y);
+        *hi = *reinterpret_cast<const uint32_t*>(&h);
+        *lo = *reinterpret_cast<const uint32_t*>(&l);
     }
 }
 
-template <int FMT>
-__device__ __forceinline__ uint32_t pack2_lo(float a, float b) {
-    if (FMT == 0)
-        return (uint32_t)__half_as_ushort(__float2half_rn(a)) |
-               ((uint32_t)__half_as_ushort(__float2half_rn(b)) << 16);
-    return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(a)) |
-           ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(b)) << 16);
+// Bounded wait that also gives up at once when another role has aborted.
+__device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                              unsigned int* err) {
+    if (*abort_flag) return false;
+    if (tc::mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = tc::global_ns();
+    while (!tc::mbar_try_wait(bar, parity)) {
+        if (*abort_flag) return false;
+        if (tc::global_ns() - t0 > kWaitNs) {
+            *abort_flag = 1;
+            if (err) atomicOr(err, 1u);
+            return false;
+        }
+    }
+    return true;
 }
 
-template <int FMT, bool TRACE>
-__global__ void __launch_bounds__(THREADS, 1) k_rollout_mma(const RolloutArgs a, const MmaArgs mm) {
-    extern __shared__ __align__(1024) unsigned char sm[];
-    uint64_t* mma_done = reinterpret_cast<uint64_t*>(sm + SmemM::bars);
-    uint64_t* bfull = mma_done + 2;
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + SmemM::tslot);
-    volatile int* okflag = reinterpret_cast<volatile int*>(sm + SmemM::flag);
-    float* qh = reinterpret_cast<float*>(sm + SmemM::qh);
-    float2* mh = reinterpret_cast<float2*>(sm + SmemM::mh);
-    float* ep = reinterpret_cast<float*>(sm + SmemM::ep);
-    float* omh = reinterpret_cast<float*>(sm + SmemM::om);
+__device__ __forceinline__ void producers_sync() {
+    asm volatile("bar.sync 1, 256;" ::: "memory");
+}
 
-    const int tid = threadIdx.x, warp = tid >> 5;
-    const int m = tid & (MT - 1);
-    const int h = tid >> 7;
-    const int s0 = blockIdx.x * MT;
-    const int mvalid = min(MT, a.K - s0);
-    const bool active = m < mvalid;
-    const int s_me = s0 + (active ? m : 0);
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_addr(bar)) : "memory");
+}
+
+// R producer threads per sample: a CTA owns MTC = 256 / R samples (rows
+// m >= MTC of the 128-row MMA tile are never written; their TMEM lanes are
+// not read) and each thread makes KPT = 16 / R points of every chunk.
+template <int FMT, int R, bool TRACE>
+__global__ void __launch_bounds__(THREADS, 1) k_rollout_mma(const RolloutArgs a, const MmaArgs mm, int nstage) {
+    constexpr int MTC = NPROD / R;
+    constexpr int KPT = KC / R;
+    extern __shared__ __align__(1024) unsigned char sm[];
+    const MLayout L = mma_layout(nstage, mm.nblocks * BLK);
+    uint64_t* a_full = reinterpret_cast<uint64_t*>(sm + L.bars);
+    uint64_t* b_full = a_full + NSTAGE;
+    uint64_t* empty = b_full + NSTAGE;
+    uint64_t* pass_done = empty + NSTAGE;
+    uint64_t* tmem_free = pass_done + 1;
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + L.tslot);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + L.abort_flag);
+    float4* xs_s = reinterpret_cast<float4*>(sm + L.xs);
+    float2* al_s = reinterpret_cast<float2*>(sm + L.al);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int NB = mm.nblocks;                 // 64-column blocks of L^-T
     const int npass = (NB + BLOCKS_PER_PASS - 1) / BLOCKS_PER_PASS;
 
     if (tid == 0) {
-        for (int i = 0; i < 4; ++i) tc::mbar_init(mma_done + i, 1);
-        *okflag = 1;
+        for (int i = 0; i < nstage; ++i) {
+            tc::mbar_init(a_full + i, NPROD / 32);
+            tc::mbar_init(b_full + i, 1);
+            tc::mbar_init(empty + i, 1);
+        }
+        tc::mbar_init(pass_done, 1);
+        tc::mbar_init(tmem_free, NPROD / 32);
+        *abort_flag = 0;
         tc::fence_mbar_init();
+    }
+    // scaled training inputs and alpha in shared memory; rows j >= N get a far
+    // point (exp2 underflows to exactly 0) and alpha 0
+    for (int j = tid; j < NB * BLK; j += THREADS) {
+        if (j < a.N) {
+            xs_s[j] = __ldg(reinterpret_cast<const float4*>(a.Xs) + j);
+            al_s[j] = __ldg(reinterpret_cast<const float2*>(a.alpha) + j);
+        } else {
+            xs_s[j] = make_float4(1.0e4f, 1.0e4f, 1.0e4f, 1.0e4f);
+            al_s[j] = make_float2(0.0f, 0.0f);
+        }
     }
     if (warp == 0 && NB > 0) tc::tmem_alloc(tslot, 512);
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t taddr = *tslot;
-    const uint32_t idesc = tc::idesc_f16(FMT, MT, BLK);
+
+    if (warp >= NPROD / 32) {
+        // ======================= control warps ===============================
+        if (lane != 0 || NB == 0) return;       // one thread per role
+        const bool issuer = (warp == NPROD / 32);
+        const uint32_t idesc = tc::idesc_f16(FMT, MT, BLK);
+        uint32_t n = 0, pc = 0;
+        for (int k = 0; k < a.T; ++k) {
+            for (int g = 0; g < npass; ++g, ++pc) {
+                const int b0 = g * BLOCKS_PER_PASS;
+                const int b1 = min(NB, b0 + BLOCKS_PER_PASS);
+                const int nchunk = 8 * b1;               // block b needs chunks 0 .. 8b+7
+                if (issuer && pc > 0) {
+                    wait_or_abort(tmem_free, (pc - 1) & 1u, abort_flag, a.err);
+                    tc::fence_after_sync();
+                }
+                for (int c = 0; c < nchunk; ++c, ++n) {
+                    const int st = (int)(n % (uint32_t)nstage);
+                    const uint32_t use = n / (uint32_t)nstage;
+                    unsigned char* stage = sm + st * STAGE;
+                    if (!issuer) {
+                        // tile loader: wait until the stage's previous MMAs are done
+                        if (n >= (uint32_t)nstage && !wait_or_abort(empty + st, (use - 1) & 1u, abort_flag, a.err))
+                            continue;
+                        // active blocks at chunk c are a suffix [ba, b1) of the pass
+                        // (block b needs chunks c < 8b + 8); their pieces are
+                        // contiguous in the tile arrays, one copy per part
+                        int ba = b0;
+                        while (ba < b1 && c >= 8 * ba + 8) ++ba;
+                        const uint32_t bytes = (uint32_t)((b1 - ba) * B_PART);
+                        tc::mbar_expect_tx(b_full + st, 2u * bytes);
+                        const size_t off = ((size_t)c * NB + ba) * (B_PART / 2);
+                        unsigned char* dst = stage + 2 * A_PART + (ba - b0) * B_PART;
+                        bulk_copy(dst, mm.Bhi + off, bytes, b_full + st);
+                        bulk_copy(dst + BLOCKS_PER_PASS * B_PART, mm.Blo + off, bytes, b_full + st);
+                    } else {
+                        if (!wait_or_abort(a_full + st, use & 1u, abort_flag, a.err)) continue;
+                        if (!wait_or_abort(b_full + st, use & 1u, abort_flag, a.err)) continue;
+                        tc::fence_after_sync();
+                        const uint32_t aHi = tc::smem_addr(stage), aLo = aHi + A_PART;
+                        const uint64_t dAh = tc::smem_desc(aHi, MT * 16, 128);
+                        const uint64_t dAl = tc::smem_desc(aLo, MT * 16, 128);
+                        for (int b = b0; b < b1; ++b) {
+                            if (c >= 8 * b + 8) continue;
+                            const uint32_t bHi = aHi + 2 * A_PART + (b - b0) * B_PART;
+                            const uint64_t dBh = tc::smem_desc(bHi, BLK * 16, 128);
+                            const uint64_t dBl = tc::smem_desc(bHi + BLOCKS_PER_PASS * B_PART, BLK * 16, 128);
+                            const uint32_t d = taddr + (uint32_t)((b - b0) * BLK);
+                            tc::mma_f16(d, dAh, dBh, idesc, c > 0 ? 1u : 0u);
+                            tc::mma_f16(d, dAh, dBl, idesc, 1u);
+                            tc::mma_f16(d, dAl, dBh, idesc, 1u);
+                        }
+                        tc::mma_commit(empty + st);
+                        if (c == nchunk - 1) tc::mma_commit(pass_done);
+                    }
+                }
+            }
+        }
+        return;
+    }
+
+    // ========================== producer warps =================================
+    const int m = tid % MTC;           // sample within the CTA
+    const int u = tid / MTC;           // which of its R threads
+    const int mr = tid & (MT - 1);     // TMEM lane this thread reads at a pass end
+    const int hr = tid >> 7;           // which half of the pass's columns
+    const int s0 = blockIdx.x * MTC;
+    const int mvalid = min(MTC, a.K - s0);
+    const bool active = m < mvalid;
+    const int s_me = s0 + (active ? m : 0);
+    float* qh = reinterpret_cast<float*>(sm + L.qh);
+    float2* mh = reinterpret_cast<float2*>(sm + L.mh);
+    float* ep = reinterpret_cast<float*>(sm + L.ep);
+    float* omh = reinterpret_cast<float*>(sm + L.om);
 
     float mu0 = a.x0[0], mu1 = a.x0[1], mu2 = a.x0[2], mu3 = a.x0[3], mu4 = a.x0[4];
     float S00 = 0, S01 = 0, S02 = 0, S03 = 0, S04 = 0, S11 = 0, S12 = 0, S13 = 0, S14 = 0,
           S22 = 0, S23 = 0, S24 = 0, S33 = 0, S34 = 0, S44 = 0;
     float cost = 0.0f, disc = 1.0f;
-    uint32_t n = 0;                 // chunks issued so far (all passes, all steps)
-    bool ok = true;                 // no bounded wait gave up (CTA-uniform via okflag)
+    uint32_t n = 0, pc = 0;
 
     for (int k = 0; k < a.T; ++k) {
         // ---------------- P1: noise, clamp, query (both halves) ------------
@@ -132,113 +258,73 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_mma(const RolloutArgs a,
         float2 ut;
         ut.x = fminf(fmaxf(__ldg(a.U + 2 * k) + e.x, a.umin0), a.umax0);
         ut.y = fminf(fmaxf(__ldg(a.U + 2 * k + 1) + e.y, a.umin1), a.umax1);
-        if (h == 0 && active) a.u_tilde[(size_t)k * a.K + s_me] = ut;
+        if (u == 0 && active) a.u_tilde[(size_t)k * a.K + s_me] = ut;
         const float z0 = mu3 * a.zscale[0], z1 = mu4 * a.zscale[1];
         const float z2 = ut.x * a.zscale[2], z3 = ut.y * a.zscale[3];
 
-        // ---------------- P2/P3: kernel row, mean, variance on tcgen05 ------
+        // ---------------- P2/P3: kernel-row tiles for the tensor cores ------
         float qpart = 0.0f, mv = 0.0f, mw = 0.0f, cv = 0.0f, cw = 0.0f;
-        for (int g = 0; g < npass; ++g) {
+        for (int g = 0; g < npass; ++g, ++pc) {
+            const int b1 = min(NB, (g + 1) * BLOCKS_PER_PASS);
             const int b0 = g * BLOCKS_PER_PASS;
-            const int b1 = min(NB, b0 + BLOCKS_PER_PASS);
-            const int nchunk = 2 * b1;           // block b needs chunks 0 .. 2b+1
+            const int nchunk = 8 * b1;
             const bool last_pass = (g == npass - 1);
             for (int c = 0; c < nchunk; ++c, ++n) {
-                const int st = (int)(n & 1u);
-                const uint32_t use = n >> 1;
+                const int st = (int)(n % (uint32_t)nstage);
+                const uint32_t use = n / (uint32_t)nstage;
                 unsigned char* stage = sm + st * STAGE;
-                if (n >= 2 && ok) ok = tc::mbar_wait(mma_done + st, (use - 1) & 1u, kWaitNs, a.err);
-                if (tid == 0 && ok) {
-                    int nact = 0;
-                    for (int b = b0; b < b1; ++b) nact += (c < 2 * b + 2) ? 1 : 0;
-                    tc::mbar_expect_tx(bfull + st, (uint32_t)(nact * 2 * B_TILE));
-                    for (int b = b0; b < b1; ++b) {
-                        if (c >= 2 * b + 2) continue;
-                        unsigned char* dst = stage + 2 * A_PART + (b - b0) * 2 * B_TILE;
-                        const size_t tile = ((size_t)b * mm.nchunks + c) * (B_TILE / 2);
-                        bulk_copy(dst, mm.Bhi + tile, B_TILE, bfull + st);
-                        bulk_copy(dst + B_TILE, mm.Blo + tile, B_TILE, bfull + st);
+                // this thread's KPT training points of the chunk
+                const int jb = c * KC + u * KPT;
+                float av[KPT];
+#pragma unroll
+                for (int e = 0; e < KPT; ++e) {
+                    const float4 x = xs_s[jb + e];
+                    const float d0 = z0 - x.x, d1 = z1 - x.y, d2 = z2 - x.z, d3 = z3 - x.w;
+                    av[e] = exp2f(-(d0 * d0 + d1 * d1 + d2 * d2 + d3 * d3));
+                }
+                if (last_pass) {
+#pragma unroll
+                    for (int e = 0; e < KPT; ++e) {
+                        const float2 al = al_s[jb + e];
+                        kahan_add(mv, cv, av[e] * al.x);
+                        kahan_add(mw, cw, av[e] * al.y);
                     }
                 }
-                // kernel-row tile: this thread's 16 training points = slabs 2h, 2h+1
+                uint32_t hw[KPT / 2], lw[KPT / 2];
+#pragma unroll
+                for (int q = 0; q < KPT / 2; ++q) split2<FMT>(av[2 * q], av[2 * q + 1], &hw[q], &lw[q]);
+                // the stage is free once the MMAs that last read it completed
+                if (n >= (uint32_t)nstage) wait_or_abort(empty + st, (use - 1) & 1u, abort_flag, a.err);
                 {
-                    uint32_t hw[8], lw[8];
-                    const int jb = c * KC + 16 * h;
-#pragma unroll
-                    for (int q = 0; q < 8; ++q) {
-                        float av[2];
-#pragma unroll
-                        for (int u = 0; u < 2; ++u) {
-                            const int j = jb + 2 * q + u;
-                            float v = 0.0f;
-                            if (j < a.N) {
-                                const float4 x = __ldg(reinterpret_cast<const float4*>(a.Xs) + j);
-                                const float d0 = z0 - x.x, d1 = z1 - x.y, d2 = z2 - x.z, d3 = z3 - x.w;
-                                v = exp2f(-(d0 * d0 + d1 * d1 + d2 * d2 + d3 * d3));
-                                if (last_pass) {
-                                    const float2 al = __ldg(reinterpret_cast<const float2*>(a.alpha) + j);
-                                    kahan_add(mv, cv, v * al.x);
-                                    kahan_add(mw, cw, v * al.y);
-                                }
-                            }
-                            av[u] = v;
-                        }
-                        float r0, r1;
-                        hw[q] = pack2<FMT>(av[0], av[1], &r0, &r1);
-                        lw[q] = pack2_lo<FMT>(r0, r1);
+                    // slab (u KPT) / 8, byte offset ((u KPT) % 8) * 2 within the row
+                    const int sl = (u * KPT) / 8, off = ((u * KPT) % 8) * 2;
+                    unsigned char* ph = stage + sl * MT * 16 + m * 16 + off;
+                    unsigned char* pl = ph + A_PART;
+                    if (KPT == 8) {
+                        *reinterpret_cast<uint4*>(ph) = make_uint4(hw[0], hw[1 % (KPT / 2)], hw[2 % (KPT / 2)], hw[3 % (KPT / 2)]);
+                        *reinterpret_cast<uint4*>(pl) = make_uint4(lw[0], lw[1 % (KPT / 2)], lw[2 % (KPT / 2)], lw[3 % (KPT / 2)]);
+                    } else if (KPT == 4) {
+                        *reinterpret_cast<uint2*>(ph) = make_uint2(hw[0], hw[1 % (KPT / 2)]);
+                        *reinterpret_cast<uint2*>(pl) = make_uint2(lw[0], lw[1 % (KPT / 2)]);
+                    } else {
+                        *reinterpret_cast<uint32_t*>(ph) = hw[0];
+                        *reinterpret_cast<uint32_t*>(pl) = lw[0];
                     }
-                    unsigned char* Ahi = stage;
-                    unsigned char* Alo = stage + A_PART;
-                    const int sl = 2 * h;
-                    *reinterpret_cast<uint4*>(Ahi + sl * MT * 16 + m * 16) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-                    *reinterpret_cast<uint4*>(Ahi + (sl + 1) * MT * 16 + m * 16) = make_uint4(hw[4], hw[5], hw[6], hw[7]);
-                    *reinterpret_cast<uint4*>(Alo + sl * MT * 16 + m * 16) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
-                    *reinterpret_cast<uint4*>(Alo + (sl + 1) * MT * 16 + m * 16) = make_uint4(lw[4], lw[5], lw[6], lw[7]);
                 }
                 tc::fence_proxy_async();
-                __syncthreads();
-                ok = ok && (*okflag != 0);
-                if (tid == 0 && ok) {
-                    if (!tc::mbar_wait(bfull + st, use & 1u, kWaitNs, a.err)) {
-                        ok = false;
-                        *okflag = 0;
-                    } else {
-                        tc::fence_after_sync();
-                        const uint32_t aHi = tc::smem_addr(stage), aLo = aHi + A_PART;
-                        for (int b = b0; b < b1; ++b) {
-                            if (c >= 2 * b + 2) continue;
-                            const uint32_t bHi = aHi + 2 * A_PART + (b - b0) * 2 * B_TILE;
-                            const uint32_t bLo = bHi + B_TILE;
-                            const uint32_t d = taddr + (uint32_t)((b - b0) * BLK);
-#pragma unroll
-                            for (int ks = 0; ks < 2; ++ks) {
-                                const uint32_t ao = ks * 2 * MT * 16, bo = ks * 2 * BLK * 16;
-                                const uint64_t dAh = tc::smem_desc(aHi + ao, MT * 16, 128);
-                                const uint64_t dAl = tc::smem_desc(aLo + ao, MT * 16, 128);
-                                const uint64_t dBh = tc::smem_desc(bHi + bo, BLK * 16, 128);
-                                const uint64_t dBl = tc::smem_desc(bLo + bo, BLK * 16, 128);
-                                const uint32_t acc0 = (c > 0 || ks > 0) ? 1u : 0u;
-                                tc::mma_f16(d, dAh, dBh, idesc, acc0);
-                                tc::mma_f16(d, dAh, dBl, idesc, 1u);
-                                tc::mma_f16(d, dAl, dBh, idesc, 1u);
-                            }
-                        }
-                        tc::mma_commit(mma_done + st);
-                    }
-                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(a_full + st);
             }
             // pass end: every MMA of the pass has landed in TMEM
-            const uint32_t lastn = n - 1;
-            if (ok) ok = tc::mbar_wait(mma_done + (lastn & 1u), (lastn >> 1) & 1u, kWaitNs, a.err);
-            ok = __all_sync(0xffffffffu, ok);     // tcgen05.ld below is warp-collective
+            bool ok = wait_or_abort(pass_done, pc & 1u, abort_flag, a.err);
+            ok = __all_sync(0xffffffffu, ok);        // tcgen05.ld below is warp-collective
             tc::fence_after_sync();
-            if (ok) {
+            if (ok && 32 * (warp & 3) < MTC) {
                 const int half_cols = (b1 - b0) * BLK / 2;
                 const uint32_t row = taddr + ((uint32_t)(32 * (warp & 3)) << 16);
                 for (int cc = 0; cc < half_cols; cc += 32) {
                     float v[32];
-                    tc::tmem_ld32(row + (uint32_t)(h * half_cols + cc), v);
-                    // two-level sum of squares: 4 partials of 8, then the batch
+                    tc::tmem_ld32(row + (uint32_t)(hr * half_cols + cc), v);
                     float p0 = 0.0f, p1 = 0.0f, p2 = 0.0f, p3 = 0.0f;
 #pragma unroll
                     for (int i = 0; i < 8; ++i) {
@@ -251,18 +337,22 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_mma(const RolloutArgs a,
                 }
             }
             tc::fence_before_sync();
-            __syncthreads();
-            if (!ok) *okflag = 0;
+            __syncwarp();
+            if (lane == 0) mbar_arrive(tmem_free);
         }
-        qh[h * MT + m] = qpart;
-        mh[h * MT + m] = make_float2(mv + cv, mw + cw);
-        __syncthreads();
-        ok = ok && (*okflag != 0);
+        qh[hr * MT + mr] = qpart;
+        mh[u * MTC + m] = make_float2(mv + cv, mw + cw);
+        producers_sync();
         const float q = (qh[m] + qh[MT + m]) * mm.qscale;
-        const float2 m0 = mh[m], m1 = mh[MT + m];
-        const float mean_v = a.sf2 * (m0.x + m1.x), mean_w = a.sf2 * (m0.y + m1.y);
+        float2 msum = mh[m];
+#pragma unroll
+        for (int i = 1; i < R; ++i) {
+            const float2 mi = mh[i * MTC + m];
+            msum.x += mi.x;
+            msum.y += mi.y;
+        }
+        const float mean_v = a.sf2 * msum.x, mean_w = a.sf2 * msum.y;
         const float s = fmaxf(0.0f, a.sf2 - q);
-
         // ---------------- P4: dynamics, covariance, obstacles ---------------
         float sn, cs;
         sincosf(mu2, &sn, &cs);
@@ -308,7 +398,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_mma(const RolloutArgs a,
         const float lmax = fmaxf(0.0f, 0.5f * (sxx + syy) + hypotf(0.5f * (sxx - syy), sxy));
         const float rbar = a.r - a.sq_chi2 * sqrtf(lmax);
         float om = FLT_MAX;
-        for (int o = h; o < a.O; o += 2) {
+        for (int o = u; o < a.O; o += R) {
             const float cx = __ldg(a.obst + 3 * o), cy = __ldg(a.obst + 3 * o + 1),
                         R = __ldg(a.obst + 3 * o + 2);
             const float dx = mu0 - cx, dy = mu1 - cy;
@@ -324,7 +414,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_mma(const RolloutArgs a,
         }
         // ---------------- P5: lane distance (segments split by half) -------
         float best = FLT_MAX;
-        for (int gsg = h; gsg < a.S; gsg += 2) {
+        for (int gsg = u; gsg < a.S; gsg += R) {
             const float4 sg = __ldg(a.seg + gsg);
             const float il2 = __ldg(a.seg_il2 + gsg);
             const float px = mu0 - sg.x, py = mu1 - sg.y;
@@ -332,11 +422,16 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_mma(const RolloutArgs a,
             const float qx = px - t * sg.z, qy = py - t * sg.w;
             best = fminf(best, qx * qx + qy * qy);
         }
-        omh[h * MT + m] = om;
-        ep[h * MT + m] = best;
-        __syncthreads();
-        const float omargin = fminf(omh[m], omh[MT + m]);
-        const float e_lane = sqrtf(fminf(ep[m], ep[MT + m]));
+        omh[u * MTC + m] = om;
+        ep[u * MTC + m] = best;
+        producers_sync();
+        float omargin = omh[m], e2min = ep[m];
+#pragma unroll
+        for (int i = 1; i < R; ++i) {
+            omargin = fminf(omargin, omh[i * MTC + m]);
+            e2min = fminf(e2min, ep[i * MTC + m]);
+        }
+        const float e_lane = sqrtf(e2min);
         // ---------------- P6: stage cost ------------------------------------
         float stage = a.c_var * (s + s) + a.c_speed * (a.v_des - mu3) * (a.v_des - mu3);
         if (omargin <= 0.0f) stage += a.c_coll;
@@ -345,7 +440,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_mma(const RolloutArgs a,
         if (lmargin > 0.0f) stage += a.c_lane * disc;
         cost += stage;
         disc *= 0.9f;
-        if (TRACE && active && h == 0) {
+        if (TRACE && active && u == 0) {
             const size_t sk = (size_t)s_me * a.T + k;
             if (a.tr_mu) {
                 float* o = a.tr_mu + sk * 5;
@@ -365,40 +460,50 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_mma(const RolloutArgs a,
             }
         }
     }
-    if (active && h == 0 && a.costs) a.costs[s_me] = cost;
-    // release TMEM; after a failed wait give copies and MMAs in flight a
-    // bounded time to land first
-    if (!ok && tid == 0 && n > 0) {
+    if (active && u == 0 && a.costs) a.costs[s_me] = cost;
+    // after an abort, give copies and MMAs in flight a bounded time to land
+    // before the shared memory and TMEM are released
+    if (*abort_flag && tid == 0 && n > 0) {
         const uint64_t t0 = tc::global_ns();
-        for (uint32_t i = (n >= 2 ? n - 2 : 0); i < n; ++i) {
-            while (!tc::mbar_try_wait(mma_done + (i & 1u), (i >> 1) & 1u) &&
+        for (uint32_t i = (n >= (uint32_t)nstage ? n - (uint32_t)nstage : 0); i < n; ++i)
+            while (!tc::mbar_try_wait(empty + (i % (uint32_t)nstage), (i / (uint32_t)nstage) & 1u) &&
                    tc::global_ns() - t0 < 200000000ull) {
             }
-        }
     }
     tc::fence_before_sync();
-    __syncthreads();
+    producers_sync();
     if (warp == 0 && NB > 0) tc::tmem_dealloc(taddr, 512);
 }
 
 }  // namespace
 
-int rollout_mma_smem_bytes() { return SmemM::total; }
+int rollout_mma_stages(int NpM, int smem_optin) { return mma_stages(NpM, smem_optin); }
 
 int launch_rollout_mma(const RolloutArgs& a, const MmaArgs& mm, int fmt, bool trace, cudaStream_t st) {
-    const int smem = SmemM::total;
-    const int grid = (a.K + MT - 1) / MT;
-#define GPM_LAUNCH_MMA(F, TR)                                                                     \
+    const int nstage = mm.stages;
+    if (nstage < 2 || nstage > NSTAGE) return fail(GPMPPI_ERR_INVALID_ARG, "rollout: bad MMA pipeline depth");
+    if (mm.rps != 2 && mm.rps != 4 && mm.rps != 8) return fail(GPMPPI_ERR_INVALID_ARG, "rollout: bad threads per sample");
+    const int smem = mma_layout(nstage, mm.nblocks * BLK).total;
+    const int mtc = NPROD / mm.rps;
+    const int grid = (a.K + mtc - 1) / mtc;
+#define GPM_LAUNCH_MMA(F, RR, TR)                                                                 \
     do {                                                                                          \
-        auto kern = k_rollout_mma<F, TR>;                                                         \
+        auto kern = k_rollout_mma<F, RR, TR>;                                                     \
         GPM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));  \
-        kern<<<grid, THREADS, smem, st>>>(a, mm);                                                 \
+        kern<<<grid, THREADS, smem, st>>>(a, mm, nstage);                                         \
+    } while (0)
+#define GPM_LAUNCH_MMA_R(F, TR)                          \
+    do {                                                 \
+        if (mm.rps == 2) GPM_LAUNCH_MMA(F, 2, TR);       \
+        else if (mm.rps == 4) GPM_LAUNCH_MMA(F, 4, TR);  \
+        else GPM_LAUNCH_MMA(F, 8, TR);                   \
     } while (0)
     if (fmt == 0) {
-        if (trace) GPM_LAUNCH_MMA(0, true); else GPM_LAUNCH_MMA(0, false);
+        if (trace) GPM_LAUNCH_MMA_R(0, true); else GPM_LAUNCH_MMA_R(0, false);
     } else {
-        if (trace) GPM_LAUNCH_MMA(1, true); else GPM_LAUNCH_MMA(1, false);
+        if (trace) GPM_LAUNCH_MMA_R(1, true); else GPM_LAUNCH_MMA_R(1, false);
     }
+#undef GPM_LAUNCH_MMA_R
 #undef GPM_LAUNCH_MMA
     GPM_CUDA(cudaGetLastError());
     return GPMPPI_OK;

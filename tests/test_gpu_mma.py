@@ -109,3 +109,18 @@ def test_mma_cfg3_sampled_and_properties(lib, precision):
         ut[:, k] = np.clip(sc.U0[k] + eps, P.u_min, P.u_max)
     U_chk = sc.U0 + np.einsum("s,skc->kc", w, ut - sc.U0[None])
     assert np.max(np.abs(U_new - U_chk)) <= TOL_U
+
+
+@pytest.mark.parametrize("rps", [2, 4, 8])
+def test_mma_threads_per_sample_layouts(lib, rps, monkeypatch):
+    """Every producer layout (128, 64 or 32 samples per CTA) gives the same
+    parity; K = 300 spans several CTAs with a ragged tail in each layout."""
+    monkeypatch.setenv("GPMPPI_MMA_THREADS_PER_SAMPLE", str(rps))
+    sc = _sc("small", 2, K=300, N=333, T=6)
+    g, ctrl = make_ctrl(lib, sc)
+    fits = O.gp_fit(sc.X, sc.Y, sc.hyper)
+    ro = O.rollout(sc, fits, sc.x0, sc.U0, 5)
+    tr = gpu_trace(lib, ctrl, sc, sc.x0, sc.U0, it=5)
+    check_trace(sc, ro, tr)
+    U_new, w, c = gpu_step(lib, ctrl, sc, sc.x0, sc.U0, it=5)
+    check_step(sc, ro, sc.U0, U_new, w, c)
