@@ -464,7 +464,16 @@ int mppi_create(const gpmppi_params* p, const float* obstacles, int32_t O, const
             c->mm.nchunks = g.NpM / 16;
             const double r = (double)g.sf2[0] / (g.mma_cB > 0.0f ? (double)g.mma_cB : 1.0);
             c->mm.qscale = (float)(r * r);
-            c->mm.stages = rollout_mma_stages(g.NpM, smem_optin);
+            c->mm.scene_smem = 1;
+            c->mm.stages = rollout_mma_stages(g.NpM, c->S, O, smem_optin);
+            if (c->mm.stages < 3) {
+                // keep the pipeline deep; read the scene from global memory instead
+                const int st_noscene = rollout_mma_stages(g.NpM, 0, 0, smem_optin);
+                if (st_noscene > c->mm.stages) {
+                    c->mm.stages = st_noscene;
+                    c->mm.scene_smem = 0;
+                }
+            }
             // fewest threads per sample (largest sample tile) that still
             // gives every SM a CTA; small K falls back to 32 samples per CTA
             c->mm.rps = 8;

@@ -171,6 +171,7 @@ struct MmaArgs {
     float qscale;           // (sf2 / cB)^2: |L^-1 k*|^2 = qscale * |V'|^2
     int stages;             // shared-memory pipeline depth (2..4)
     int rps;                // producer threads per sample (2, 4, 8): 128, 64, 32 samples per CTA
+    int scene_smem;         // lane segments and obstacles staged in shared memory
 };
 
 struct UpdateArgs {
@@ -203,7 +204,7 @@ int launch_noise(uint64_t seed, int K, int T, uint64_t it, float sv, float sw, f
 int launch_nominal(const RolloutArgs& a, float* sxy_out, cudaStream_t st);
 int rollout_fp32_smem_bytes(int Np, int mtp, int stages);
 int launch_rollout_mma(const RolloutArgs& a, const MmaArgs& mm, int fmt, bool trace, cudaStream_t st);
-int rollout_mma_stages(int NpM, int smem_optin);
+int rollout_mma_stages(int NpM, int S, int O, int smem_optin);
 int build_mma_tiles(GpDevice& g, int fmt);
 int launch_mma_selftest(int fmt, int N, int K, int variant, const uint16_t* A, const uint16_t* B,
                         float* D, unsigned int* err, cudaStream_t st);

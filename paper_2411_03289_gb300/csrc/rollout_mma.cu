@@ -44,10 +44,10 @@ constexpr uint64_t kWaitNs = 2000000000ull;
 
 // Shared-memory layout for a given pipeline depth and padded training-set size.
 struct MLayout {
-    int bars, tslot, abort_flag, qh, mh, ep, om, xs, al, total;
+    int bars, tslot, abort_flag, qh, mh, ep, om, xs, al, seg, il2, obs, total;
 };
 
-__host__ __device__ inline MLayout mma_layout(int nstage, int NpM) {
+__host__ __device__ inline MLayout mma_layout(int nstage, int NpM, int S, int O) {
     MLayout L;
     L.bars = nstage * STAGE;                     // a_full, b_full, empty [NSTAGE] + pass_done, tmem_free
     L.tslot = L.bars + 8 * (3 * NSTAGE + 2);
@@ -58,14 +58,17 @@ __host__ __device__ inline MLayout mma_layout(int nstage, int NpM) {
     L.om = L.ep + 2 * MT * 4;                    // 2 x 128 floats
     L.xs = ((L.om + 2 * MT * 4 + 127) / 128) * 128;   // NpM float4: scaled training inputs
     L.al = L.xs + NpM * 16;                      // NpM float2: alpha
-    L.total = L.al + NpM * 8;
+    L.seg = L.al + NpM * 8;                      // S float4: lane segments
+    L.il2 = L.seg + S * 16;                      // S floats
+    L.obs = L.il2 + ((S + 3) / 4) * 16;          // O x 3 floats: obstacles
+    L.total = L.obs + O * 12;
     return L;
 }
 
 // deepest pipeline that fits (0 if none)
-inline int mma_stages(int NpM, int optin) {
+inline int mma_stages(int NpM, int S, int O, int optin) {
     for (int s = NSTAGE; s >= 2; --s)
-        if (mma_layout(s, NpM).total <= optin) return s;
+        if (mma_layout(s, NpM, S, O).total <= optin) return s;
     return 0;
 }
 
@@ -128,7 +131,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_mma(const RolloutArgs a,
     constexpr int MTC = NPROD / R;
     constexpr int KPT = KC / R;
     extern __shared__ __align__(1024) unsigned char sm[];
-    const MLayout L = mma_layout(nstage, mm.nblocks * BLK);
+    const int Ssm = mm.scene_smem ? a.S : 0, Osm = mm.scene_smem ? a.O : 0;
+    const MLayout L = mma_layout(nstage, mm.nblocks * BLK, Ssm, Osm);
     uint64_t* a_full = reinterpret_cast<uint64_t*>(sm + L.bars);
     uint64_t* b_full = a_full + NSTAGE;
     uint64_t* empty = b_full + NSTAGE;
@@ -138,6 +142,9 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_mma(const RolloutArgs a,
     volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + L.abort_flag);
     float4* xs_s = reinterpret_cast<float4*>(sm + L.xs);
     float2* al_s = reinterpret_cast<float2*>(sm + L.al);
+    float4* seg_s = reinterpret_cast<float4*>(sm + L.seg);
+    float* il2_s = reinterpret_cast<float*>(sm + L.il2);
+    float* obs_s = reinterpret_cast<float*>(sm + L.obs);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int NB = mm.nblocks;                 // 64-column blocks of L^-T
@@ -165,6 +172,16 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_mma(const RolloutArgs a,
             al_s[j] = make_float2(0.0f, 0.0f);
         }
     }
+    // lane segments and obstacles too: the cost phase reads them every step
+    for (int i = tid; i < Ssm; i += THREADS) {
+        seg_s[i] = __ldg(a.seg + i);
+        il2_s[i] = __ldg(a.seg_il2 + i);
+    }
+    for (int i = tid; i < 3 * Osm; i += THREADS) obs_s[i] = __ldg(a.obst + i);
+    // a scene too large for shared memory is read from global memory instead
+    const float4* segp = mm.scene_smem ? seg_s : a.seg;
+    const float* il2p = mm.scene_smem ? il2_s : a.seg_il2;
+    const float* obsp = mm.scene_smem ? obs_s : a.obst;
     if (warp == 0 && NB > 0) tc::tmem_alloc(tslot, 512);
     tc::fence_before_sync();
     __syncthreads();
@@ -399,8 +416,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_mma(const RolloutArgs a,
         const float rbar = a.r - a.sq_chi2 * sqrtf(lmax);
         float om = FLT_MAX;
         for (int o = u; o < a.O; o += R) {
-            const float cx = __ldg(a.obst + 3 * o), cy = __ldg(a.obst + 3 * o + 1),
-                        R = __ldg(a.obst + 3 * o + 2);
+            const float cx = obsp[3 * o], cy = obsp[3 * o + 1], R = obsp[3 * o + 2];
             const float dx = mu0 - cx, dy = mu1 - cy;
             const float rho = sqrtf(dx * dx + dy * dy);
             float spread;
@@ -415,8 +431,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_mma(const RolloutArgs a,
         // ---------------- P5: lane distance (segments split by half) -------
         float best = FLT_MAX;
         for (int gsg = u; gsg < a.S; gsg += R) {
-            const float4 sg = __ldg(a.seg + gsg);
-            const float il2 = __ldg(a.seg_il2 + gsg);
+            const float4 sg = segp[gsg];
+            const float il2 = il2p[gsg];
             const float px = mu0 - sg.x, py = mu1 - sg.y;
             const float t = fminf(fmaxf((px * sg.z + py * sg.w) * il2, 0.0f), 1.0f);
             const float qx = px - t * sg.z, qy = py - t * sg.w;
@@ -477,13 +493,13 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_mma(const RolloutArgs a,
 
 }  // namespace
 
-int rollout_mma_stages(int NpM, int smem_optin) { return mma_stages(NpM, smem_optin); }
+int rollout_mma_stages(int NpM, int S, int O, int smem_optin) { return mma_stages(NpM, S, O, smem_optin); }
 
 int launch_rollout_mma(const RolloutArgs& a, const MmaArgs& mm, int fmt, bool trace, cudaStream_t st) {
     const int nstage = mm.stages;
     if (nstage < 2 || nstage > NSTAGE) return fail(GPMPPI_ERR_INVALID_ARG, "rollout: bad MMA pipeline depth");
     if (mm.rps != 2 && mm.rps != 4 && mm.rps != 8) return fail(GPMPPI_ERR_INVALID_ARG, "rollout: bad threads per sample");
-    const int smem = mma_layout(nstage, mm.nblocks * BLK).total;
+    const int smem = mma_layout(nstage, mm.nblocks * BLK, mm.scene_smem ? a.S : 0, mm.scene_smem ? a.O : 0).total;
     const int mtc = NPROD / mm.rps;
     const int grid = (a.K + mtc - 1) / mtc;
 #define GPM_LAUNCH_MMA(F, RR, TR)                                                                 \

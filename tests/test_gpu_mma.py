@@ -124,3 +124,16 @@ def test_mma_threads_per_sample_layouts(lib, rps, monkeypatch):
     check_trace(sc, ro, tr)
     U_new, w, c = gpu_step(lib, ctrl, sc, sc.x0, sc.U0, it=5)
     check_step(sc, ro, sc.U0, U_new, w, c)
+
+
+def test_mma_scene_too_large_for_shared_memory(lib):
+    """A scene whose segments and obstacles do not fit next to the pipeline
+    is read from global memory: same parity."""
+    sc = _sc("small", 2, K=70, N=1900, T=3, O=1500)
+    t = np.linspace(0, 2 * np.pi, 6000)
+    sc = sc.replace(path=np.stack([6 * np.cos(t), 3 * np.sin(t)], axis=1))
+    g, ctrl = make_ctrl(lib, sc)
+    fits = O.gp_fit(sc.X, sc.Y, sc.hyper)
+    ro = O.rollout(sc, fits, sc.x0, sc.U0, 1)
+    tr = gpu_trace(lib, ctrl, sc, sc.x0, sc.U0, it=1)
+    check_trace(sc, ro, tr)
