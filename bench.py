@@ -415,6 +415,124 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+def run_batched(args):
+    """cfg5: 64 independent controllers (K, T, N, obstacles and paths all
+    different) advanced together, one CUDA-graph replay per step."""
+    import numpy as np
+    import torch
+
+    import paper_2411_03289_gb300 as gp
+    import scenarios as S
+    from paper_2411_03289_gb300 import build as B
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    B.build()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    prec = PRECISIONS[args.precision]
+    scs = S.batched_scenarios(args.batch, first_seed=args.batch * rank)
+    for sc in scs:
+        sc.params.precision = prec
+    t_fit = time.perf_counter()
+    gps = [gp.gp_fit(sc.X, sc.Y, sc.hyper) for sc in scs]
+    ctrls = [gp.mppi_create(sc.params, sc.obstacles, sc.path, g) for sc, g in zip(scs, gps)]
+    torch.cuda.synchronize()
+    t_fit = time.perf_counter() - t_fit
+    batch = gp.mppi_batch_create(ctrls)
+    host_state = [torch.tensor(sc.x0, dtype=torch.float32).pin_memory() for sc in scs]
+    host_U = [torch.tensor(sc.U0, dtype=torch.float32).pin_memory() for sc in scs]
+    for i in range(len(scs)):
+        batch.state[i].copy_(host_state[i])
+        batch.U_nom[i].copy_(host_U[i])
+    stream = torch.cuda.Stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    chosen = gp.mppi_batch_autotune(batch, stream)
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            gp.mppi_batch_graph(batch, stream)
+        stream.synchronize()
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        clocks = ClockSampler(torch.cuda.current_device())
+        clocks.start()
+        barrier()
+        for i in range(args.steps):
+            starts[i].record(stream)
+            gp.mppi_batch_graph(batch, stream)
+            ends[i].record(stream)
+            flush.fill_(float(i))
+        stream.synchronize()
+        barrier()
+        clk = clocks.stop()
+        step_ms = [a.elapsed_time(b_) for a, b_ in zip(starts, ends)]
+        # end to end: every controller's state and controls in, results out
+        outs = [torch.empty_like(u).pin_memory() for u in host_U]
+        e2e_s = 0.0
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            stream.synchronize()
+            t0 = time.perf_counter()
+            for j in range(len(scs)):
+                batch.state[j].copy_(host_state[j], non_blocking=True)
+                batch.U_nom[j].copy_(host_U[j], non_blocking=True)
+            gp.mppi_batch_graph(batch, stream)
+            for j in range(len(scs)):
+                outs[j].copy_(batch.U_new[j], non_blocking=True)
+            stream.synchronize()
+            e2e_s += time.perf_counter() - t0
+    tot_ms = sum(step_ms)
+    if ws > 1:
+        t = torch.tensor([tot_ms, e2e_s], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        tot_ms, e2e_s = float(t[0].item()), float(t[1].item())
+    units_step = sum(sc.params.K * sc.params.T for sc in scs)
+    flops_step = sum(rollout_flops_per_sample_step(sc.N, sc.obstacles.shape[0], max(sc.path.shape[0] - 1, 1))
+                     * sc.params.K * sc.params.T for sc in scs)
+    value = units_step * args.steps * ws / (tot_ms / 1e3)
+    peak, note = measured_tensor_peak()
+    achieved = flops_step / (tot_ms / args.steps / 1e3) / 1e12
+    if rank != 0:
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": "sample-steps/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "p50_ms": statistics.median(step_ms),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {0: "f32", 1: "f32+bf16split", 2: "f32+f16split"}[prec],
+        "data": "synthetic (64 seeded controllers)",
+        "config": {"workload": f"cfg5: {len(scs)} controllers, K {min(s.params.K for s in scs)}..{max(s.params.K for s in scs)}, "
+                               f"T {min(s.params.T for s in scs)}..{max(s.params.T for s in scs)}, "
+                               f"N {min(s.N for s in scs)}..{max(s.N for s in scs)}, one CUDA-graph replay per step",
+                   "controllers": len(scs), "sample_steps_per_step": units_step,
+                   "tile_layout_threads_per_sample": chosen, "precision": args.precision,
+                   "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)",
+                   "fit_and_create_s": t_fit},
+        "gpu_launches": args.steps * (2 + sum(1 for sc in scs if sc.params.precision == 0)),
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None, "kernel": "k_rollout_mma_batched",
+                     "peak_note": note + "; whole batched step timed"},
+        "cpu_baseline": None,
+        "e2e": {"value": units_step * args.steps * ws / e2e_s, "unit": "sample-steps/s",
+                "h2d_bytes_per_step": sum(4 * (5 + 2 * sc.params.T) for sc in scs),
+                "d2h_bytes_per_step": sum(4 * 2 * sc.params.T for sc in scs)},
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
 def main():
     if len(sys.argv) >= 2 and sys.argv[1] == "--cpu-child":
         _cpu_child(int(sys.argv[2]), int(sys.argv[3]))
@@ -429,6 +547,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline leg")
     ap.add_argument("--workload", default=WORKLOAD, help="scenario name (cfg2 is the reported workload)")
     ap.add_argument("--precision", default="fp16split", choices=sorted(PRECISIONS))
+    ap.add_argument("--batch", type=int, default=64, help="controllers in the cfg5 workload")
     ap.add_argument("--no-fp32-path", action="store_true",
                     help="skip timing the plain FP32 CUDA-core path beside the headline path")
     args = ap.parse_args()
@@ -436,6 +555,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "cfg5":
+        run_batched(args)
     else:
         run_ours(args)
 

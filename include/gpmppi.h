@@ -65,6 +65,7 @@ extern "C" {
 
 typedef struct gpmppi_gp_s* gpmppi_gp;       /* opaque, owned by the library */
 typedef struct gpmppi_ctrl_s* gpmppi_ctrl;   /* opaque, owned by the library */
+typedef struct gpmppi_batch_s* gpmppi_batch; /* opaque, owned by the library */
 
 /* SE-ARD hyper-parameters of one GP output (Sec. III-A; Sec. V-A trains
  * them with GPyTorch, here they are supplied):
@@ -214,6 +215,38 @@ int mppi_destroy(gpmppi_ctrl c);
 int mppi_update_noalloc(const float* costs, const float* u_tilde, const float* U_nom,
                         float* U_new, float* weights, int32_t K, int32_t T, float lambda,
                         void* stream);
+
+/* ---- Batched iterations of many independent controllers (Alg. 1 run for
+ * several robots at once; each controller keeps its own GP, scene, sizes
+ * K, T, N, obstacles and precision). ---------------------------------------
+ *
+ * mppi_batch_create groups B distinct controllers of the current device
+ * (per-sample variance mode only).  The batch owns device buffers for every
+ * controller's state (5 floats), nominal controls U_nom (T x 2), result U_new
+ * (T x 2) and weights (K); mppi_batch_buffers returns their device addresses
+ * (and that of the controller's cost array, K floats).  The caller writes
+ * states and U_nom there (e.g. cudaMemcpyAsync) before a step and reads the
+ * results after it.  The Philox iteration counter of each controller lives in
+ * device memory while batched: it starts from the controller's counter at
+ * creation, advances by one per batched step, and is read back with
+ * mppi_batch_get_iteration (the controller's own counter is not updated).
+ * A step = all tensor-core controllers in one launch per 16-bit format (CTAs
+ * over (controller, sample-tile) items, largest work first), the FP32
+ * controllers one after the other, then one update launch for all. */
+int mppi_batch_create(const gpmppi_ctrl* ctrls, int32_t B, gpmppi_batch* out);
+int mppi_batch_buffers(gpmppi_batch b, int32_t i, float** state, float** U_nom, float** U_new,
+                       float** weights, float** costs);
+/* One iteration of every controller, enqueued on stream (NULL = legacy). */
+int mppi_batch_step(gpmppi_batch b, void* stream);
+/* The same iteration through a CUDA graph: captured on first use (stream
+ * must be a created stream, not NULL) and replayed by every later call. */
+int mppi_batch_graph(gpmppi_batch b, void* stream);
+/* Autotuner: times the tensor-core tile layouts (2, 4 or 8 producer threads
+ * per sample, i.e. 128, 64 or 32 samples per CTA) on this batch, keeps the
+ * fastest and returns it in *chosen.  Blocking; restores the counters. */
+int mppi_batch_autotune(gpmppi_batch b, void* stream, int32_t* chosen);
+int mppi_batch_get_iteration(gpmppi_batch b, int32_t i, uint64_t* it);
+int mppi_batch_destroy(gpmppi_batch b);
 
 /* Raw Philox4x32-10 blocks as the kernels draw them (Salmon et al., SC'11):
  *   ctr  device, M x 4 uint32 counters; out device, M x 4 uint32 words. */

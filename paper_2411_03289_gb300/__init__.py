@@ -35,7 +35,9 @@ GPMPPI_FP16_SPLIT = 2
 # names every build of the library exports (checked by the CPU test suite)
 EXPORTS = ("gp_fit", "gp_destroy", "gp_factors", "gp_predict", "mppi_create", "mppi_step",
            "mppi_rollout_trace", "mppi_set_iteration", "mppi_get_iteration", "mppi_nominal_sxy",
-           "mppi_destroy", "mppi_set_profiling", "mppi_last_profile", "mppi_device_status", "mppi_update_noalloc", "gpmppi_philox", "gpmppi_control_noise", "gpmppi_mma_selftest", "gpmppi_last_error",
+           "mppi_destroy", "mppi_set_profiling", "mppi_last_profile", "mppi_device_status", "mppi_update_noalloc", "mppi_batch_create",
+           "mppi_batch_buffers", "mppi_batch_step", "mppi_batch_graph", "mppi_batch_autotune",
+           "mppi_batch_get_iteration", "mppi_batch_destroy", "gpmppi_philox", "gpmppi_control_noise", "gpmppi_mma_selftest", "gpmppi_last_error",
            "gpmppi_version")
 
 
@@ -90,6 +92,13 @@ def load():
         "mppi_set_profiling": [vp, i32],
         "mppi_last_profile": [vp, vp, vp],
         "mppi_device_status": [vp],
+        "mppi_batch_create": [vp, i32, ctypes.POINTER(vp)],
+        "mppi_batch_buffers": [vp, i32, vp, vp, vp, vp, vp],
+        "mppi_batch_step": [vp, vp],
+        "mppi_batch_graph": [vp, vp],
+        "mppi_batch_autotune": [vp, vp, vp],
+        "mppi_batch_get_iteration": [vp, i32, ctypes.POINTER(u64)],
+        "mppi_batch_destroy": [vp],
         "mppi_update_noalloc": [vp, vp, vp, vp, vp, i32, i32, ctypes.c_float, vp],
         "gpmppi_philox": [u64, vp, i32, vp, vp],
         "gpmppi_control_noise": [u64, i32, i32, u64, vp, vp, vp],
@@ -335,3 +344,72 @@ def gpmppi_mma_selftest(fmt: int, A, B, D, variant: int = 0):
     N, K = B.shape
     _check(load().gpmppi_mma_selftest(fmt, N, K, variant, _dptr(A, name="A"), _dptr(B, name="B"),
                                       _dptr(D, numel=128 * N, name="D")))
+
+
+class _DevArray:
+    """A device pointer exposed through __cuda_array_interface__ (zero copy)."""
+
+    def __init__(self, ptr, shape, typestr="<f4"):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr,
+                                         "data": (int(ptr), False), "version": 3, "strides": None}
+
+
+def _as_tensor(ptr, shape):
+    import torch
+    return torch.as_tensor(_DevArray(ptr, shape), device="cuda")
+
+
+class Batch:
+    """Owning wrapper of a gpmppi_batch handle (keeps its controllers alive).
+    ``state[i]``, ``U_nom[i]``, ``U_new[i]``, ``weights[i]`` and ``costs[i]``
+    are torch views of the batch's device buffers for controller i."""
+
+    def __init__(self, handle, ctrls):
+        self.handle, self.ctrls = handle, list(ctrls)
+        self.state, self.U_nom, self.U_new, self.weights, self.costs = [], [], [], [], []
+        for i, c in enumerate(self.ctrls):
+            ptrs = [ctypes.c_void_p() for _ in range(5)]
+            _check(load().mppi_batch_buffers(handle, i, *[ctypes.byref(p) for p in ptrs]))
+            self.state.append(_as_tensor(ptrs[0].value, (5,)))
+            self.U_nom.append(_as_tensor(ptrs[1].value, (c.T, 2)))
+            self.U_new.append(_as_tensor(ptrs[2].value, (c.T, 2)))
+            self.weights.append(_as_tensor(ptrs[3].value, (c.K,)))
+            self.costs.append(_as_tensor(ptrs[4].value, (c.K,)))
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.mppi_batch_destroy(self.handle)
+            self.handle = None
+
+
+def mppi_batch_create(ctrls) -> Batch:
+    arr = (ctypes.c_void_p * len(ctrls))(*[c.handle for c in ctrls])
+    h = ctypes.c_void_p()
+    _check(load().mppi_batch_create(ctypes.cast(arr, ctypes.c_void_p), len(ctrls), ctypes.byref(h)))
+    return Batch(h.value, ctrls)
+
+
+def mppi_batch_step(batch: Batch, stream=None):
+    _check(load().mppi_batch_step(batch.handle, _stream(stream)))
+
+
+def mppi_batch_graph(batch: Batch, stream=None):
+    _check(load().mppi_batch_graph(batch.handle, _stream(stream)))
+
+
+def mppi_batch_autotune(batch: Batch, stream=None) -> int:
+    v = ctypes.c_int32()
+    _check(load().mppi_batch_autotune(batch.handle, _stream(stream), ctypes.byref(v)))
+    return v.value
+
+
+def mppi_batch_get_iteration(batch: Batch, i: int) -> int:
+    v = ctypes.c_uint64()
+    _check(load().mppi_batch_get_iteration(batch.handle, i, ctypes.byref(v)))
+    return v.value
+
+
+def mppi_batch_destroy(batch: Batch):
+    if batch.handle:
+        _check(load().mppi_batch_destroy(batch.handle))
+        batch.handle = None

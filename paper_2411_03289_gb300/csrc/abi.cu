@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "handles.cuh"
 
 namespace gpm {
 
@@ -35,8 +36,8 @@ using namespace gpm;
 
 namespace {
 
-constexpr uint32_t kGpMagic = 0x47504d31u;     // "GPM1"
-constexpr uint32_t kCtrlMagic = 0x4d505031u;   // "MPP1"
+constexpr uint32_t kGpMagic = kGpMagicValue;
+constexpr uint32_t kCtrlMagic = kCtrlMagicValue;
 
 bool is_finite(double v) { return std::isfinite(v); }
 
@@ -81,38 +82,6 @@ int check_dev_ptr(const void* p, const char* name, bool nullable) {
 }
 
 }  // namespace
-
-struct gpmppi_gp_s {
-    uint32_t magic = kGpMagic;
-    GpDevice g;
-};
-
-struct gpmppi_ctrl_s {
-    uint32_t magic = kCtrlMagic;
-    gpmppi_params p{};
-    gpmppi_gp gp = nullptr;
-    int device = 0;
-    int O = 0, P = 0, S = 0;
-    int mt = 1, n_upd = 1;
-    uint64_t it = 0;
-    double sq_chi2 = 0.0, phi_inv = 0.0;
-    float* obst = nullptr;
-    float4* seg = nullptr;
-    float* seg_il2 = nullptr;
-    float* costs = nullptr;       // K, used when the caller passes no costs array
-    float2* u_tilde = nullptr;    // T x K
-    float* partial = nullptr;     // n_upd x T x 2
-    unsigned int* counter = nullptr;
-    float* nom_sxy = nullptr;     // T x 3
-    unsigned int* err = nullptr;  // device status word written by the rollout
-    int stages = 2;               // per-warp TMA pipeline depth
-    CUtensorMap tmW;              // TMA map over the GP's W
-    MmaArgs mm{};                 // tensor-core tiles (split precisions)
-    int fmt = -1;                 // 0 = FP16, 1 = BF16 split, -1 = FP32 path
-    bool profiling = false;
-    bool profiled = false;
-    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
-};
 
 namespace {
 
@@ -198,7 +167,9 @@ int check_state(const float* state) {
     return GPMPPI_OK;
 }
 
-RolloutArgs make_rollout_args(gpmppi_ctrl c, const float* state, const float* U) {
+}  // namespace
+
+RolloutArgs gpm::make_rollout_args(gpmppi_ctrl c, const float* state, const float* U) {
     const gpmppi_params& p = c->p;
     const GpDevice& g = c->gp->g;
     RolloutArgs a;
@@ -251,6 +222,8 @@ RolloutArgs make_rollout_args(gpmppi_ctrl c, const float* state, const float* U)
     a.it1 = (uint32_t)(c->it >> 32);
     return a;
 }
+
+namespace {
 
 int check_ctrl_device(gpmppi_ctrl c) {
     int dev = 0;

@@ -157,6 +157,10 @@ struct RolloutArgs {
     float c_coll;           // beta_1 * P_coll
     float r, v_des, sq_chi2, phi_inv;
     uint32_t key0, key1, it0, it1;
+    // when set, the initial state and the iteration are read from device
+    // memory instead of x0 / it0 / it1 (batched and graph-replayed steps)
+    const float* x0_dev;
+    const unsigned long long* it_dev;
 };
 
 // Tensor-core variance contraction: L^-T (scaled by cB, a power of two) split
@@ -195,6 +199,11 @@ int make_w_tensor_map(CUtensorMap* out, const float* W, int Np);
 // pipeline depth that fits shared memory (0 if none fits)
 int rollout_fp32_stages(int Np, int smem_optin);
 int launch_update(const UpdateArgs& a, int n_cta, cudaStream_t st);
+int launch_update_batched(const UpdateArgs* args, const int2* items, const int* ncta,
+                          unsigned long long* iters, int nitems, int maxT, cudaStream_t st);
+int launch_rollout_mma_batched(const RolloutArgs* args, const MmaArgs* mms, const int2* items, int nitems,
+                               int fmt, int rps, int smem, cudaStream_t st);
+int rollout_mma_smem(const MmaArgs& mm, int S, int O);
 int launch_gp_predict(const GpDevice& g, const float* Z, int M, float* mean, float* var,
                       cudaStream_t st);
 int gp_fit_device(GpDevice& g, const double* X, const double* Y, int N, cudaStream_t st);

@@ -29,8 +29,8 @@ __device__ __forceinline__ float warp_min(float v) {
     return v;
 }
 
-__global__ void __launch_bounds__(UPD_THREADS) k_update(const UpdateArgs a) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+__device__ __forceinline__ void update_body(const UpdateArgs& a, int cta, int n_cta,
+                                            unsigned long long* it_dev, unsigned char* smem_raw) {
     float2* wpart = reinterpret_cast<float2*>(smem_raw);   // UPD_WARPS x T
     __shared__ float red[UPD_WARPS];
     __shared__ float bcast[2];
@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update(const UpdateArgs a) {
     const float inv_z = 1.0f / bcast[1];
 
     // own samples
-    const int s = blockIdx.x * a.per_cta + tid;
+    const int s = cta * a.per_cta + tid;
     const bool act = (tid < a.per_cta) && (s < K);
     const float w = act ? expf((rho - __ldg(a.costs + s)) * a.inv_lambda) * inv_z : 0.0f;
     if (act && a.weights) a.weights[s] = w;
@@ -89,22 +89,41 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update(const UpdateArgs a) {
             sv += p.x;
             sw += p.y;
         }
-        a.partial[((size_t)blockIdx.x * T + k) * 2] = sv;
-        a.partial[((size_t)blockIdx.x * T + k) * 2 + 1] = sw;
+        a.partial[((size_t)cta * T + k) * 2] = sv;
+        a.partial[((size_t)cta * T + k) * 2 + 1] = sw;
     }
     // last CTA combines the partials in CTA order
     __threadfence();
     __syncthreads();
-    if (tid == 0) is_last = (atomicAdd(a.counter, 1u) == gridDim.x - 1) ? 1u : 0u;
+    if (tid == 0) is_last = (atomicAdd(a.counter, 1u) == (unsigned int)n_cta - 1u) ? 1u : 0u;
     __syncthreads();
     if (!is_last) return;
     __threadfence();
     for (int i = tid; i < 2 * T; i += UPD_THREADS) {
         float acc = 0.0f;
-        for (int c = 0; c < (int)gridDim.x; ++c) acc += __ldcg(a.partial + (size_t)c * 2 * T + i);
+        for (int c = 0; c < n_cta; ++c) acc += __ldcg(a.partial + (size_t)c * 2 * T + i);
         a.U_new[i] = __ldg(a.U + i) + acc;
     }
-    if (tid == 0) *a.counter = 0u;
+    if (tid == 0) {
+        *a.counter = 0u;
+        if (it_dev) *it_dev += 1ull;     // the next iteration's Philox counter
+    }
+}
+
+__global__ void __launch_bounds__(UPD_THREADS) k_update(const UpdateArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    update_body(a, blockIdx.x, gridDim.x, nullptr, smem_raw);
+}
+
+// Many controllers: CTA i serves CTA items[i].y of controller items[i].x,
+// whose update needs ncta[items[i].x] CTAs; the last one advances its
+// iteration counter.
+__global__ void __launch_bounds__(UPD_THREADS)
+    k_update_batched(const UpdateArgs* __restrict__ args, const int2* __restrict__ items,
+                     const int* __restrict__ ncta, unsigned long long* __restrict__ iters) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int2 it = items[blockIdx.x];
+    update_body(args[it.x], it.y, ncta[it.x], iters + it.x, smem_raw);
 }
 
 __global__ void k_philox(uint32_t key0, uint32_t key1, const uint4* __restrict__ ctr, int M,
@@ -220,6 +239,16 @@ int launch_update(const UpdateArgs& a, int n_cta, cudaStream_t st) {
     const int smem = UPD_WARPS * a.T * (int)sizeof(float2);
     GPM_CUDA(cudaFuncSetAttribute(k_update, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     k_update<<<n_cta, UPD_THREADS, smem, st>>>(a);
+    GPM_CUDA(cudaGetLastError());
+    return GPMPPI_OK;
+}
+
+int launch_update_batched(const UpdateArgs* args, const int2* items, const int* ncta,
+                          unsigned long long* iters, int nitems, int maxT, cudaStream_t st) {
+    if (nitems == 0) return GPMPPI_OK;
+    const int smem = UPD_WARPS * maxT * (int)sizeof(float2);
+    GPM_CUDA(cudaFuncSetAttribute(k_update_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    k_update_batched<<<nitems, UPD_THREADS, smem, st>>>(args, items, ncta, iters);
     GPM_CUDA(cudaGetLastError());
     return GPMPPI_OK;
 }

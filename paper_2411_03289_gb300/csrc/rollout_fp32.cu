@@ -156,6 +156,15 @@ __global__ void __launch_bounds__(THREADS, 1)
     const bool active = owner && (lane < mvalid);
     const int s_me = s0 + ((lane < mvalid) ? lane : 0);
     float mu0 = a.x0[0], mu1 = a.x0[1], mu2 = a.x0[2], mu3 = a.x0[3], mu4 = a.x0[4];
+    uint32_t it0 = a.it0, it1 = a.it1;
+    if (a.x0_dev) {
+        mu0 = a.x0_dev[0]; mu1 = a.x0_dev[1]; mu2 = a.x0_dev[2]; mu3 = a.x0_dev[3]; mu4 = a.x0_dev[4];
+    }
+    if (a.it_dev) {
+        const unsigned long long v = *a.it_dev;
+        it0 = (uint32_t)v;
+        it1 = (uint32_t)(v >> 32);
+    }
     // symmetric Sigma, upper triangle
     float S00 = 0, S01 = 0, S02 = 0, S03 = 0, S04 = 0, S11 = 0, S12 = 0, S13 = 0, S14 = 0,
           S22 = 0, S23 = 0, S24 = 0, S33 = 0, S34 = 0, S44 = 0;
@@ -178,7 +187,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     for (int k = 0; k < a.T; ++k) {
         // ---------------- P1: noise, clamp, query --------------------------
         if (owner) {
-            const float2 e = control_eps((uint32_t)k, (uint32_t)s_me, a.it0, a.it1, a.key0, a.key1,
+            const float2 e = control_eps((uint32_t)k, (uint32_t)s_me, it0, it1, a.key0, a.key1,
                                          a.sig_v, a.sig_w);
             ut.x = fminf(fmaxf(__ldg(a.U + 2 * k) + e.x, a.umin0), a.umax0);
             ut.y = fminf(fmaxf(__ldg(a.U + 2 * k + 1) + e.y, a.umin1), a.umax1);

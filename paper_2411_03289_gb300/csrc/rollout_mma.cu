@@ -127,10 +127,11 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 // m >= MTC of the 128-row MMA tile are never written; their TMEM lanes are
 // not read) and each thread makes KPT = 16 / R points of every chunk.
 template <int FMT, int R, bool TRACE>
-__global__ void __launch_bounds__(THREADS, 1) k_rollout_mma(const RolloutArgs a, const MmaArgs mm, int nstage) {
+__device__ __forceinline__ void rollout_mma_body(const RolloutArgs& a, const MmaArgs& mm, int tile,
+                                                 unsigned char* sm) {
     constexpr int MTC = NPROD / R;
     constexpr int KPT = KC / R;
-    extern __shared__ __align__(1024) unsigned char sm[];
+    const int nstage = mm.stages;
     const int Ssm = mm.scene_smem ? a.S : 0, Osm = mm.scene_smem ? a.O : 0;
     const MLayout L = mma_layout(nstage, mm.nblocks * BLK, Ssm, Osm);
     uint64_t* a_full = reinterpret_cast<uint64_t*>(sm + L.bars);
@@ -253,7 +254,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_mma(const RolloutArgs a,
     const int u = tid / MTC;           // which of its R threads
     const int mr = tid & (MT - 1);     // TMEM lane this thread reads at a pass end
     const int hr = tid >> 7;           // which half of the pass's columns
-    const int s0 = blockIdx.x * MTC;
+    const int s0 = tile * MTC;
     const int mvalid = min(MTC, a.K - s0);
     const bool active = m < mvalid;
     const int s_me = s0 + (active ? m : 0);
@@ -263,6 +264,15 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_mma(const RolloutArgs a,
     float* omh = reinterpret_cast<float*>(sm + L.om);
 
     float mu0 = a.x0[0], mu1 = a.x0[1], mu2 = a.x0[2], mu3 = a.x0[3], mu4 = a.x0[4];
+    uint32_t it0 = a.it0, it1 = a.it1;
+    if (a.x0_dev) {
+        mu0 = a.x0_dev[0]; mu1 = a.x0_dev[1]; mu2 = a.x0_dev[2]; mu3 = a.x0_dev[3]; mu4 = a.x0_dev[4];
+    }
+    if (a.it_dev) {
+        const unsigned long long v = *a.it_dev;
+        it0 = (uint32_t)v;
+        it1 = (uint32_t)(v >> 32);
+    }
     float S00 = 0, S01 = 0, S02 = 0, S03 = 0, S04 = 0, S11 = 0, S12 = 0, S13 = 0, S14 = 0,
           S22 = 0, S23 = 0, S24 = 0, S33 = 0, S34 = 0, S44 = 0;
     float cost = 0.0f, disc = 1.0f;
@@ -270,7 +280,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_mma(const RolloutArgs a,
 
     for (int k = 0; k < a.T; ++k) {
         // ---------------- P1: noise, clamp, query (both halves) ------------
-        const float2 e = control_eps((uint32_t)k, (uint32_t)s_me, a.it0, a.it1, a.key0, a.key1,
+        const float2 e = control_eps((uint32_t)k, (uint32_t)s_me, it0, it1, a.key0, a.key1,
                                      a.sig_v, a.sig_w);
         float2 ut;
         ut.x = fminf(fmaxf(__ldg(a.U + 2 * k) + e.x, a.umin0), a.umax0);
@@ -491,6 +501,24 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_mma(const RolloutArgs a,
     if (warp == 0 && NB > 0) tc::tmem_dealloc(taddr, 512);
 }
 
+template <int FMT, int R, bool TRACE>
+__global__ void __launch_bounds__(THREADS, 1) k_rollout_mma(const RolloutArgs a, const MmaArgs mm) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    rollout_mma_body<FMT, R, TRACE>(a, mm, blockIdx.x, sm);
+}
+
+// Many controllers in one launch: CTA i runs tile items[i].y of controller
+// items[i].x (items ordered by decreasing work), with that controller's
+// arguments, state and Philox iteration read from device memory.
+template <int FMT, int R>
+__global__ void __launch_bounds__(THREADS, 1)
+    k_rollout_mma_batched(const RolloutArgs* __restrict__ args, const MmaArgs* __restrict__ mms,
+                          const int2* __restrict__ items) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    const int2 it = items[blockIdx.x];
+    rollout_mma_body<FMT, R, false>(args[it.x], mms[it.x], it.y, sm);
+}
+
 }  // namespace
 
 int rollout_mma_stages(int NpM, int S, int O, int smem_optin) { return mma_stages(NpM, S, O, smem_optin); }
@@ -506,7 +534,7 @@ int launch_rollout_mma(const RolloutArgs& a, const MmaArgs& mm, int fmt, bool tr
     do {                                                                                          \
         auto kern = k_rollout_mma<F, RR, TR>;                                                     \
         GPM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));  \
-        kern<<<grid, THREADS, smem, st>>>(a, mm, nstage);                                         \
+        kern<<<grid, THREADS, smem, st>>>(a, mm);                                                 \
     } while (0)
 #define GPM_LAUNCH_MMA_R(F, TR)                          \
     do {                                                 \
@@ -521,6 +549,33 @@ int launch_rollout_mma(const RolloutArgs& a, const MmaArgs& mm, int fmt, bool tr
     }
 #undef GPM_LAUNCH_MMA_R
 #undef GPM_LAUNCH_MMA
+    GPM_CUDA(cudaGetLastError());
+    return GPMPPI_OK;
+}
+
+}  // namespace gpm
+
+namespace gpm {
+
+int rollout_mma_smem(const MmaArgs& mm, int S, int O) {
+    return mma_layout(mm.stages, mm.nblocks * BLK, mm.scene_smem ? S : 0, mm.scene_smem ? O : 0).total;
+}
+
+int launch_rollout_mma_batched(const RolloutArgs* args, const MmaArgs* mms, const int2* items, int nitems,
+                               int fmt, int rps, int smem, cudaStream_t st) {
+    if (nitems == 0) return GPMPPI_OK;
+#define GPM_LAUNCH_MMA_B(F, RR)                                                                   \
+    do {                                                                                          \
+        auto kern = k_rollout_mma_batched<F, RR>;                                                 \
+        GPM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));  \
+        kern<<<nitems, THREADS, smem, st>>>(args, mms, items);                                    \
+    } while (0)
+    if (fmt == 0) {
+        if (rps == 2) GPM_LAUNCH_MMA_B(0, 2); else if (rps == 4) GPM_LAUNCH_MMA_B(0, 4); else GPM_LAUNCH_MMA_B(0, 8);
+    } else {
+        if (rps == 2) GPM_LAUNCH_MMA_B(1, 2); else if (rps == 4) GPM_LAUNCH_MMA_B(1, 4); else GPM_LAUNCH_MMA_B(1, 8);
+    }
+#undef GPM_LAUNCH_MMA_B
     GPM_CUDA(cudaGetLastError());
     return GPMPPI_OK;
 }

@@ -1,0 +1,110 @@
+"""Batched iterations of many independent controllers (uneven K, T, N,
+obstacles, paths and precisions) against the FP64 oracle, against individual
+mppi_step calls, through CUDA-graph replay and after autotuning."""
+import numpy as np
+import pytest
+
+import oracle as O
+import scenarios as S
+from parity import TOL_U, check_step, make_ctrl, to_np
+
+pytestmark = pytest.mark.gpu
+
+SPECS = [  # (K, T, N, O, path, precision, seed)
+    (300, 7, 200, 6, "eight", 2, 11),
+    (77, 5, 45, 3, "sine", 2, 12),
+    (513, 9, 333, 10, "straight", 2, 13),
+    (129, 4, 0, 0, "eight", 2, 14),
+    (260, 6, 140, 5, "sine", 1, 15),
+    (200, 8, 90, 4, "eight", 0, 16),
+]
+
+
+def _scenarios():
+    out = []
+    for K, T, N, O_, path, prec, seed in SPECS:
+        sc = S.scenario("small", K=K, T=T, N=N, O=O_, path=path, precision=prec, seed=seed)
+        rng = np.random.default_rng(seed)
+        x0 = sc.x0.copy()
+        x0[3] = 0.5 + rng.random()
+        U = np.tile([sc.params.v_desired, 0.0], (T, 1))
+        U[:, 1] = 0.4 * np.sin(np.arange(T) + seed)
+        out.append((sc, x0, U))
+    return out
+
+
+def _batch(lib):
+    import torch
+    items = _scenarios()
+    ctrls = [make_ctrl(lib, sc)[1] for sc, _, _ in items]
+    b = lib.mppi_batch_create(ctrls)
+    for i, (sc, x0, U) in enumerate(items):
+        b.state[i].copy_(torch.tensor(x0, dtype=torch.float32))
+        b.U_nom[i].copy_(torch.tensor(U, dtype=torch.float32))
+    return b, ctrls, items
+
+
+def test_batch_matches_oracle_and_single_steps(lib):
+    import torch
+    b, ctrls, items = _batch(lib)
+    lib.mppi_batch_step(b)
+    torch.cuda.synchronize()
+    for i, (sc, x0, U) in enumerate(items):
+        fits = O.gp_fit(sc.X, sc.Y, sc.hyper)
+        ro = O.rollout(sc, fits, x0.astype(np.float32).astype(np.float64), U, 0)
+        info = check_step(sc, ro, U, to_np(b.U_new[i]), to_np(b.weights[i]), to_np(b.costs[i]))
+        assert lib.mppi_batch_get_iteration(b, i) == 1
+        # the same controller stepped on its own
+        Ud = torch.tensor(U, dtype=torch.float32, device="cuda")
+        U1 = torch.empty_like(Ud)
+        w1 = torch.empty(sc.params.K, device="cuda")
+        c1 = torch.empty_like(w1)
+        lib.mppi_set_iteration(ctrls[i], 0)
+        lib.mppi_step(ctrls[i], x0, Ud, U1, w1, c1)
+        torch.cuda.synchronize()
+        assert np.max(np.abs(to_np(U1) - to_np(b.U_new[i]))) <= TOL_U
+        np.testing.assert_allclose(to_np(c1), to_np(b.costs[i]), rtol=1e-5, atol=1e-5)
+        print(i, info)
+
+
+def test_batch_graph_replay_equals_steps(lib):
+    import torch
+    b1, _, _ = _batch(lib)
+    b2, _, _ = _batch(lib)
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        for _ in range(3):
+            lib.mppi_batch_step(b1, st)
+            lib.mppi_batch_graph(b2, st)
+    st.synchronize()
+    for i in range(len(SPECS)):
+        assert np.array_equal(to_np(b1.U_new[i]), to_np(b2.U_new[i]))
+        assert np.array_equal(to_np(b1.costs[i]), to_np(b2.costs[i]))
+        assert lib.mppi_batch_get_iteration(b2, i) == 3
+
+
+def test_batch_autotune_keeps_parity(lib):
+    import torch
+    b, ctrls, items = _batch(lib)
+    chosen = lib.mppi_batch_autotune(b)
+    assert chosen in (2, 4, 8)
+    assert all(lib.mppi_batch_get_iteration(b, i) == 0 for i in range(len(SPECS)))
+    lib.mppi_batch_step(b)
+    torch.cuda.synchronize()
+    for i, (sc, x0, U) in enumerate(items):
+        fits = O.gp_fit(sc.X, sc.Y, sc.hyper)
+        ro = O.rollout(sc, fits, x0.astype(np.float32).astype(np.float64), U, 0)
+        check_step(sc, ro, U, to_np(b.U_new[i]), to_np(b.weights[i]), to_np(b.costs[i]))
+
+
+def test_batch_rejects_bad_groups(lib):
+    sc = S.scenario("small")
+    g, c = make_ctrl(lib, sc)
+    with pytest.raises(lib.GpmppiError) as ei:
+        lib.mppi_batch_create([c, c])
+    assert ei.value.code == lib.GPMPPI_ERR_INVALID_ARG
+    sc2 = S.scenario("small", variance_mode=1)
+    g2, c2 = make_ctrl(lib, sc2)
+    with pytest.raises(lib.GpmppiError) as ei:
+        lib.mppi_batch_create([c, c2])
+    assert ei.value.code == lib.GPMPPI_ERR_UNSUPPORTED
