@@ -20,6 +20,9 @@ Parity status per function (the pins live in ``tests/test_oracle_*.py``):
   costs / tightening ....... pinned (quantile closed forms, scipy, eigvalsh,
                               hand-computable straight-path cases)
   weights / update ......... pinned (sum to one, temperature limits, K=1)
+  smoothed objective / gradient ... pinned (Richardson agreement, the
+                              straight-line analytic gradient, sigmoid ->
+                              indicator as the slope grows)
   nominal tightening mode .. parity unpinned beyond the zero-noise identity
                               with the per-sample mode (the placement of
                               Alg. 1 Step 2 is a reading, not a definition)
@@ -33,3 +36,4 @@ from .mppi import (  # noqa: F401
     stage_cost, rollout, mppi_weights, mppi_update, mppi_step, nominal_tightening,
     Controller,
 )
+from .gradient import objective, fd_gradient, with_lengthscale  # noqa: F401

@@ -111,8 +111,16 @@ def tightening_constants(p_x):
     return np.sqrt(chi2_2_quantile(p_x)), normal_quantile(p_x)
 
 
-def stage_cost(k, mu, Sxy, var, sc, consts):
+def sigmoid(x):
+    return 0.5 * (1.0 + np.tanh(0.5 * np.asarray(x, dtype=np.float64)))
+
+
+def stage_cost(k, mu, Sxy, var, sc, consts, slope=None):
     """Stage cost c_track + c_avoidance at stage k.
+
+    slope=None uses the indicators of Eq. 11-12; a positive slope replaces
+    them by logistic sigmoids of slope * margin (lane) and -slope * margin
+    (collision), the smooth surrogate the gradient is taken of.
 
     mu (S,5) is the state after the update of step k, Sxy (S,2,2) the
     position covariance used for tightening, var (S,2) the GP variance of
@@ -128,7 +136,7 @@ def stage_cost(k, mu, Sxy, var, sc, consts):
     r_bar = r - sq_chi2 * np.sqrt(lmax)                       # Eq. 14
     e = lane_distance(mu[:, :2], sc.path)
     lane_margin = e - r_bar
-    lane_viol = (lane_margin > 0.0).astype(np.float64)
+    lane_viol = (lane_margin > 0.0).astype(np.float64) if slope is None else sigmoid(slope * lane_margin)
     a = P.alpha
     cost = (a[0] * trC + a[1] * e / r
             + a[3] * P.P_lane * LANE_DISCOUNT ** k * lane_viol      # Eq. 11
@@ -147,7 +155,10 @@ def stage_cost(k, mu, Sxy, var, sc, consts):
         obs_margin = np.min(d_bar, axis=1)
     else:
         obs_margin = np.full(mu.shape[0], np.inf)
-    coll = (obs_margin <= 0.0).astype(np.float64)
+    if slope is None:
+        coll = (obs_margin <= 0.0).astype(np.float64)
+    else:
+        coll = sigmoid(-slope * obs_margin) if O > 0 else np.zeros_like(obs_margin)
     b = P.beta
     cost = cost + b[0] * trC + b[1] * P.P_coll * coll                 # Eq. 12
     return cost, lane_margin, obs_margin
@@ -162,7 +173,7 @@ def _check_params(P):
         raise ValueError("slip (alpha_2) and goal terms (beta_2, beta_3) are not modelled")
 
 
-def rollout(sc, fits, state, U, it, samples=None, nominal_sxy=None, noise=True):
+def rollout(sc, fits, state, U, it, samples=None, nominal_sxy=None, noise=True, slope=None):
     """Alg. 1 Step 1 for the listed samples (all K by default).
 
     state (5,), U (T,2), it the MPPI iteration (Philox counter words 2-3).
@@ -196,7 +207,7 @@ def rollout(sc, fits, state, U, it, samples=None, nominal_sxy=None, noise=True):
         mu[:, 4] += m[:, 1]
         Sig = covariance_step(Sig, A, var)                                # Eq. 10
         Sxy = Sig[:, :2, :2] if nominal_sxy is None else np.broadcast_to(nominal_sxy[k], (S, 2, 2))
-        c, lm, om = stage_cost(k, mu, Sxy, var, sc, consts)
+        c, lm, om = stage_cost(k, mu, Sxy, var, sc, consts, slope)
         out["costs"] += c
         out["u_tilde"][:, k] = ut
         out["mu"][:, k] = mu
