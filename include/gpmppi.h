@@ -191,6 +191,36 @@ int mppi_device_status(gpmppi_ctrl c);
 /* Release a controller and its device buffers (synchronises its device). */
 int mppi_destroy(gpmppi_ctrl c);
 
+/* Gradient of the smoothed chance-constrained rollout cost (adjoint rollout).
+ * J(U, l) = sum_s w_s S_s, where S_s is the cost of sample s over the horizon
+ * (Alg. 1 Step 1: Eq. 6 and 10 for mean and covariance, Eq. 11-16 for the
+ * stage cost) with the lane and collision indicators of Eq. 11-12 replaced by
+ * logistic sigmoids of slope * (e - r_bar) and -slope * min_j d_bar_j, and the
+ * control noise fixed at the draws of the controller's current iteration
+ * (the counter is not advanced).  The gradient is exact for that smoothed
+ * cost up to FP32 rounding, taken by a reverse pass over the horizon that
+ * stores the state every ceil(sqrt(T)) steps and recomputes each segment;
+ * derivatives of sqrt(lambda_max) and sqrt(n^T Sigma n) are taken as zero
+ * where their argument is zero (Sigma_XY(1) = 0), and those of the clamps
+ * (Eq. 8, the variance at zero) as zero outside the box.
+ *   state          host, 5 floats (x0)
+ *   U_nom          device, T x 2 floats
+ *   sample_weights device, K floats w_s, or NULL for w_s = 1/K
+ *   slope          sigmoid slope > 0 (20 in the differentiable workload)
+ *   J              device, 1 float (output)
+ *   dU             device, T x 2 floats dJ/dU (output), or NULL to evaluate J only
+ *   dlengthscale   device, 2 x 4 floats dJ/dl_{o,d} for output o (v, omega) and
+ *                  GP input d (output), or NULL.  It includes the dependence of
+ *                  alpha = K^-1 y and K^-1 on the lengthscales (one more kernel
+ *                  and T * K * N floats of scratch)
+ * Needs variance mode GPMPPI_VAR_PER_SAMPLE (else GPMPPI_ERR_UNSUPPORTED) and
+ * enough shared memory for 2 x 8 x N floats (GPMPPI_ERR_UNSUPPORTED beyond).
+ * The first call, and the first call asking for dlengthscale, allocate
+ * device scratch owned by the controller (freed by mppi_destroy) and may
+ * synchronise.  Runs on the controller's FP32 path whatever its precision. */
+int mppi_grad(gpmppi_ctrl c, const float state[5], const float* U_nom, const float* sample_weights,
+              float slope, float* J, float* dU, float* dlengthscale, void* stream);
+
 /* Allocation-free weights-and-update step (the paper has no counterpart;
  * this is a deployment aid).  Some callers cannot allocate device memory
  * once running: a controller in a real-time loop whose memory is fixed at

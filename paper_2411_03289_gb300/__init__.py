@@ -35,7 +35,8 @@ GPMPPI_FP16_SPLIT = 2
 # names every build of the library exports (checked by the CPU test suite)
 EXPORTS = ("gp_fit", "gp_destroy", "gp_factors", "gp_predict", "mppi_create", "mppi_step",
            "mppi_rollout_trace", "mppi_set_iteration", "mppi_get_iteration", "mppi_nominal_sxy",
-           "mppi_destroy", "mppi_set_profiling", "mppi_last_profile", "mppi_device_status", "mppi_update_noalloc", "mppi_batch_create",
+           "mppi_destroy", "mppi_set_profiling", "mppi_last_profile", "mppi_device_status", "mppi_grad",
+           "mppi_update_noalloc", "mppi_batch_create",
            "mppi_batch_buffers", "mppi_batch_step", "mppi_batch_graph", "mppi_batch_autotune",
            "mppi_batch_get_iteration", "mppi_batch_destroy", "gpmppi_philox", "gpmppi_control_noise", "gpmppi_mma_selftest", "gpmppi_last_error",
            "gpmppi_version")
@@ -92,6 +93,7 @@ def load():
         "mppi_set_profiling": [vp, i32],
         "mppi_last_profile": [vp, vp, vp],
         "mppi_device_status": [vp],
+        "mppi_grad": [vp, vp, vp, vp, ctypes.c_float, vp, vp, vp, vp],
         "mppi_batch_create": [vp, i32, ctypes.POINTER(vp)],
         "mppi_batch_buffers": [vp, i32, vp, vp, vp, vp, vp],
         "mppi_batch_step": [vp, vp],
@@ -186,8 +188,8 @@ def make_params(p) -> Params:
 class GP:
     """Owning wrapper of a gpmppi_gp handle."""
 
-    def __init__(self, handle, N):
-        self.handle, self.N = handle, N
+    def __init__(self, handle, N, hyper=None):
+        self.handle, self.N, self.hyper = handle, N, hyper
 
     def __del__(self):
         if getattr(self, "handle", None) and _lib is not None:
@@ -217,7 +219,7 @@ def gp_fit(X, Y, hyper) -> GP:
     h = ctypes.c_void_p()
     _check(lib.gp_fit(X.ctypes.data_as(ctypes.c_void_p), Y.ctypes.data_as(ctypes.c_void_p),
                       X.shape[0], ctypes.cast(hy, ctypes.c_void_p), ctypes.byref(h)))
-    return GP(h.value, X.shape[0])
+    return GP(h.value, X.shape[0], hyper)
 
 
 def gp_destroy(gp: GP):
@@ -312,6 +314,83 @@ def mppi_destroy(ctrl: Ctrl):
     if ctrl.handle:
         _check(load().mppi_destroy(ctrl.handle))
         ctrl.handle = None
+
+
+def mppi_grad(ctrl: Ctrl, state, U_nom, slope=20.0, weights=None, J=None, dU=None, dl=None,
+              want_dU=True, want_dl=True, stream=None):
+    """Smoothed rollout cost J and its adjoint gradients dJ/dU (T,2) and
+    dJ/dl (2,4) (see mppi_grad in the C header).  Returns (J, dU, dl) as CUDA
+    tensors; dU / dl are None when not requested."""
+    import torch
+    dev = U_nom.device
+    if J is None:
+        J = torch.empty(1, dtype=torch.float32, device=dev)
+    if want_dU and dU is None:
+        dU = torch.empty(ctrl.T, 2, dtype=torch.float32, device=dev)
+    if want_dl and dl is None:
+        dl = torch.empty(2, 4, dtype=torch.float32, device=dev)
+    if not want_dU:
+        dU, dl = None, None
+    if not want_dl:
+        dl = None
+    st = _f32(state).reshape(5)
+    _check(load().mppi_grad(ctrl.handle, st.ctypes.data_as(ctypes.c_void_p),
+                            _dptr(U_nom, torch.float32, 2 * ctrl.T, "U_nom"),
+                            _dptr(weights, torch.float32, ctrl.K, "weights"), float(slope),
+                            _dptr(J, torch.float32, 1, "J"),
+                            _dptr(dU, torch.float32, 2 * ctrl.T, "dU"),
+                            _dptr(dl, torch.float32, 8, "dl"), _stream(stream)))
+    return J, dU, dl
+
+
+def _make_autograd():
+    import torch
+
+    class SmoothedRolloutCost(torch.autograd.Function):
+        """J(U, l) of mppi_grad as a differentiable op.  The adjoint kernel
+        returns the gradients in the same pass as J, so forward computes them
+        (only those whose inputs require grad) and backward scales them."""
+
+        @staticmethod
+        def forward(ctx, U, lengthscale, ctrl, state, slope, weights):
+            need_u = ctx.needs_input_grad[0]
+            need_l = ctx.needs_input_grad[1]
+            J, dU, dl = mppi_grad(ctrl, state, U.detach().contiguous(), slope, weights,
+                                  want_dU=need_u or need_l, want_dl=need_l)
+            ctx.save_for_backward(dU if dU is not None else torch.zeros_like(U),
+                                  dl if dl is not None else torch.zeros(2, 4, device=U.device))
+            return J.reshape(())
+
+        @staticmethod
+        def backward(ctx, gJ):
+            dU, dl = ctx.saved_tensors
+            return gJ * dU, gJ * dl, None, None, None, None
+
+    return SmoothedRolloutCost
+
+
+_AUTOGRAD = None
+
+
+def smoothed_rollout_cost(ctrl: Ctrl, state, U, lengthscale=None, slope=20.0, weights=None):
+    """Differentiable smoothed chance-constrained rollout cost (torch scalar).
+
+    U (T,2) CUDA tensor; lengthscale (2,4) CUDA tensor equal to the lengthscales
+    the controller's GP was fitted with (refit and recreate the controller to
+    move them), or None.  Gradients flow to whichever of U / lengthscale
+    requires grad."""
+    import torch
+    global _AUTOGRAD
+    if _AUTOGRAD is None:
+        _AUTOGRAD = _make_autograd()
+    if lengthscale is None:
+        lengthscale = torch.tensor([list(h.lengthscale) for h in ctrl.gp.hyper],
+                                   dtype=torch.float32, device=U.device)
+    elif ctrl.gp.hyper is not None:
+        fitted = np.array([list(h.lengthscale) for h in ctrl.gp.hyper], dtype=np.float32)
+        if not np.allclose(lengthscale.detach().cpu().numpy(), fitted, rtol=1e-6, atol=0):
+            raise ValueError("lengthscale differs from the fitted GP's; refit the GP first")
+    return _AUTOGRAD.apply(U, lengthscale, ctrl, state, float(slope), weights)
 
 
 def mppi_update_noalloc(costs, u_tilde, U_nom, U_new, weights, K: int, T: int, lam: float,

@@ -98,6 +98,8 @@ void free_gp(gpmppi_gp h) {
         cudaFree(g.mma_hi[f]);
         cudaFree(g.mma_lo[f]);
     }
+    cudaFree(g.Wt);
+    cudaFree(g.ubar);
     if (!g.shared) {
         cudaFree(g.Xs[1]);
         cudaFree(g.W[1]);
@@ -118,6 +120,7 @@ void free_ctrl(gpmppi_ctrl c) {
     cudaFree(c->counter);
     cudaFree(c->nom_sxy);
     cudaFree(c->err);
+    cudaFree(c->grad_scr);
     for (cudaEvent_t e : c->ev)
         if (e) cudaEventDestroy(e);
     if (c->gp && c->gp->magic == kGpMagic) c->gp->g.n_controllers--;
@@ -529,6 +532,123 @@ int mppi_rollout_trace(gpmppi_ctrl c, const float state[5], const float* U_nom, 
     a.tr_margin = margins;
     if (c->fmt >= 0) return launch_rollout_mma(a, c->mm, c->fmt, true, (cudaStream_t)stream);
     return launch_rollout_fp32(a, &c->tmW, true, (cudaStream_t)stream);
+}
+
+int mppi_grad(gpmppi_ctrl c, const float state[5], const float* U_nom, const float* sample_weights,
+              float slope, float* J, float* dU, float* dlengthscale, void* stream) {
+    if (!valid_ctrl(c)) return fail(GPMPPI_ERR_INVALID_ARG, "mppi_grad: invalid handle");
+    int rc;
+    if ((rc = check_ctrl_device(c))) return rc;
+    if ((rc = check_state(state))) return rc;
+    if ((rc = check_dev_ptr(U_nom, "mppi_grad: U_nom", false))) return rc;
+    if ((rc = check_dev_ptr(sample_weights, "mppi_grad: sample_weights", true))) return rc;
+    if ((rc = check_dev_ptr(J, "mppi_grad: J", false))) return rc;
+    if ((rc = check_dev_ptr(dU, "mppi_grad: dU", true))) return rc;
+    if ((rc = check_dev_ptr(dlengthscale, "mppi_grad: dlengthscale", true))) return rc;
+    if (!(slope > 0.0f) || !is_finite(slope)) return fail(GPMPPI_ERR_INVALID_ARG, "mppi_grad: slope must be > 0");
+    if (dlengthscale && !dU)
+        return fail(GPMPPI_ERR_INVALID_ARG, "mppi_grad: dlengthscale needs dU");
+    if (c->p.variance_mode != GPMPPI_VAR_PER_SAMPLE)
+        return fail(GPMPPI_ERR_UNSUPPORTED, "mppi_grad: needs the per-sample variance mode");
+    GpDevice& g = c->gp->g;
+    const int K = c->p.K, T = c->p.T, Np = g.Np, N = g.N;
+    int C = (int)std::ceil(std::sqrt((double)T));
+    if (C < 1) C = 1;
+    const int nseg = (T + C - 1) / C;
+    const int gm = grad_samples_per_cta();
+    const int ncta = (K + gm - 1) / gm;
+    const int Kpad = ncta * gm;
+    int optin = 0;
+    GPM_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
+    if (grad_smem_bytes(Np, C) > optin)
+        return fail(GPMPPI_ERR_UNSUPPORTED, "mppi_grad: GP too large for the adjoint kernel's shared memory");
+    int nsm = 0;
+    GPM_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool want_l = dlengthscale != nullptr;
+    // per-GP factors of the adjoint, built once
+    if (!g.Wt) {
+        GPM_CUDA(cudaMalloc(&g.Wt, sizeof(float) * (size_t)Np * Np));
+        if ((rc = launch_transpose(g.W[0], Np, g.Wt, st))) return rc;
+        GPM_CUDA(cudaStreamSynchronize(st));
+    }
+    if (want_l && !g.ubar) {
+        GPM_CUDA(cudaMalloc(&g.ubar, sizeof(float) * 8 * (size_t)Np));
+        if ((rc = launch_dk_alpha(g.Xs[0], g.alpha, N, Np, g.sf2[0], g.ubar, st))) return rc;
+        GPM_CUDA(cudaStreamSynchronize(st));
+    }
+    // scratch layout (bytes, each piece 256-aligned)
+    const int Q = T * Kpad;
+    int nsplit = 1;
+    const int pairs = gram_trace_blocks(Np, 1);
+    while (pairs * nsplit < 4 * nsm && Q / (nsplit * 2) >= 256) nsplit *= 2;
+    const int nparts = want_l ? gram_trace_blocks(Np, nsplit) : 0;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off += (bytes + 255) & ~(size_t)255;
+        return o;
+    };
+    const size_t o_v = take(sizeof(float) * (size_t)ncta * C * Np * gm);
+    const size_t o_ck = take(sizeof(float) * (size_t)ncta * nseg * gm * 20);
+    const size_t o_S = take(sizeof(float) * (size_t)K);
+    const size_t o_dU = take(sizeof(float) * (size_t)2 * T * K);
+    const size_t o_dl = take(sizeof(float) * (size_t)8 * K);
+    size_t o_B = 0, o_q = 0, o_p = 0;
+    if (want_l) {
+        o_B = take(sizeof(float) * (size_t)Q * Np);
+        o_q = take(sizeof(float4) * (size_t)Q);
+        o_p = take(sizeof(float) * 8 * (size_t)nparts);
+    }
+    if (off > c->grad_bytes) {
+        cudaFree(c->grad_scr);
+        c->grad_scr = nullptr;
+        c->grad_bytes = 0;
+        GPM_CUDA(cudaMalloc(&c->grad_scr, off));
+        c->grad_bytes = off;
+    }
+    char* base = static_cast<char*>(c->grad_scr);
+    GradArgs ga;
+    std::memset(&ga, 0, sizeof(ga));
+    ga.r = make_rollout_args(c, state, U_nom);
+    ga.r.nom_sxy = nullptr;
+    ga.Wt = g.Wt;
+    ga.ubar = want_l ? g.ubar : nullptr;
+    ga.weight = sample_weights;
+    ga.slope = slope;
+    ga.inv_K = 1.0f / (float)K;
+    ga.C = C;
+    ga.nseg = nseg;
+    ga.Kpad = Kpad;
+    ga.backward = dU ? 1 : 0;
+    ga.vscr = reinterpret_cast<float*>(base + o_v);
+    ga.ckpt = reinterpret_cast<float*>(base + o_ck);
+    ga.S_out = reinterpret_cast<float*>(base + o_S);
+    ga.dU_out = reinterpret_cast<float*>(base + o_dU);
+    ga.dl_out = want_l ? reinterpret_cast<float*>(base + o_dl) : nullptr;
+    ga.Bq = want_l ? reinterpret_cast<float*>(base + o_B) : nullptr;
+    ga.qbar = want_l ? reinterpret_cast<float4*>(base + o_q) : nullptr;
+    if ((rc = launch_grad(ga, ncta, st))) return rc;
+    if (want_l &&
+        (rc = launch_gram_trace(ga.Bq, ga.qbar, Q, Np, N, g.Xs[0], g.sf2[0], nsplit,
+                                reinterpret_cast<float*>(base + o_p), st)))
+        return rc;
+    GradReduceArgs rr;
+    std::memset(&rr, 0, sizeof(rr));
+    rr.dU_out = ga.dU_out;
+    rr.S_out = ga.S_out;
+    rr.dl_out = ga.dl_out;
+    rr.parts = want_l ? reinterpret_cast<float*>(base + o_p) : nullptr;
+    rr.nparts = nparts;
+    rr.weight = sample_weights;
+    rr.inv_K = ga.inv_K;
+    rr.K = K;
+    rr.T = dU ? T : 0;
+    rr.dU = dU;
+    rr.J = J;
+    rr.dl = dlengthscale;
+    for (int d = 0; d < 4; ++d) rr.ell[d] = (float)g.hyper[0].lengthscale[d];
+    return launch_grad_reduce(rr, st);
 }
 
 int mppi_set_iteration(gpmppi_ctrl c, uint64_t it) {

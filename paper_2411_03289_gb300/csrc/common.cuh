@@ -119,6 +119,10 @@ struct GpDevice {
     uint16_t* mma_lo[2] = {nullptr, nullptr};
     float mma_cB = 0.0f;
     int NpM = 0;
+    // adjoint rollout, built on first use: rows of L^-1 (Np x Np) and the
+    // vectors (dK/dl_d) alpha_o (8 x Np)
+    float* Wt = nullptr;
+    float* ubar = nullptr;
     gpmppi_hyper hyper[2];
     int n_controllers = 0;
 };
@@ -178,6 +182,40 @@ struct MmaArgs {
     int scene_smem;         // lane segments and obstacles staged in shared memory
 };
 
+// Adjoint rollout (gradient of the smoothed cost); see adjoint.cu.
+struct GradArgs {
+    RolloutArgs r;          // scene, GP, controls and constants of the controller
+    const float* Wt;        // Np x Np rows of L^-1 (zero above the diagonal and in the padding)
+    const float* ubar;      // 8 x Np: (dK/dl_d) alpha_o / (2 ln2 / l_d), row o*4+d; null: no K terms
+    const float* weight;    // K sample weights, or null for 1/K
+    float slope;            // sigmoid slope of the smoothed indicators
+    float inv_K;
+    int C, nseg, Kpad;      // checkpoint interval, segments, CTAs x samples per CTA
+    int backward;           // 0: objective only
+    float* vscr;            // n_cta x C x Np x 8: v = L^-1 k* of the current segment
+    float* ckpt;            // n_cta x nseg x 8 x 20: (mu, Sigma) at the segment starts
+    float* S_out;           // K smoothed rollout costs
+    float* dU_out;          // 2T x K per-sample control adjoints (weighted)
+    float* dl_out;          // 8 x K per-sample lengthscale terms, or null
+    float* Bq;              // (T Kpad) x Np: b = K^-1 k* per query, or null
+    float4* qbar;           // T Kpad: (mbar_v, mbar_w, sbar_v, sbar_w) per query
+};
+
+struct GradReduceArgs {
+    const float* dU_out;
+    const float* S_out;
+    const float* dl_out;
+    const float* parts;     // nparts x 8 Gram-trace partials
+    int nparts;
+    const float* weight;
+    float inv_K;
+    int K, T;
+    float* dU;              // T x 2
+    float* J;               // 1
+    float* dl;              // 2 x 4, or null
+    float ell[4];
+};
+
 struct UpdateArgs {
     const float* costs;     // K
     const float2* u_tilde;  // T x K
@@ -218,5 +256,15 @@ int build_mma_tiles(GpDevice& g, int fmt);
 int launch_mma_selftest(int fmt, int N, int K, int variant, const uint16_t* A, const uint16_t* B,
                         float* D, unsigned int* err, cudaStream_t st);
 int rollout_fp32_mtp(int Np);
+int grad_smem_bytes(int Np, int C);
+int grad_samples_per_cta();
+int launch_grad(const GradArgs& g, int ncta, cudaStream_t st);
+int launch_gram_trace(const float* Bq, const float4* qbar, int Q, int Np, int N, const float* Xs,
+                      float sf2, int nsplit, float* part, cudaStream_t st);
+int gram_trace_blocks(int Np, int nsplit);
+int launch_dk_alpha(const float* Xs, const float* alpha, int N, int Np, float sf2, float* ubar,
+                    cudaStream_t st);
+int launch_transpose(const float* W, int Np, float* Wt, cudaStream_t st);
+int launch_grad_reduce(const GradReduceArgs& r, cudaStream_t st);
 
 }  // namespace gpm

@@ -34,6 +34,9 @@ struct gpmppi_ctrl_s {
     CUtensorMap tmW;              // TMA map over the GP's W
     gpm::MmaArgs mm{};              // tensor-core tiles (split precisions)
     int fmt = -1;                 // 0 = FP16, 1 = BF16 split, -1 = FP32 path
+    // adjoint-rollout scratch (allocated by the first mppi_grad call)
+    void* grad_scr = nullptr;
+    size_t grad_bytes = 0;
     bool profiling = false;
     bool profiled = false;
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
