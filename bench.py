@@ -415,6 +415,175 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+GRAD_SLOPE = 20.0
+GRAD_CPU_ROWS = 4
+
+
+def grad_flops_per_sample_step(N, O, S):
+    """Algorithmic FP32 flops of the adjoint kernel per sample-step: the
+    forward rollout (as above), the second triangular product b = L^-T v
+    (N(N+1)), 60N for the GP adjoint row (kernel row, weights, z and
+    lengthscale accumulators, the (dK/dl) alpha terms), 10 per lane segment
+    and 30 per obstacle for the cost adjoint, 400 for the covariance and mean
+    adjoints.  The recomputation of each checkpointed segment is not counted."""
+    return rollout_flops_per_sample_step(N, O, S) + N * (N + 1) + 60 * N + 10 * S + 30 * O + 400
+
+
+def _grad_cpu_child(rows):
+    import numpy as np
+    import oracle as O
+    import scenarios as S
+    sc = S.scenario("cfg4")
+    U = sc.U0.copy()
+    U[:, 1] = 0.4 * np.sin(np.arange(sc.params.T) / 6.0)
+    t0 = time.perf_counter()
+    O.fd_gradient(sc, sc.hyper, sc.x0, U, 0, list(range(rows)), GRAD_SLOPE, h_u=1e-3, h_l=1e-3)
+    dt = time.perf_counter() - t0
+    print(json.dumps({"seconds": dt, "sample_steps": rows * sc.params.T}))
+
+
+def grad_cpu_baseline(rows=GRAD_CPU_ROWS):
+    cores = os.cpu_count() or 1
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = str(cores)
+    cmd = [sys.executable, os.path.abspath(__file__), "--grad-cpu-child", str(rows)]
+    out = subprocess.run(cmd, capture_output=True, text=True, env=env, cwd=ROOT, timeout=900)
+    line = [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
+    if out.returncode != 0 or not line:
+        return {"value": None, "unit": "sample-steps/s", "cores": cores, "kind": "oracle",
+                "sample": f"failed: {out.stderr.strip()[-200:]}"}
+    d = json.loads(line[-1])
+    return {"value": d["sample_steps"] / d["seconds"], "unit": "sample-steps/s", "cores": cores,
+            "kind": "oracle",
+            "sample": f"FP64 oracle gradient (central differences, h=1e-3, all 100 control and 8 "
+                      f"lengthscale components) of the objective over {rows} of the K samples x T=50 "
+                      f"({d['seconds']:.1f} s), BLAS threads = {cores}"}
+
+
+def run_grad(args):
+    """cfg4: one step = one mppi_grad call (smoothed cost J, dJ/dU (T x 2) and
+    dJ/dl (2 x 4)) over all K samples."""
+    import numpy as np
+    import torch
+
+    import paper_2411_03289_gb300 as gp
+    import scenarios as S
+    from paper_2411_03289_gb300 import build as B
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    B.build()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    sc = S.scenario("cfg4", seed=1 + rank)
+    P = sc.params
+    g = gp.gp_fit(sc.X, sc.Y, sc.hyper)
+    ctrl = gp.mppi_create(P, sc.obstacles, sc.path, g)
+    U0 = sc.U0.copy()
+    U0[:, 1] = 0.4 * np.sin(np.arange(P.T) / 6.0)
+    U = torch.tensor(U0, dtype=torch.float32, device=dev)
+    J = torch.empty(1, dtype=torch.float32, device=dev)
+    dU = torch.empty(P.T, 2, dtype=torch.float32, device=dev)
+    dl = torch.empty(2, 4, dtype=torch.float32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    x0 = sc.x0.astype(np.float32)
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+
+    def one():
+        gp.mppi_grad(ctrl, x0, U, GRAD_SLOPE, None, J, dU, dl)
+
+    for _ in range(args.warmup):
+        one()
+        flush.fill_(1.0)
+    gp.mppi_set_profiling(ctrl, True)
+    torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    adj_ms, rest_ms = [], []
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        starts[i].record(stream)
+        one()
+        ends[i].record(stream)
+        a_ms, r_ms = gp.mppi_last_profile(ctrl)
+        adj_ms.append(a_ms)
+        rest_ms.append(r_ms)
+        flush.fill_(float(i))
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    gp.mppi_set_profiling(ctrl, False)
+    step_ms = [a.elapsed_time(b_) for a, b_ in zip(starts, ends)]
+    tot_ms = sum(step_ms)
+    # end to end: controls in from pinned host memory, J and both gradients out
+    U_host = torch.tensor(U0, dtype=torch.float32).pin_memory()
+    out_host = torch.empty(1 + 2 * P.T + 8, dtype=torch.float32).pin_memory()
+    e2e_s = 0.0
+    for i in range(max(3, args.steps // 4) + 3):
+        flush.fill_(float(i))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        U.copy_(U_host, non_blocking=True)
+        one()
+        out_host[:1].copy_(J, non_blocking=True)
+        out_host[1:1 + 2 * P.T].copy_(dU.view(-1), non_blocking=True)
+        out_host[1 + 2 * P.T:].copy_(dl.view(-1), non_blocking=True)
+        torch.cuda.synchronize()
+        if i >= 3:
+            e2e_s += time.perf_counter() - t0
+    n_e2e = max(3, args.steps // 4)
+    if ws > 1:
+        t = torch.tensor([tot_ms, e2e_s], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        tot_ms, e2e_s = float(t[0].item()), float(t[1].item())
+    if rank != 0:
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return
+    S_seg = max(sc.path.shape[0] - 1, 1)
+    flops = grad_flops_per_sample_step(sc.N, sc.obstacles.shape[0], S_seg) * P.K * P.T
+    a_avg = sum(adj_ms) / len(adj_ms)
+    achieved = flops / (a_avg / 1e3) / 1e12
+    peak = fp32_peak_tflops(2070.0)
+    units = P.K * P.T
+    line = {
+        "metric": METRIC, "value": units * args.steps * ws / (tot_ms / 1e3), "unit": "sample-steps/s",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_ms / args.steps,
+        "p50_ms": statistics.median(step_ms), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded GP training set, obstacles, figure-eight path)",
+        "config": {"workload": f"cfg4: K={P.K} T={P.T} N={sc.N} obstacles={sc.obstacles.shape[0]} figure-eight, "
+                               f"gradient of the sigmoid-smoothed cost (slope {GRAD_SLOPE:g}) in U and the "
+                               f"lengthscales, checkpoints every ceil(sqrt(T)) steps",
+                   "K": P.K, "T": P.T, "N": sc.N, "obstacles": int(sc.obstacles.shape[0]),
+                   "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)"},
+        "gpu_launches": 3 * args.steps,
+        "kernel_ms": {"adjoint_avg": a_avg, "gram_trace_and_reduce_avg": sum(rest_ms) / len(rest_ms)},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": committed_traffic("adjoint", "cfg4"),
+                     "kernel": "k_grad",
+                     "peak_note": "FP32 FMA pipe 152 SM x 128 lanes x 2 flops x 2070 MHz (derived)"},
+        "cpu_baseline": grad_cpu_baseline() if (ws == 1 and not args.no_cpu) else None,
+        "e2e": {"value": units * n_e2e * ws / e2e_s, "unit": "sample-steps/s",
+                "h2d_bytes_per_step": U_host.numel() * 4 + 20, "d2h_bytes_per_step": out_host.numel() * 4},
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
 def run_batched(args):
     """cfg5: 64 independent controllers (K, T, N, obstacles and paths all
     different) advanced together, one CUDA-graph replay per step."""
@@ -537,6 +706,9 @@ def main():
     if len(sys.argv) >= 2 and sys.argv[1] == "--cpu-child":
         _cpu_child(int(sys.argv[2]), int(sys.argv[3]))
         return
+    if len(sys.argv) >= 2 and sys.argv[1] == "--grad-cpu-child":
+        _grad_cpu_child(int(sys.argv[2]))
+        return
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=400)
@@ -557,6 +729,8 @@ def main():
         run_reference(args)
     elif args.workload == "cfg5":
         run_batched(args)
+    elif args.workload == "cfg4":
+        run_grad(args)
     else:
         run_ours(args)
 

@@ -178,7 +178,9 @@ int mppi_nominal_sxy(gpmppi_ctrl c, float* sxy, void* stream);
 /* Per-kernel timing of mppi_step.  When enabled, mppi_step records CUDA
  * events on its stream around the rollout kernel and around the update
  * kernel(s); mppi_last_profile waits for the last step's events and returns
- * the two durations in milliseconds (host floats).  Off by default. */
+ * the two durations in milliseconds (host floats).  mppi_grad records the
+ * same pair around its adjoint kernel and around the rest (Gram trace and
+ * reductions); the last call of either is reported.  Off by default. */
 int mppi_set_profiling(gpmppi_ctrl c, int32_t on);
 int mppi_last_profile(gpmppi_ctrl c, float* rollout_ms, float* update_ms);
 

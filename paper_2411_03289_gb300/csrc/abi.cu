@@ -628,7 +628,9 @@ int mppi_grad(gpmppi_ctrl c, const float state[5], const float* U_nom, const flo
     ga.dl_out = want_l ? reinterpret_cast<float*>(base + o_dl) : nullptr;
     ga.Bq = want_l ? reinterpret_cast<float*>(base + o_B) : nullptr;
     ga.qbar = want_l ? reinterpret_cast<float4*>(base + o_q) : nullptr;
+    if (c->profiling) GPM_CUDA(cudaEventRecord(c->ev[0], st));
     if ((rc = launch_grad(ga, ncta, st))) return rc;
+    if (c->profiling) GPM_CUDA(cudaEventRecord(c->ev[1], st));
     if (want_l &&
         (rc = launch_gram_trace(ga.Bq, ga.qbar, Q, Np, N, g.Xs[0], g.sf2[0], nsplit,
                                 reinterpret_cast<float*>(base + o_p), st)))
@@ -648,7 +650,12 @@ int mppi_grad(gpmppi_ctrl c, const float state[5], const float* U_nom, const flo
     rr.J = J;
     rr.dl = dlengthscale;
     for (int d = 0; d < 4; ++d) rr.ell[d] = (float)g.hyper[0].lengthscale[d];
-    return launch_grad_reduce(rr, st);
+    if ((rc = launch_grad_reduce(rr, st))) return rc;
+    if (c->profiling) {
+        GPM_CUDA(cudaEventRecord(c->ev[2], st));
+        c->profiled = true;
+    }
+    return GPMPPI_OK;
 }
 
 int mppi_set_iteration(gpmppi_ctrl c, uint64_t it) {

@@ -65,54 +65,100 @@ __device__ __forceinline__ float4 ldg4(const float* p) {
     return __ldg(reinterpret_cast<const float4*>(p));
 }
 
-// out[i * GMT + s] = sum_r in[r * GMT + s] * M[r * Np + i] for every column i < Np.
-// Thread t owns columns c0 + 4t .. c0 + 4t + 3 of each pass of 4 * GT columns.
-// LOWER = false: M holds rows of L^-T (M[r][i] = 0 for i < r), so a warp needs
-// rows up to its last column; LOWER = true: M holds rows of L^-1 (M[r][i] = 0
-// for i > r), so a warp needs rows from its first column on.  Both matrices
-// are zero-padded to Np x Np.  Called by all threads; no barrier inside.
-template <bool LOWER>
-__device__ void tri_product(const float* __restrict__ M, int Np, const float* in, float* out) {
-    const int tid = threadIdx.x, warp = tid >> 5;
-    for (int c0 = 0; c0 < Np; c0 += 4 * GT) {
-        const int wmin = c0 + 128 * warp;
-        if (wmin >= Np) continue;
-        const int wend = min(Np, wmin + 128);
-        const int col = c0 + 4 * tid;
-        const bool colok = col < Np;
-        const int r0 = LOWER ? wmin : 0;
-        const int r1 = LOWER ? Np : wend;
-        float acc[GMT][4];
+__device__ __forceinline__ float2 ldg2(const float* p) {
+    return __ldg(reinterpret_cast<const float2*>(p));
+}
+
+// Rows [r0, r1) of the product for the thread's two column pairs: LO / HI say
+// which of the pairs (at pl / ph) take part.  r0 and r1 are multiples of 16.
+template <bool LO, bool HI>
+__device__ __forceinline__ void tri_rows(int Np, const float* in, int r0, int r1, const float* pl,
+                                         const float* ph, bool okl, bool okh, float (&al)[GMT][2],
+                                         float (&ah)[GMT][2]) {
+    for (int r = r0; r < r1; r += 8) {
+        float2 ml[8], mh[8];
 #pragma unroll
-        for (int s = 0; s < GMT; ++s)
+        for (int u = 0; u < 8; ++u) {
+            if (LO) ml[u] = okl ? ldg2(pl + (size_t)(r + u) * Np) : make_float2(0.f, 0.f);
+            if (HI) mh[u] = okh ? ldg2(ph + (size_t)(r + u) * Np) : make_float2(0.f, 0.f);
+        }
 #pragma unroll
-            for (int c = 0; c < 4; ++c) acc[s][c] = 0.0f;
-        const float* mp = M + (colok ? col : 0);
-        for (int r = r0; r < r1; r += 8) {      // r0, r1 are multiples of 16
-            float4 m[8];
+        for (int u = 0; u < 8; ++u) {
+            const float4 x0 = *reinterpret_cast<const float4*>(in + (r + u) * GMT);
+            const float4 x1 = *reinterpret_cast<const float4*>(in + (r + u) * GMT + 4);
+            const float xs[GMT] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
 #pragma unroll
-            for (int u = 0; u < 8; ++u)
-                m[u] = colok ? ldg4(mp + (size_t)(r + u) * Np) : make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const float4 x0 = *reinterpret_cast<const float4*>(in + (r + u) * GMT);
-                const float4 x1 = *reinterpret_cast<const float4*>(in + (r + u) * GMT + 4);
-                const float xs[GMT] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
-#pragma unroll
-                for (int s = 0; s < GMT; ++s) {
-                    acc[s][0] = fmaf(xs[s], m[u].x, acc[s][0]);
-                    acc[s][1] = fmaf(xs[s], m[u].y, acc[s][1]);
-                    acc[s][2] = fmaf(xs[s], m[u].z, acc[s][2]);
-                    acc[s][3] = fmaf(xs[s], m[u].w, acc[s][3]);
+            for (int s = 0; s < GMT; ++s) {
+                if (LO) {
+                    al[s][0] = fmaf(xs[s], ml[u].x, al[s][0]);
+                    al[s][1] = fmaf(xs[s], ml[u].y, al[s][1]);
+                }
+                if (HI) {
+                    ah[s][0] = fmaf(xs[s], mh[u].x, ah[s][0]);
+                    ah[s][1] = fmaf(xs[s], mh[u].y, ah[s][1]);
                 }
             }
         }
-        if (colok) {
+    }
+}
+
+// out[i * GMT + s] = sum_r in[r * GMT + s] * M[r * Np + i] for every column i < Np.
+// LOWER = false: M holds rows of L^-T (M[r][i] = 0 for i < r), so column block
+// [b, b + 64) needs rows [0, b + 64); LOWER = true: M holds rows of L^-1
+// (M[r][i] = 0 for i > r), so it needs rows [b, Np).  Both matrices are
+// zero-padded to Np x Np.  Each pass covers 16 blocks of 64 columns; warp w
+// takes blocks w and 15 - w (lane l their columns 2l, 2l + 1), so that every
+// warp visits the same number of rows of either triangle.  Called by all
+// threads; no barrier inside.
+template <bool LOWER>
+__device__ void tri_product(const float* __restrict__ M, int Np, const float* in, float* out) {
+    constexpr int NBLK = 2 * (GT / 32);
+    constexpr int BW = 64;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int c0 = 0; c0 < Np; c0 += NBLK * BW) {
+        const int blo = c0 + BW * warp, bhi = c0 + BW * (NBLK - 1 - warp);
+        if (blo >= Np) continue;                  // then bhi >= Np too (warp-uniform)
+        const int clo = blo + 2 * lane, chi = bhi + 2 * lane;
+        const bool okl = clo < Np, okh = chi < Np;
+        const bool hi_any = bhi < Np;              // warp-uniform
+        float al[GMT][2], ah[GMT][2];
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                float4* o = reinterpret_cast<float4*>(out + (col + c) * GMT);
-                o[0] = make_float4(acc[0][c], acc[1][c], acc[2][c], acc[3][c]);
-                o[1] = make_float4(acc[4][c], acc[5][c], acc[6][c], acc[7][c]);
+        for (int s = 0; s < GMT; ++s) {
+            al[s][0] = al[s][1] = 0.0f;
+            ah[s][0] = ah[s][1] = 0.0f;
+        }
+        const float* pl = M + (okl ? clo : 0);
+        const float* ph = M + (okh ? chi : 0);
+        if (!LOWER) {
+            const int el = min(Np, blo + BW);
+            if (hi_any) {
+                tri_rows<true, true>(Np, in, 0, el, pl, ph, okl, okh, al, ah);
+                tri_rows<false, true>(Np, in, el, min(Np, bhi + BW), pl, ph, okl, okh, al, ah);
+            } else {
+                tri_rows<true, false>(Np, in, 0, el, pl, ph, okl, okh, al, ah);
+            }
+        } else {
+            if (hi_any) {
+                tri_rows<true, false>(Np, in, blo, bhi, pl, ph, okl, okh, al, ah);
+                tri_rows<true, true>(Np, in, bhi, Np, pl, ph, okl, okh, al, ah);
+            } else {
+                tri_rows<true, false>(Np, in, blo, Np, pl, ph, okl, okh, al, ah);
+            }
+        }
+        if (okl) {
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                float4* o = reinterpret_cast<float4*>(out + (clo + c) * GMT);
+                o[0] = make_float4(al[0][c], al[1][c], al[2][c], al[3][c]);
+                o[1] = make_float4(al[4][c], al[5][c], al[6][c], al[7][c]);
+            }
+        }
+        if (okh) {
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                float4* o = reinterpret_cast<float4*>(out + (chi + c) * GMT);
+                o[0] = make_float4(ah[0][c], ah[1][c], ah[2][c], ah[3][c]);
+                o[1] = make_float4(ah[4][c], ah[5][c], ah[6][c], ah[7][c]);
             }
         }
     }
@@ -127,7 +173,7 @@ struct StepInfo {
 // One forward step of sample s (warp w); all threads of the CTA call it.
 // mu / S are the warp's (lane-replicated) state, advanced in place.
 __device__ void fwd_step(const GradArgs& g, int k, int s, bool act, float mu[5], float S[15],
-                         float* kT, float* vT, float* vstore, StepInfo& inf) {
+                         float* kT, float* vT, float* vstore, StepInfo& inf, float* save) {
     const RolloutArgs& a = g.r;
     const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
     const int Np = a.Np;
@@ -154,9 +200,31 @@ __device__ void fwd_step(const GradArgs& g, int k, int s, bool act, float mu[5],
     }
     mv = wsum(mv + cv);
     mw = wsum(mw + cw);
+    // the warp's state waits in shared memory while the product runs, so that
+    // its registers are free for the product's tiles
+    if (lane == 0) {
+#pragma unroll
+        for (int i = 0; i < 5; ++i) save[i] = mu[i];
+#pragma unroll
+        for (int i = 0; i < 15; ++i) save[5 + i] = S[i];
+        save[20] = mv;
+        save[21] = mw;
+        save[22] = inf.ux;
+        save[23] = inf.uy;
+        save[24] = __int_as_float(inf.mask);
+    }
     __syncthreads();
     tri_product<false>(a.W, Np, kT, vT);
     __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 5; ++i) mu[i] = save[i];
+#pragma unroll
+    for (int i = 0; i < 15; ++i) S[i] = save[5 + i];
+    mv = save[20];
+    mw = save[21];
+    inf.ux = save[22];
+    inf.uy = save[23];
+    inf.mask = __float_as_int(save[24]);
     float q = 0.0f;
     for (int i = lane; i < Np; i += 32) {
         const float x = vT[i * GMT + w];
@@ -390,7 +458,10 @@ __device__ float stage_cost_adjoint(const GradArgs& g, int k, const float mu[5],
     return wt * a.c_var;
 }
 
-__global__ void __launch_bounds__(GT, 1) k_grad(const GradArgs g) {
+constexpr int SAVE = 40;     // per-warp spill area for state live across a product
+constexpr int CARRY = 28;    // per-warp adjoint carry: mu_bar (5), Sigma_bar (15), l_bar (8)
+
+__global__ void __launch_bounds__(GT, 2) k_grad(const GradArgs g) {
     extern __shared__ __align__(16) float gsm[];
     const RolloutArgs& a = g.r;
     const int Np = a.Np, C = g.C, T = a.T;
@@ -398,7 +469,11 @@ __global__ void __launch_bounds__(GT, 1) k_grad(const GradArgs g) {
     float* bufB = bufA + Np * GMT;
     float* rec = bufB + Np * GMT;                                   // (C + 1) x GMT x REC
     StepInfo* info = reinterpret_cast<StepInfo*>(rec + (C + 1) * GMT * REC);   // C x GMT
+    float* saves = reinterpret_cast<float*>(info + C * GMT);        // GMT x SAVE
+    float* carries = saves + GMT * SAVE;                            // GMT x CARRY
     const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+    float* save = saves + w * SAVE;
+    float* carry = carries + w * CARRY;
     const int s = blockIdx.x * GMT + w;
     const bool act = s < a.K;
     const float wt = act ? (g.weight ? __ldg(g.weight + s) : g.inv_K) : 0.0f;
@@ -421,19 +496,16 @@ __global__ void __launch_bounds__(GT, 1) k_grad(const GradArgs g) {
             for (int i = 0; i < 15; ++i) dst[5 + i] = S[i];
         }
         StepInfo inf;
-        fwd_step(g, k, s, act, mu, S, bufA, bufB, nullptr, inf);
+        fwd_step(g, k, s, act, mu, S, bufA, bufB, nullptr, inf, save);
         if (act) kahan_add(Jsum, Jc, stage_cost(g, k, mu, S, inf.sraw));
     }
     if (act && lane == 0) g.S_out[s] = Jsum + Jc;
     if (!g.backward) return;
-    __syncthreads();     // checkpoint stores before the reloads below
+    if (lane == 0)
+        for (int i = 0; i < CARRY; ++i) carry[i] = 0.0f;
+    __syncthreads();     // checkpoint stores and the zeroed carry before the reloads below
 
     // ---- passes 2 and 3, one segment at a time, last segment first --------
-    float mub[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-    float Sb[15];
-#pragma unroll
-    for (int i = 0; i < 15; ++i) Sb[i] = 0.0f;
-    float dl[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     float* vslot = g.vscr + (size_t)blockIdx.x * C * Np * GMT;
     for (int sg = g.nseg - 1; sg >= 0; --sg) {
         const int k0 = sg * C;
@@ -454,7 +526,7 @@ __global__ void __launch_bounds__(GT, 1) k_grad(const GradArgs g) {
         }
         for (int t = 0; t < len; ++t) {
             StepInfo inf;
-            fwd_step(g, k0 + t, s, act, mu, S, bufA, bufB, vslot + (size_t)t * Np * GMT, inf);
+            fwd_step(g, k0 + t, s, act, mu, S, bufA, bufB, vslot + (size_t)t * Np * GMT, inf, save);
             if (lane == 0) {
                 float* r1 = rec + ((t + 1) * GMT + w) * REC;
 #pragma unroll
@@ -469,25 +541,30 @@ __global__ void __launch_bounds__(GT, 1) k_grad(const GradArgs g) {
             const int k = k0 + t;
             const float* pre = rec + (t * GMT + w) * REC;
             const float* post = rec + ((t + 1) * GMT + w) * REC;
-            const StepInfo inf = info[t * GMT + w];
-            float m0[5], S0[15], m1[5], S1[15];
+            float mub[5], Sb[15];
 #pragma unroll
-            for (int i = 0; i < 5; ++i) {
-                m0[i] = pre[i];
-                m1[i] = post[i];
-            }
+            for (int i = 0; i < 5; ++i) mub[i] = carry[i];
 #pragma unroll
-            for (int i = 0; i < 15; ++i) {
-                S0[i] = pre[5 + i];
-                S1[i] = post[5 + i];
-            }
-            // stage cost of step k (scored on the post-step state)
+            for (int i = 0; i < 15; ++i) Sb[i] = carry[5 + i];
             float sbv = 0.0f, sbw = 0.0f;
-            if (act) {
-                const float gs = stage_cost_adjoint(g, k, m1, S1, wt, mub, Sb);
-                sbv = gs;
-                sbw = gs;
+            {
+                float m1[5], S1[15];
+#pragma unroll
+                for (int i = 0; i < 5; ++i) m1[i] = post[i];
+#pragma unroll
+                for (int i = 0; i < 15; ++i) S1[i] = post[5 + i];
+                // stage cost of step k (scored on the post-step state)
+                if (act) {
+                    const float gs = stage_cost_adjoint(g, k, m1, S1, wt, mub, Sb);
+                    sbv = gs;
+                    sbw = gs;
+                }
             }
+            float m0[5], S0[15];
+#pragma unroll
+            for (int i = 0; i < 5; ++i) m0[i] = pre[i];
+#pragma unroll
+            for (int i = 0; i < 15; ++i) S0[i] = pre[5 + i];
             // covariance adjoint: Sigma' = A Sigma A^T + diag(0,0,0,s,s)
             sbv += Sb[sidx(3, 3)];
             sbw += Sb[sidx(4, 4)];
@@ -541,7 +618,6 @@ __global__ void __launch_bounds__(GT, 1) k_grad(const GradArgs g) {
                 }
             // mean adjoint (Eq. 6 with the GP mean), with the A_bar terms
             const float mbv = mub[3], mbw = mub[4];
-            float ubx = mub[3] * a.kv, uby = mub[4] * a.kw;
             float nm[5];
             nm[0] = mub[0];
             nm[1] = mub[1];
@@ -551,9 +627,21 @@ __global__ void __launch_bounds__(GT, 1) k_grad(const GradArgs g) {
             nm[3] = mub[0] * (a.dt * cs) + mub[1] * (a.dt * sn) + mub[3] * a.av +
                     Ab02 * (-a.dt * sn) + Ab12 * (a.dt * cs);
             nm[4] = mub[2] * a.dt + mub[4] * a.aw;
-            if (!(inf.sraw > 0.0f)) {       // variance clamped at zero: no gradient through it
+            const StepInfo inf0 = info[t * GMT + w];
+            if (!(inf0.sraw > 0.0f)) {       // variance clamped at zero: no gradient through it
                 sbv = 0.0f;
                 sbw = 0.0f;
+            }
+            // the adjoints wait in shared memory while the product runs
+            if (lane == 0) {
+#pragma unroll
+                for (int i = 0; i < 5; ++i) save[i] = nm[i];
+#pragma unroll
+                for (int i = 0; i < 15; ++i) save[5 + i] = Sb[i];
+                save[20] = sbv;
+                save[21] = sbw;
+                save[22] = mbv;
+                save[23] = mbw;
             }
             // b = L^-T v = K^-1 k* for all samples of the CTA
             {
@@ -564,18 +652,22 @@ __global__ void __launch_bounds__(GT, 1) k_grad(const GradArgs g) {
             __syncthreads();
             tri_product<true>(g.Wt, Np, bufA, bufB);
             __syncthreads();
+            const float sbv2 = save[20], sbw2 = save[21], mbv2 = save[22], mbw2 = save[23];
             if (g.Bq) {
                 const size_t q0 = (size_t)k * g.Kpad + (size_t)blockIdx.x * GMT;
-                for (int i = tid; i < Np * GMT; i += GT) {
-                    const int ws = i / Np, j = i - ws * Np;
-                    g.Bq[(q0 + ws) * Np + j] = bufB[j * GMT + ws];
+                for (int ws = 0; ws < GMT; ++ws) {
+                    float* dst = g.Bq + (q0 + ws) * Np;
+                    for (int j = tid; j < Np; j += GT) dst[j] = bufB[j * GMT + ws];
                 }
                 if (lane == 0)
-                    g.qbar[q0 + w] = act ? make_float4(mbv, mbw, sbv, sbw) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    g.qbar[q0 + w] = act ? make_float4(mbv2, mbw2, sbv2, sbw2) : make_float4(0.f, 0.f, 0.f, 0.f);
             }
             // GP adjoint: z_bar and the lengthscale terms
+            float nv3 = save[3], nv4 = save[4];
             if (act) {
-                const float z0 = m0[3] * a.zscale[0], z1 = m0[4] * a.zscale[1],
+                const StepInfo inf = info[t * GMT + w];
+                float ubx = mbv2 * a.kv, uby = mbw2 * a.kw;
+                const float z0 = pre[3] * a.zscale[0], z1 = pre[4] * a.zscale[1],
                             z2 = inf.ux * a.zscale[2], z3 = inf.uy * a.zscale[3];
                 float zb[4] = {0.f, 0.f, 0.f, 0.f};
                 float lb[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
@@ -585,8 +677,8 @@ __global__ void __launch_bounds__(GT, 1) k_grad(const GradArgs g) {
                     const float kj = a.sf2 * exp2f(-(d[0] * d[0] + d[1] * d[1] + d[2] * d[2] + d[3] * d[3]));
                     const float bj = bufB[j * GMT + w];
                     const float2 al = __ldg(reinterpret_cast<const float2*>(a.alpha) + j);
-                    const float wv = kj * (mbv * al.x - 2.0f * sbv * bj);
-                    const float ww = kj * (mbw * al.y - 2.0f * sbw * bj);
+                    const float wv = kj * (mbv2 * al.x - 2.0f * sbv2 * bj);
+                    const float ww = kj * (mbw2 * al.y - 2.0f * sbw2 * bj);
                     const float wz = wv + ww;
 #pragma unroll
                     for (int dd = 0; dd < 4; ++dd) {
@@ -598,32 +690,44 @@ __global__ void __launch_bounds__(GT, 1) k_grad(const GradArgs g) {
                     if (g.ubar) {
 #pragma unroll
                         for (int dd = 0; dd < 4; ++dd) {
-                            lb[dd] = fmaf(-mbv * bj, __ldg(g.ubar + (size_t)dd * Np + j), lb[dd]);
-                            lb[4 + dd] = fmaf(-mbw * bj, __ldg(g.ubar + (size_t)(4 + dd) * Np + j), lb[4 + dd]);
+                            lb[dd] = fmaf(-mbv2 * bj, __ldg(g.ubar + (size_t)dd * Np + j), lb[dd]);
+                            lb[4 + dd] = fmaf(-mbw2 * bj, __ldg(g.ubar + (size_t)(4 + dd) * Np + j), lb[4 + dd]);
                         }
                     }
                 }
 #pragma unroll
                 for (int dd = 0; dd < 4; ++dd) zb[dd] = -2.0f * kLn2 * a.zscale[dd] * wsum(zb[dd]);
 #pragma unroll
-                for (int i = 0; i < 8; ++i) dl[i] += wsum(lb[i]);
-                nm[3] += zb[0];
-                nm[4] += zb[1];
+                for (int i = 0; i < 8; ++i) lb[i] = wsum(lb[i]);
+                nv3 += zb[0];
+                nv4 += zb[1];
                 ubx += zb[2];
                 uby += zb[3];
                 if (lane == 0) {
                     g.dU_out[(size_t)(2 * k) * a.K + s] = (inf.mask & 1) ? ubx : 0.0f;
                     g.dU_out[(size_t)(2 * k + 1) * a.K + s] = (inf.mask & 2) ? uby : 0.0f;
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) carry[20 + i] += lb[i];
                 }
             }
+            // carry the pre-step adjoints to step k - 1
+            __syncwarp();
+            if (lane == 0) {
+                carry[0] = save[0];
+                carry[1] = save[1];
+                carry[2] = save[2];
+                carry[3] = nv3;
+                carry[4] = nv4;
 #pragma unroll
-            for (int i = 0; i < 5; ++i) mub[i] = nm[i];
+                for (int i = 0; i < 15; ++i) carry[5 + i] = save[5 + i];
+            }
+            __syncwarp();
         }
         __syncthreads();     // rec / info / scratch reuse by the next segment
     }
     if (act && lane == 0 && g.dl_out) {
 #pragma unroll
-        for (int i = 0; i < 8; ++i) g.dl_out[(size_t)i * a.K + s] = dl[i];
+        for (int i = 0; i < 8; ++i) g.dl_out[(size_t)i * a.K + s] = carry[20 + i];
     }
 }
 
@@ -806,7 +910,7 @@ __global__ void k_grad_reduce(const GradReduceArgs r) {
 
 int grad_smem_bytes(int Np, int C) {
     return (int)(sizeof(float) * (2 * (size_t)Np * GMT + (size_t)(C + 1) * GMT * REC) +
-                 sizeof(StepInfo) * (size_t)C * GMT);
+                 sizeof(StepInfo) * (size_t)C * GMT + sizeof(float) * GMT * (SAVE + CARRY));
 }
 
 int grad_samples_per_cta() { return GMT; }
