@@ -65,3 +65,40 @@ def gp_predict(fits, Z):
         V = sla.solve_triangular(f["L"], Ks.T, lower=True)            # L^-1 k*, (N, M)
         var[:, j] = np.maximum(0.0, f["signal_var"] - np.sum(V * V, axis=0))
     return mean, var
+
+
+class Ensemble:
+    """Weighted terrain ensemble of Eq. 3: M fitted GP pairs and weights w."""
+
+    def __init__(self, fits, w):
+        self.fits = list(fits)
+        self.w = np.asarray(w, dtype=np.float64)
+        if len(self.fits) != self.w.shape[0]:
+            raise ValueError("one weight per terrain")
+
+
+def gp_predict_ensemble(ens, Z):
+    """Eq. 3: mean sum_i w_i m_i(z), covariance sum_i w_i^2 C_i(z) (diagonal,
+    the two outputs are independent GPs)."""
+    Z = np.asarray(Z, dtype=np.float64)
+    mean = np.zeros((Z.shape[0], 2))
+    var = np.zeros((Z.shape[0], 2))
+    for wi, f in zip(ens.w, ens.fits):
+        m, v = gp_predict(f, Z)
+        mean += wi * m
+        var += wi * wi * v
+    return mean, var
+
+
+def predict(model, Z):
+    """Mean and variance of the residual model: one GP pair or an Ensemble."""
+    if isinstance(model, Ensemble):
+        return gp_predict_ensemble(model, Z)
+    return gp_predict(model, Z)
+
+
+def fit_scenario(sc):
+    """The residual model of a scenario: its GP pair, or its terrain ensemble."""
+    if sc.terrains is None:
+        return gp_fit(sc.X, sc.Y, sc.hyper)
+    return Ensemble([gp_fit(X, Y, h) for X, Y, h in sc.terrains], sc.terrain_w)

@@ -20,8 +20,13 @@ Readings of the paper used here (the paper leaves these open):
     (Eq. 16); indicator weights are alpha_3 * P_lane and beta_1 * P_coll.
   * Speed term: alpha_4 * (v_desired - mu_v)^2 (squared so that both signs
     of deviation are penalised).
-  * Slip (alpha_2) and goal terms (beta_2, beta_3) are not part of this
-    rollout; their weights must be zero.
+  * Slip (alpha_2) is not part of this rollout (the planar state has no
+    lateral velocity); its weight must be zero.
+  * Goal terms (Eq. 12): g = |mu_XY(k+1) - goal| at every stage, weight
+    beta_2; F = P_goal * 1[|mu_XY(T) - goal| > goal_radius] on the last stage
+    only, weight beta_3.
+  * Terrain ensemble (Eq. 3): mean sum_i w_i m_i, variance sum_i w_i^2 var_i
+    per output; M = 1, w = 1 is the single GP.
   * MPPI weights (Alg. 1, deferred to the MPPI reference): w = softmax of
     -(S - min S) / lambda; update U <- U + sum_s w_s (u~_s - U).
   * Variance mode 0 ("per sample") tightens each sample with its own
@@ -32,7 +37,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from .gp import gp_predict
+from .gp import predict
 from .philox import control_noise
 from .quantiles import chi2_2_quantile, normal_quantile
 
@@ -161,6 +166,13 @@ def stage_cost(k, mu, Sxy, var, sc, consts, slope=None):
         coll = sigmoid(-slope * obs_margin) if O > 0 else np.zeros_like(obs_margin)
     b = P.beta
     cost = cost + b[0] * trC + b[1] * P.P_coll * coll                 # Eq. 12
+    if b[2] != 0.0 or b[3] != 0.0:
+        dg = np.hypot(mu[:, 0] - P.goal[0], mu[:, 1] - P.goal[1])
+        cost = cost + b[2] * dg                                       # g, every stage
+        if k == P.T - 1:                                              # F, terminal stage
+            miss = (dg > P.goal_radius).astype(np.float64) if slope is None \
+                else sigmoid(slope * (dg - P.goal_radius))
+            cost = cost + b[3] * P.P_goal * miss
     return cost, lane_margin, obs_margin
 
 
@@ -169,8 +181,8 @@ def stage_cost(k, mu, Sxy, var, sc, consts, slope=None):
 # --------------------------------------------------------------------------
 
 def _check_params(P):
-    if P.alpha[2] != 0.0 or P.beta[2] != 0.0 or P.beta[3] != 0.0:
-        raise ValueError("slip (alpha_2) and goal terms (beta_2, beta_3) are not modelled")
+    if P.alpha[2] != 0.0:
+        raise ValueError("the slip term (alpha_2) is not modelled")
 
 
 def rollout(sc, fits, state, U, it, samples=None, nominal_sxy=None, noise=True, slope=None):
@@ -200,7 +212,7 @@ def rollout(sc, fits, state, U, it, samples=None, nominal_sxy=None, noise=True, 
         eps = control_noise(P.seed, k, s_idx, it, P.sigma) if noise else np.zeros((S, 2))
         ut = np.clip(np.asarray(U[k], dtype=np.float64) + eps, umin, umax)   # Eq. 8
         z = np.stack([mu[:, 3], mu[:, 4], ut[:, 0], ut[:, 1]], axis=1)
-        m, var = gp_predict(fits, z)                                      # Eq. 3
+        m, var = predict(fits, z)                                         # Eq. 3
         A = jacobian(mu, P.dt, P.tau_v, P.tau_w)
         mu = nominal_step(mu, ut, P.dt, P.tau_v, P.tau_w)                 # Eq. 6, 10
         mu[:, 3] += m[:, 0]
@@ -244,7 +256,7 @@ def nominal_tightening(sc, fits, state, U):
     for k in range(P.T):
         u = np.clip(np.asarray(U[k], dtype=np.float64), umin, umax)[None]
         z = np.stack([mu[:, 3], mu[:, 4], u[:, 0], u[:, 1]], axis=1)
-        m, var = gp_predict(fits, z)
+        m, var = predict(fits, z)
         A = jacobian(mu, P.dt, P.tau_v, P.tau_w)
         mu = nominal_step(mu, u, P.dt, P.tau_v, P.tau_w)
         mu[:, 3] += m[:, 0]

@@ -51,7 +51,10 @@ class Params:
     v_desired: float = 1.5
     seed: int = 0
     variance_mode: int = 0            # 0 = per sample, 1 = nominal (Alg. 1 Step 2)
-    precision: int = 0                # 0 = FP32, 1 = BF16 hi/lo split
+    precision: int = 0                # 0 = FP32, 1 = BF16 hi/lo split, 2 = FP16 hi/lo split
+    goal: tuple = (0.0, 0.0)          # goal position of the stage and terminal terms (Eq. 12)
+    goal_radius: float = 0.5          # the terminal term fires when the final mean is farther
+    P_goal: float = 100.0             # penalty multiplying the terminal indicator
 
 
 @dataclass
@@ -75,6 +78,10 @@ class Scenario:
     x0: np.ndarray          # (5,) initial state X, Y, theta, v, omega
     U0: np.ndarray          # (T, 2) initial nominal control sequence
     meta: dict = field(default_factory=dict)
+    # terrain ensemble (Eq. 3): M training sets and hyper-parameter pairs, and
+    # the weights w_i; None for the single GP above
+    terrains: list = None   # [(X_i, Y_i, (Hyper, Hyper)), ...]
+    terrain_w: tuple = None
 
     @property
     def N(self) -> int:
@@ -216,6 +223,48 @@ def scenario(name: str, **overrides) -> Scenario:
     U0 = np.tile(np.array([p.v_desired, 0.0]), (p.T, 1))
     return Scenario(name=name, params=p, X=X, Y=Y, hyper=(Hyper(), Hyper()),
                     obstacles=obst, path=path, x0=x0, U0=U0, meta={"path": kind})
+
+
+# --------------------------------------------------------------------------
+# terrain ensemble (Eq. 3): stand-ins for the paper's grass, asphalt and tile
+# --------------------------------------------------------------------------
+
+TERRAIN_COEF = (      # (a, b, c): delta_v = -a v |w| - c v, delta_w = -b w v
+    (0.15, 0.30, 0.05),
+    (0.05, 0.10, 0.00),
+    (0.10, 0.20, 0.02),
+)
+TERRAIN_LENGTHSCALE = (0.5, 0.6, 0.45)
+TERRAIN_SIGNAL_VAR = (0.1, 0.08, 0.12)
+
+
+def terrain_residual(i, v, w, v_cmd, w_cmd):
+    """Synthetic residual of terrain i (the controller only sees GP fits of it)."""
+    a, b, c = TERRAIN_COEF[i % len(TERRAIN_COEF)]
+    v = np.asarray(v, dtype=np.float64)
+    w = np.asarray(w, dtype=np.float64)
+    return np.stack([-a * v * np.abs(w) - c * v, -b * w * v], axis=-1)
+
+
+def terrain_scenario(name: str = "cfg2", M: int = 3, N: int = None, w=None, **overrides) -> Scenario:
+    """The named workload with its single GP replaced by M terrain GPs (N
+    points each, own hyper-parameters shared by the two outputs of a terrain)
+    mixed with weights w (Eq. 3)."""
+    sc = scenario(name, **overrides)
+    N = sc.N if N is None else int(N)
+    rng = np.random.Generator(np.random.PCG64(7_000 + sc.params.seed))
+    terrains = []
+    for i in range(M):
+        X = GP_INPUT_LO + (GP_INPUT_HI - GP_INPUT_LO) * rng.random((N, 4))
+        Y = terrain_residual(i, X[:, 0], X[:, 1], X[:, 2], X[:, 3])
+        Y = Y + np.sqrt(1e-4) * rng.standard_normal((N, 2))
+        ell = TERRAIN_LENGTHSCALE[i % 3]
+        h = Hyper((ell,) * 4, TERRAIN_SIGNAL_VAR[i % 3], 1e-4)
+        terrains.append((X, Y, (h, Hyper(h.lengthscale, h.signal_var, h.noise_var))))
+    if w is None:
+        w = (0.5, 0.3, 0.2)[:M] if M <= 3 else tuple([1.0 / M] * M)
+        w = tuple(np.asarray(w) / np.sum(w))
+    return sc.replace(name=f"{name}-terrain{M}", terrains=terrains, terrain_w=tuple(float(x) for x in w))
 
 
 def batched_scenarios(B: int = 64, first_seed: int = 0):
