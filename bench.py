@@ -164,12 +164,15 @@ def committed_traffic(kernel="rollout_fp32", workload=WORKLOAD):
 CPU_SAMPLE_ROWS = 512
 
 
-def _cpu_child(rows, reps):
+def _cpu_child(rows, reps, workload=WORKLOAD):
     import numpy as np  # noqa: F401
     import oracle as O
     import scenarios as S
-    sc = S.scenario(WORKLOAD)
-    fits = O.gp_fit(sc.X, sc.Y, sc.hyper)
+    if workload.endswith("-terrain3"):
+        sc = S.terrain_scenario(workload[:-len("-terrain3")], M=3)
+    else:
+        sc = S.scenario(workload)
+    fits = O.fit_scenario(sc)
     samples = list(range(rows))
     t0 = time.perf_counter()
     for r in range(reps):
@@ -178,13 +181,13 @@ def _cpu_child(rows, reps):
     print(json.dumps({"seconds": dt, "sample_steps": rows * sc.params.T * reps}))
 
 
-def cpu_baseline(rows=CPU_SAMPLE_ROWS, reps=8):
+def cpu_baseline(rows=CPU_SAMPLE_ROWS, reps=8, workload=WORKLOAD):
     cores = os.cpu_count() or 1
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         env[k] = str(cores)
     env.pop("CUDA_VISIBLE_DEVICES", None)
-    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-child", str(rows), str(reps)]
+    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-child", str(rows), str(reps), workload]
     out = subprocess.run(cmd, capture_output=True, text=True, env=env, cwd=ROOT, timeout=900)
     line = [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
     if out.returncode != 0 or not line:
@@ -315,10 +318,18 @@ def run_ours(args):
         torch.cuda.set_device(0)
     B.build()
     dev = torch.device("cuda", torch.cuda.current_device())
-    sc = S.scenario(args.workload, seed=1 + rank, precision=PRECISIONS[args.precision])
-    P = sc.params
-    g = gp.gp_fit(sc.X, sc.Y, sc.hyper)
-    ctrl = gp.mppi_create(P, sc.obstacles, sc.path, g)
+    terrain = args.workload.endswith("-terrain3")
+    if terrain:
+        # the terrain ensemble of Eq. 3 (three GPs mixed per step) runs in FP32
+        sc = S.terrain_scenario(args.workload[:-len("-terrain3")], M=3, seed=1 + rank, precision=0)
+        P = sc.params
+        gps = [gp.gp_fit(X, Y, h) for X, Y, h in sc.terrains]
+        ctrl = gp.mppi_create_ensemble(P, sc.obstacles, sc.path, gps, sc.terrain_w)
+    else:
+        sc = S.scenario(args.workload, seed=1 + rank, precision=PRECISIONS[args.precision])
+        P = sc.params
+        g = gp.gp_fit(sc.X, sc.Y, sc.hyper)
+        ctrl = gp.mppi_create(P, sc.obstacles, sc.path, g)
     U = torch.tensor(sc.U0, dtype=torch.float32, device=dev)
     U_new = torch.empty_like(U)
     w = torch.empty(P.K, dtype=torch.float32, device=dev)
@@ -371,11 +382,21 @@ def run_ours(args):
     units = P.K * P.T * args.steps * ws
     value = units / (tot_ms / 1e3)
     S_seg = max(sc.path.shape[0] - 1, 1)
-    flops = rollout_flops_per_sample_step(sc.N, sc.obstacles.shape[0], S_seg) * P.K * P.T
+    if terrain:
+        flops = sum(rollout_flops_per_sample_step(X.shape[0], sc.obstacles.shape[0], S_seg)
+                    for X, _, _ in sc.terrains) * P.K * P.T
+    else:
+        flops = rollout_flops_per_sample_step(sc.N, sc.obstacles.shape[0], S_seg) * P.K * P.T
     r_avg = sum(rollout_ms) / len(rollout_ms)
     achieved = flops / (r_avg / 1e3) / 1e12
-    traffic = committed_traffic("rollout_fp32" if P.precision == 0 else "rollout_mma", args.workload)
-    if P.precision == 0:
+    traffic = committed_traffic("ensemble" if terrain else ("rollout_fp32" if P.precision == 0 else "rollout_mma"),
+                                args.workload)
+    if terrain:
+        roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak_tflops(2070.0), "unit": "TFLOP/s",
+                "traffic": traffic, "kernel": "k_rollout_ens",
+                "peak_note": "FP32 FMA pipe 152 SM x 128 lanes x 2 flops x 2070 MHz (derived); "
+                             "flops summed over the three terrain GPs"}
+    elif P.precision == 0:
         roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak_tflops(2070.0), "unit": "TFLOP/s",
                 "traffic": traffic, "kernel": "k_rollout_fp32",
                 "peak_note": "FP32 FMA pipe 152 SM x 128 lanes x 2 flops x 2070 MHz (derived)"}
@@ -398,11 +419,14 @@ def run_ours(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {0: "f32", 1: "f32+bf16split", 2: "f32+f16split"}[P.precision],
         "data": "synthetic (seeded GP training set, obstacles and figure-eight path)",
-        "config": describe(sc),
+        "config": describe(sc) if not terrain else {
+            **describe(sc), "workload": f"{sc.name}: K={P.K} T={P.T} three terrain GPs of N={sc.terrains[0][0].shape[0]} "
+                                        f"mixed by Eq. 3 (w={sc.terrain_w}), obstacles={sc.obstacles.shape[0]}, "
+                                        f"figure-eight, fp32", "terrains": 3},
         "gpu_launches": 2 * args.steps,
         "kernel_ms": {"rollout_avg": r_avg, "update_avg": sum(update_ms) / len(update_ms)},
         "roofline": roof,
-        "cpu_baseline": cpu_baseline() if (rank == 0 and ws == 1 and not args.no_cpu) else None,
+        "cpu_baseline": cpu_baseline(workload=args.workload) if (rank == 0 and ws == 1 and not args.no_cpu) else None,
         "e2e": {"value": units / e2e_s, "unit": "sample-steps/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "clocks": clk,
@@ -704,7 +728,7 @@ def run_batched(args):
 
 def main():
     if len(sys.argv) >= 2 and sys.argv[1] == "--cpu-child":
-        _cpu_child(int(sys.argv[2]), int(sys.argv[3]))
+        _cpu_child(int(sys.argv[2]), int(sys.argv[3]), sys.argv[4] if len(sys.argv) > 4 else WORKLOAD)
         return
     if len(sys.argv) >= 2 and sys.argv[1] == "--grad-cpu-child":
         _grad_cpu_child(int(sys.argv[2]))

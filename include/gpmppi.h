@@ -88,13 +88,17 @@ typedef struct gpmppi_params {
     float p_x;               /* chance level of Eq. 7, in (0, 1)                    */
     float u_min[2], u_max[2];/* control box of Eq. 8                                */
     float alpha[5];          /* Eq. 11 weights; alpha[2] (slip) must be 0           */
-    float beta[4];           /* Eq. 12 weights; beta[2], beta[3] (goal) must be 0   */
+    float beta[4];           /* Eq. 12 weights: variance, collision, goal distance,
+                                terminal miss                                        */
     float P_lane, P_coll;    /* penalties multiplying the two indicators            */
     float lane_half_width;   /* r of Eq. 13, > 0                                    */
     float v_desired;         /* v_desired of Eq. 11                                 */
     uint64_t seed;           /* Philox key                                          */
     int32_t variance_mode;   /* GPMPPI_VAR_*                                        */
     int32_t precision;       /* GPMPPI_FP32, GPMPPI_BF16_SPLIT or GPMPPI_FP16_SPLIT */
+    float goal[2];           /* goal position of the Eq. 12 goal terms              */
+    float goal_radius;       /* terminal term: penalty when |mu_XY(T) - goal| > this */
+    float P_goal;            /* penalty multiplying the terminal indicator          */
 } gpmppi_params;
 
 /* Fit the two residual GPs of Sec. III-A (outputs delta_v and delta_omega)
@@ -192,6 +196,37 @@ int mppi_device_status(gpmppi_ctrl c);
 
 /* Release a controller and its device buffers (synchronises its device). */
 int mppi_destroy(gpmppi_ctrl c);
+
+/* Terrain ensemble (Eq. 3): a controller whose residual model is the
+ * mixture of M terrain GP pairs, mean sum_i w_i m_i(z) and variance
+ * sum_i w_i^2 var_i(z) per output.  gps: M fitted GPs (host array of
+ * handles; each terrain's two outputs must share hyper-parameters; the
+ * controller keeps them alive as mppi_create does), weights: host, M floats
+ * (any finite values; Eq. 4 keeps them on the simplex).  2 <= M <= 8, or
+ * M = 1 (weight 1 gives the single-GP controller of mppi_create).  The
+ * ensemble rollout runs in FP32 with per-sample variance
+ * (GPMPPI_ERR_UNSUPPORTED for other precisions / modes); mppi_step and
+ * mppi_rollout_trace use it, mppi_grad and the batch API reject it.
+ * mppi_set_terrain_weights replaces the weights (host, M floats) for the
+ * following steps, e.g. with the result of terrain_weights. */
+int mppi_create_ensemble(const gpmppi_params* p, const float* obstacles, int32_t O, const float* path,
+                         int32_t P, const gpmppi_gp* gps, int32_t M, const float* weights,
+                         gpmppi_ctrl* out);
+int mppi_set_terrain_weights(gpmppi_ctrl c, const float* weights, int32_t M);
+
+/* Terrain-weight estimation, Eq. 4 (Alg. 1 Step 3), on the host:
+ *   w* = argmin |Yv - Fv w|^2 + |Yw - Fw w|^2 + gamma |w - w_prev|_1
+ *        s.t. 0 <= w_i <= 1, sum w_i = 1.
+ *   Yv, Yw   host, H doubles: observed velocity residuals over the last H steps
+ *   Fv, Fw   host, H x M doubles row-major: the terrains' GP mean predictions
+ *            (e.g. from gp_predict) at the same inputs
+ *   w_prev   host, M doubles; gamma >= 0; w_out host, M doubles (output)
+ * Exact: every pattern of active bounds and L1 kinks is solved as a small KKT
+ * system (4^M of them, 1 <= M <= 8) and the feasible candidate of least
+ * objective returned.  Pure host computation; no device is touched.
+ * Errors: INVALID_ARG, NONFINITE. */
+int terrain_weights(const double* Yv, const double* Yw, const double* Fv, const double* Fw, int32_t H,
+                    int32_t M, const double* w_prev, double gamma, double* w_out);
 
 /* Gradient of the smoothed chance-constrained rollout cost (adjoint rollout).
  * J(U, l) = sum_s w_s S_s, where S_s is the cost of sample s over the horizon

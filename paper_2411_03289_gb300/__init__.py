@@ -36,6 +36,7 @@ GPMPPI_FP16_SPLIT = 2
 EXPORTS = ("gp_fit", "gp_destroy", "gp_factors", "gp_predict", "mppi_create", "mppi_step",
            "mppi_rollout_trace", "mppi_set_iteration", "mppi_get_iteration", "mppi_nominal_sxy",
            "mppi_destroy", "mppi_set_profiling", "mppi_last_profile", "mppi_device_status", "mppi_grad",
+           "mppi_create_ensemble", "mppi_set_terrain_weights", "terrain_weights",
            "mppi_update_noalloc", "mppi_batch_create",
            "mppi_batch_buffers", "mppi_batch_step", "mppi_batch_graph", "mppi_batch_autotune",
            "mppi_batch_get_iteration", "mppi_batch_destroy", "gpmppi_philox", "gpmppi_control_noise", "gpmppi_mma_selftest", "gpmppi_last_error",
@@ -62,7 +63,9 @@ class Params(ctypes.Structure):
                 ("beta", ctypes.c_float * 4), ("P_lane", ctypes.c_float),
                 ("P_coll", ctypes.c_float), ("lane_half_width", ctypes.c_float),
                 ("v_desired", ctypes.c_float), ("seed", ctypes.c_uint64),
-                ("variance_mode", ctypes.c_int32), ("precision", ctypes.c_int32)]
+                ("variance_mode", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("goal", ctypes.c_float * 2), ("goal_radius", ctypes.c_float),
+                ("P_goal", ctypes.c_float)]
 
 
 _lib = None
@@ -94,6 +97,9 @@ def load():
         "mppi_last_profile": [vp, vp, vp],
         "mppi_device_status": [vp],
         "mppi_grad": [vp, vp, vp, vp, ctypes.c_float, vp, vp, vp, vp],
+        "mppi_create_ensemble": [vp, vp, i32, vp, i32, vp, i32, vp, ctypes.POINTER(vp)],
+        "mppi_set_terrain_weights": [vp, vp, i32],
+        "terrain_weights": [vp, vp, vp, vp, i32, i32, vp, ctypes.c_double, vp],
         "mppi_batch_create": [vp, i32, ctypes.POINTER(vp)],
         "mppi_batch_buffers": [vp, i32, vp, vp, vp, vp, vp],
         "mppi_batch_step": [vp, vp],
@@ -182,6 +188,9 @@ def make_params(p) -> Params:
     out.seed = int(p.seed) & 0xFFFFFFFFFFFFFFFF
     out.variance_mode = int(p.variance_mode)
     out.precision = int(p.precision)
+    out.goal[:] = [float(v) for v in getattr(p, "goal", (0.0, 0.0))]
+    out.goal_radius = float(getattr(p, "goal_radius", 0.5))
+    out.P_goal = float(getattr(p, "P_goal", 100.0))
     return out
 
 
@@ -255,6 +264,48 @@ def mppi_create(params, obstacles, path, gp: GP) -> Ctrl:
                            obst.shape[0], pth.ctypes.data_as(ctypes.c_void_p), pth.shape[0],
                            gp.handle, ctypes.byref(h)))
     return Ctrl(h.value, gp, p.K, p.T)
+
+
+def mppi_create_ensemble(params, obstacles, path, gps, weights) -> Ctrl:
+    """Controller over the terrain ensemble of Eq. 3 (gps: list of GP, weights: M floats)."""
+    lib = load()
+    p = make_params(params)
+    obst = _f32(obstacles).reshape(-1, 3)
+    pth = _f32(path).reshape(-1, 2)
+    M = len(gps)
+    handles = (ctypes.c_void_p * M)(*[g.handle for g in gps])
+    w = _f32(weights).reshape(M)
+    h = ctypes.c_void_p()
+    _check(lib.mppi_create_ensemble(ctypes.byref(p), obst.ctypes.data_as(ctypes.c_void_p) if obst.size else None,
+                                    obst.shape[0], pth.ctypes.data_as(ctypes.c_void_p), pth.shape[0],
+                                    ctypes.cast(handles, ctypes.c_void_p), M,
+                                    w.ctypes.data_as(ctypes.c_void_p), ctypes.byref(h)))
+    c = Ctrl(h.value, gps[0], p.K, p.T)
+    c.terrain_gps = list(gps)       # keep every terrain GP alive with the controller
+    return c
+
+
+def mppi_set_terrain_weights(ctrl: Ctrl, weights):
+    w = _f32(weights).reshape(-1)
+    _check(load().mppi_set_terrain_weights(ctrl.handle, w.ctypes.data_as(ctypes.c_void_p), w.shape[0]))
+
+
+def terrain_weights(Yv, Yw, Fv, Fw, w_prev, gamma):
+    """Eq. 4 on the host (exact); Fv, Fw (H, M).  Returns w (M,) float64."""
+    Yv = np.ascontiguousarray(np.asarray(Yv, dtype=np.float64).reshape(-1))
+    Yw = np.ascontiguousarray(np.asarray(Yw, dtype=np.float64).reshape(-1))
+    Fv = np.ascontiguousarray(np.asarray(Fv, dtype=np.float64))
+    Fw = np.ascontiguousarray(np.asarray(Fw, dtype=np.float64))
+    wp = np.ascontiguousarray(np.asarray(w_prev, dtype=np.float64).reshape(-1))
+    H, M = Fv.shape
+    if Fw.shape != (H, M) or Yv.shape[0] != H or Yw.shape[0] != H or wp.shape[0] != M:
+        raise ValueError("terrain_weights: inconsistent shapes")
+    out = np.zeros(M)
+    vp = ctypes.c_void_p
+    _check(load().terrain_weights(Yv.ctypes.data_as(vp), Yw.ctypes.data_as(vp), Fv.ctypes.data_as(vp),
+                                  Fw.ctypes.data_as(vp), H, M, wp.ctypes.data_as(vp), float(gamma),
+                                  out.ctypes.data_as(vp)))
+    return out
 
 
 def mppi_step(ctrl: Ctrl, state, U_nom, U_new, weights=None, costs=None, stream=None):

@@ -124,6 +124,8 @@ void free_ctrl(gpmppi_ctrl c) {
     for (cudaEvent_t e : c->ev)
         if (e) cudaEventDestroy(e);
     if (c->gp && c->gp->magic == kGpMagic) c->gp->g.n_controllers--;
+    for (int i = 1; i < c->M; ++i)
+        if (c->tgp[i] && c->tgp[i]->magic == kGpMagic) c->tgp[i]->g.n_controllers--;
     c->magic = 0;
     delete c;
 }
@@ -138,7 +140,8 @@ int validate_params(const gpmppi_params& p) {
     const float fs[] = {p.dt, p.tau_v, p.tau_w, p.sigma[0], p.sigma[1], p.lambda, p.p_x,
                         p.u_min[0], p.u_min[1], p.u_max[0], p.u_max[1], p.alpha[0], p.alpha[1],
                         p.alpha[2], p.alpha[3], p.alpha[4], p.beta[0], p.beta[1], p.beta[2],
-                        p.beta[3], p.P_lane, p.P_coll, p.lane_half_width, p.v_desired};
+                        p.beta[3], p.P_lane, p.P_coll, p.lane_half_width, p.v_desired,
+                        p.goal[0], p.goal[1], p.goal_radius, p.P_goal};
     for (float f : fs)
         if (!is_finite(f)) return fail(GPMPPI_ERR_NONFINITE, "params: non-finite value");
     if (!(p.dt > 0.0f) || !(p.tau_v > 0.0f) || !(p.tau_w > 0.0f)) return bad("dt, tau_v, tau_w must be > 0");
@@ -149,8 +152,7 @@ int validate_params(const gpmppi_params& p) {
     if (!(p.lane_half_width > 0.0f)) return bad("lane_half_width must be > 0");
     if (p.alpha[2] != 0.0f)
         return fail(GPMPPI_ERR_UNSUPPORTED, "params: the slip term (alpha[2]) is not modelled");
-    if (p.beta[2] != 0.0f || p.beta[3] != 0.0f)
-        return fail(GPMPPI_ERR_UNSUPPORTED, "params: goal terms (beta[2], beta[3]) are not modelled");
+    if (p.goal_radius < 0.0f) return bad("goal_radius must be >= 0");
     if (p.variance_mode != GPMPPI_VAR_PER_SAMPLE && p.variance_mode != GPMPPI_VAR_NOMINAL)
         return bad("unknown variance_mode");
     if (p.precision != GPMPPI_FP32 && p.precision != GPMPPI_BF16_SPLIT && p.precision != GPMPPI_FP16_SPLIT)
@@ -219,6 +221,11 @@ RolloutArgs gpm::make_rollout_args(gpmppi_ctrl c, const float* state, const floa
     a.v_des = p.v_desired;
     a.sq_chi2 = (float)c->sq_chi2;
     a.phi_inv = (float)c->phi_inv;
+    a.c_goal = p.beta[2];
+    a.c_term = (float)((double)p.beta[3] * p.P_goal);
+    a.goal_x = p.goal[0];
+    a.goal_y = p.goal[1];
+    a.goal_r = p.goal_radius;
     a.key0 = (uint32_t)p.seed;
     a.key1 = (uint32_t)(p.seed >> 32);
     a.it0 = (uint32_t)c->it;
@@ -227,6 +234,30 @@ RolloutArgs gpm::make_rollout_args(gpmppi_ctrl c, const float* state, const floa
 }
 
 namespace {
+
+// Launch arguments of the ensemble rollout: the single-GP arguments plus the
+// per-terrain factors and weights.
+EnsArgs make_ens_args(gpmppi_ctrl c, const RolloutArgs& a) {
+    EnsArgs e;
+    std::memset(&e, 0, sizeof(e));
+    e.r = a;
+    e.M = c->M;
+    e.Npmax = 0;
+    for (int i = 0; i < c->M; ++i) {
+        const GpDevice& g = c->tgp[i]->g;
+        TerrainGp& t = e.gp[i];
+        t.Xs = g.Xs[0];
+        t.alpha = g.alpha;
+        t.W = g.W[0];
+        t.N = g.N;
+        t.Np = g.Np;
+        t.sf2 = g.sf2[0];
+        for (int d = 0; d < 4; ++d) t.zscale[d] = g.zscale[0][d];
+        t.w = c->tw[i];
+        if (g.Np > e.Npmax) e.Npmax = g.Np;
+    }
+    return e;
+}
 
 int check_ctrl_device(gpmppi_ctrl c) {
     int dev = 0;
@@ -483,8 +514,11 @@ int mppi_step(gpmppi_ctrl c, const float state[5], const float* U_nom, float* U_
     RolloutArgs a = make_rollout_args(c, state, U_nom);
     if (costs) a.costs = costs;
     if (c->profiling) GPM_CUDA(cudaEventRecord(c->ev[0], st));
-    rc = (c->fmt < 0) ? launch_rollout_fp32(a, &c->tmW, false, st)
-                      : launch_rollout_mma(a, c->mm, c->fmt, false, st);
+    if (c->ens)
+        rc = launch_rollout_ens(make_ens_args(c, a), false, st);
+    else
+        rc = (c->fmt < 0) ? launch_rollout_fp32(a, &c->tmW, false, st)
+                          : launch_rollout_mma(a, c->mm, c->fmt, false, st);
     if (rc) return rc;
     if (c->profiling) GPM_CUDA(cudaEventRecord(c->ev[1], st));
     UpdateArgs u;
@@ -530,8 +564,63 @@ int mppi_rollout_trace(gpmppi_ctrl c, const float state[5], const float* U_nom, 
     a.tr_sig = sigma;
     a.tr_stage = stage;
     a.tr_margin = margins;
+    if (c->ens) return launch_rollout_ens(make_ens_args(c, a), true, (cudaStream_t)stream);
     if (c->fmt >= 0) return launch_rollout_mma(a, c->mm, c->fmt, true, (cudaStream_t)stream);
     return launch_rollout_fp32(a, &c->tmW, true, (cudaStream_t)stream);
+}
+
+int mppi_create_ensemble(const gpmppi_params* p, const float* obstacles, int32_t O, const float* path,
+                         int32_t P, const gpmppi_gp* gps, int32_t M, const float* weights,
+                         gpmppi_ctrl* out) {
+    if (!out) return fail(GPMPPI_ERR_INVALID_ARG, "mppi_create_ensemble: out must not be NULL");
+    *out = nullptr;
+    if (!gps || !weights) return fail(GPMPPI_ERR_INVALID_ARG, "mppi_create_ensemble: gps / weights is NULL");
+    if (M < 1 || M > kMaxTerrains) return fail(GPMPPI_ERR_INVALID_ARG, "mppi_create_ensemble: M out of range");
+    if (!p) return fail(GPMPPI_ERR_INVALID_ARG, "mppi_create_ensemble: params must not be NULL");
+    for (int i = 0; i < M; ++i) {
+        if (!valid_gp(gps[i])) return fail(GPMPPI_ERR_INVALID_ARG, "mppi_create_ensemble: invalid GP handle");
+        if (!gps[i]->g.shared)
+            return fail(GPMPPI_ERR_UNSUPPORTED, "mppi_create_ensemble: each terrain's outputs must share hyper-parameters");
+        if (gps[i]->g.device != gps[0]->g.device)
+            return fail(GPMPPI_ERR_INVALID_ARG, "mppi_create_ensemble: GPs on different devices");
+        if (!is_finite(weights[i])) return fail(GPMPPI_ERR_NONFINITE, "mppi_create_ensemble: non-finite weight");
+    }
+    // M = 1 with weight 1 is the single-GP controller (any precision);
+    // everything else runs the FP32 ensemble rollout
+    const bool ens = M > 1 || weights[0] != 1.0f;
+    if (ens && p->precision != GPMPPI_FP32)
+        return fail(GPMPPI_ERR_UNSUPPORTED, "mppi_create_ensemble: the ensemble rollout runs in FP32");
+    if (ens && p->variance_mode != GPMPPI_VAR_PER_SAMPLE)
+        return fail(GPMPPI_ERR_UNSUPPORTED, "mppi_create_ensemble: needs the per-sample variance mode");
+    int npmax = 0, optin = 0, dev = 0, rc;
+    for (int i = 0; i < M; ++i) npmax = gps[i]->g.Np > npmax ? gps[i]->g.Np : npmax;
+    if ((rc = current_device(&dev))) return rc;
+    GPM_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    if (ens && ens_smem_bytes(npmax) > optin)
+        return fail(GPMPPI_ERR_UNSUPPORTED, "mppi_create_ensemble: GPs too large for the ensemble rollout");
+    gpmppi_ctrl c = nullptr;
+    if ((rc = mppi_create(p, obstacles, O, path, P, gps[0], &c))) return rc;
+    c->M = M;
+    c->ens = ens;
+    for (int i = 0; i < M; ++i) {
+        c->tgp[i] = gps[i];
+        c->tw[i] = weights[i];
+        if (i > 0) gps[i]->g.n_controllers++;
+    }
+    *out = c;
+    return GPMPPI_OK;
+}
+
+int mppi_set_terrain_weights(gpmppi_ctrl c, const float* weights, int32_t M) {
+    if (!valid_ctrl(c)) return fail(GPMPPI_ERR_INVALID_ARG, "mppi_set_terrain_weights: invalid handle");
+    if (!weights || M != c->M) return fail(GPMPPI_ERR_INVALID_ARG, "mppi_set_terrain_weights: M differs from the controller's");
+    for (int i = 0; i < M; ++i)
+        if (!is_finite(weights[i])) return fail(GPMPPI_ERR_NONFINITE, "mppi_set_terrain_weights: non-finite weight");
+    if (!c->ens && weights[0] != 1.0f)
+        return fail(GPMPPI_ERR_UNSUPPORTED,
+                    "mppi_set_terrain_weights: a single-GP controller keeps weight 1 (create it with weight != 1)");
+    for (int i = 0; i < M; ++i) c->tw[i] = weights[i];
+    return GPMPPI_OK;
 }
 
 int mppi_grad(gpmppi_ctrl c, const float state[5], const float* U_nom, const float* sample_weights,
@@ -550,6 +639,7 @@ int mppi_grad(gpmppi_ctrl c, const float state[5], const float* U_nom, const flo
         return fail(GPMPPI_ERR_INVALID_ARG, "mppi_grad: dlengthscale needs dU");
     if (c->p.variance_mode != GPMPPI_VAR_PER_SAMPLE)
         return fail(GPMPPI_ERR_UNSUPPORTED, "mppi_grad: needs the per-sample variance mode");
+    if (c->ens) return fail(GPMPPI_ERR_UNSUPPORTED, "mppi_grad: terrain ensembles are not differentiated");
     GpDevice& g = c->gp->g;
     const int K = c->p.K, T = c->p.T, Np = g.Np, N = g.N;
     int C = (int)std::ceil(std::sqrt((double)T));

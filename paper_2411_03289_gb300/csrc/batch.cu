@@ -28,6 +28,7 @@ constexpr uint32_t kBatchMagic = 0x42415431u;   // "BAT1"
 int check_ctrl_handle(gpmppi_ctrl c) {
     if (!c || c->magic != kCtrlMagicValue || !c->gp || c->gp->magic != kGpMagicValue)
         return fail(GPMPPI_ERR_INVALID_ARG, "mppi_batch_create: invalid controller handle");
+    if (c->ens) return fail(GPMPPI_ERR_UNSUPPORTED, "mppi_batch_create: terrain ensembles are not batched");
     return GPMPPI_OK;
 }
 

@@ -160,6 +160,9 @@ struct RolloutArgs {
     float c_speed;          // alpha_4
     float c_coll;           // beta_1 * P_coll
     float r, v_des, sq_chi2, phi_inv;
+    float c_goal;           // beta_2: weight of the distance to the goal (every stage)
+    float c_term;           // beta_3 * P_goal: terminal miss penalty
+    float goal_x, goal_y, goal_r;
     uint32_t key0, key1, it0, it1;
     // when set, the initial state and the iteration are read from device
     // memory instead of x0 / it0 / it1 (batched and graph-replayed steps)
@@ -180,6 +183,38 @@ struct MmaArgs {
     int stages;             // shared-memory pipeline depth (2..4)
     int rps;                // producer threads per sample (2, 4, 8): 128, 64, 32 samples per CTA
     int scene_smem;         // lane segments and obstacles staged in shared memory
+};
+
+// Goal terms of Eq. 12 at stage k (0-based) for the mean position (x, y):
+// c_goal |p - goal| at every stage, plus c_term on the last stage when the
+// mean is farther than goal_r from the goal.
+__device__ __forceinline__ float goal_cost(const RolloutArgs& a, int k, float x, float y) {
+    if (a.c_goal == 0.0f && a.c_term == 0.0f) return 0.0f;
+    const float dx = x - a.goal_x, dy = y - a.goal_y;
+    const float d = sqrtf(dx * dx + dy * dy);
+    float c = a.c_goal * d;
+    if (k == a.T - 1 && d > a.goal_r) c += a.c_term;
+    return c;
+}
+
+// One terrain GP of an ensemble (Eq. 3) as the ensemble rollout reads it.
+struct TerrainGp {
+    const float* Xs;        // N x 4, scaled by this GP's lengthscales
+    const float* alpha;     // N x 2
+    const float* W;         // Np x Np rows of L^-T
+    int N, Np;
+    float sf2;
+    float zscale[4];
+    float w;                // ensemble weight w_i
+};
+
+constexpr int kMaxTerrains = 8;
+
+struct EnsArgs {
+    RolloutArgs r;          // scene, controls, constants (the GP fields of r are unused)
+    TerrainGp gp[kMaxTerrains];
+    int M;
+    int Npmax;              // largest Np of the terrains
 };
 
 // Adjoint rollout (gradient of the smoothed cost); see adjoint.cu.
@@ -266,5 +301,7 @@ int launch_dk_alpha(const float* Xs, const float* alpha, int N, int Np, float sf
                     cudaStream_t st);
 int launch_transpose(const float* W, int Np, float* Wt, cudaStream_t st);
 int launch_grad_reduce(const GradReduceArgs& r, cudaStream_t st);
+int ens_smem_bytes(int Npmax);
+int launch_rollout_ens(const EnsArgs& e, bool trace, cudaStream_t st);
 
 }  // namespace gpm

@@ -34,6 +34,12 @@ struct gpmppi_ctrl_s {
     CUtensorMap tmW;              // TMA map over the GP's W
     gpm::MmaArgs mm{};              // tensor-core tiles (split precisions)
     int fmt = -1;                 // 0 = FP16, 1 = BF16 split, -1 = FP32 path
+    // terrain ensemble (Eq. 3): M >= 2 GPs mixed with weights tw on the
+    // ensemble rollout; M = 1 is the single GP `gp`
+    int M = 1;
+    bool ens = false;             // runs the ensemble rollout
+    gpmppi_gp tgp[gpm::kMaxTerrains] = {};
+    float tw[gpm::kMaxTerrains] = {};
     // adjoint-rollout scratch (allocated by the first mppi_grad call)
     void* grad_scr = nullptr;
     size_t grad_bytes = 0;

@@ -433,6 +433,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             const float lmargin = e - rbar;
             stage += a.c_dev * e;
             if (lmargin > 0.0f) stage += a.c_lane * disc;
+            stage += goal_cost(a, k, mu0, mu1);                       // Eq. 12 goal terms
             cost += stage;
             disc *= 0.9f;
             if (TRACE && active) {

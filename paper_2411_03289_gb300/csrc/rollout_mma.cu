@@ -464,6 +464,7 @@ __device__ __forceinline__ void rollout_mma_body(const RolloutArgs& a, const Mma
         const float lmargin = e_lane - rbar;
         stage += a.c_dev * e_lane;
         if (lmargin > 0.0f) stage += a.c_lane * disc;
+        stage += goal_cost(a, k, mu0, mu1);                           // Eq. 12 goal terms
         cost += stage;
         disc *= 0.9f;
         if (TRACE && active && u == 0) {

@@ -45,8 +45,20 @@ def to_np(t):
 
 
 def make_ctrl(gp, sc, gpfit=None):
+    """(GP handle(s), controller) for a scenario: its GP pair, or its terrain
+    ensemble (Eq. 3) when the scenario has one."""
+    if sc.terrains is not None:
+        gps = [gp.gp_fit(X, Y, h) for X, Y, h in sc.terrains]
+        return gps, gp.mppi_create_ensemble(sc.params, sc.obstacles, sc.path, gps, sc.terrain_w)
     g = gpfit if gpfit is not None else gp.gp_fit(sc.X, sc.Y, sc.hyper)
     return g, gp.mppi_create(sc.params, sc.obstacles, sc.path, g)
+
+
+def signal_var(sc):
+    """Largest prior variance of the scenario's GP(s): the scale of the variance tolerance."""
+    if sc.terrains is not None:
+        return max(h[0].signal_var for _, _, h in sc.terrains)
+    return sc.hyper[0].signal_var
 
 
 def gpu_step(gp, ctrl, sc, state, U, it=None):
@@ -92,7 +104,7 @@ def sigma_upper(S):
 def sig_floor(sc):
     """Covariance tolerance floor: the GP variance scale sf2 plus the growth of
     the position entries over the horizon."""
-    return sc.hyper[0].signal_var * (1.0 + sc.params.T * sc.params.dt)
+    return signal_var(sc) * (1.0 + sc.params.T * sc.params.dt)
 
 
 def close(gpu, ref, rtol, floor=1.0):
@@ -117,15 +129,21 @@ def reconcile_costs(sc, ro, gpu_costs, rows=None):
     """Indicator-tie protocol.  Returns (adjusted oracle costs, number of
     samples whose cost was taken from a valid alternative)."""
     c_lane, c_coll = _penalties(sc)
+    P = sc.params
     ref = ro["costs"].copy()
     lm, om = ro["lane_margin"], ro["obs_margin"]
     T = lm.shape[1]
     disc = 0.9 ** np.arange(T)
+    c_term = P.beta[3] * P.P_goal
+    # terminal goal indicator (Eq. 12 F): distance of the final mean beyond the radius
+    gm = np.hypot(ro["mu"][:, T - 1, 0] - P.goal[0], ro["mu"][:, T - 1, 1] - P.goal[1]) - P.goal_radius
     n_alt = 0
     for s in range(ref.shape[0]):
         if close(gpu_costs[s], ref[s], TOL_COST):
             continue
         deltas = []
+        if c_term != 0.0 and abs(gm[s]) < MARGIN_WINDOW:
+            deltas.append(-c_term if gm[s] > 0 else c_term)
         for k in range(T):
             if abs(lm[s, k]) < MARGIN_WINDOW and c_lane != 0.0:
                 sign = -1.0 if lm[s, k] > 0 else 1.0
@@ -169,8 +187,6 @@ def check_step(sc, ro, U, gpu_U_new, gpu_w, gpu_c):
 def check_trace(sc, ro, tr, rows=None):
     """Per-(sample, step) parity of means, covariances, stage costs, margins."""
     rows = np.arange(ro["costs"].shape[0]) if rows is None else np.asarray(rows)
-    sf2 = sc.hyper[0].signal_var
-    P = sc.params
     mu_g = tr["mu"][rows]
     assert_close(mu_g, ro["mu"], TOL_TRAJ, what="trajectory means")
     sig_ref = sigma_upper(ro["Sigma"])
@@ -200,8 +216,6 @@ def trace_errors(sc, ro, tr, rows=None):
     """Max scaled errors per quantity (no assertion): means, covariances,
     lane margins (with the floors of the parity tolerances)."""
     rows = np.arange(ro["costs"].shape[0]) if rows is None else np.asarray(rows)
-    sf2 = sc.hyper[0].signal_var
-    P = sc.params
     sig_ref = sigma_upper(ro["Sigma"])
     mg = tr["margins"][rows]
     return dict(
