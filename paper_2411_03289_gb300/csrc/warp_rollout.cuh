@@ -49,18 +49,37 @@ __device__ __forceinline__ float2 ldg2(const float* p) {
     return __ldg(reinterpret_cast<const float2*>(p));
 }
 
-// Rows [r0, r1) of the product for the thread's two column pairs: LO / HI say
-// which of the pairs (at pl / ph) take part.  r0 and r1 are multiples of 16.
-template <bool LO, bool HI>
+template <int CPL>
+struct Cols;
+template <>
+struct Cols<1> {
+    using V = float;
+    static __device__ __forceinline__ V load(const float* p) { return __ldg(p); }
+    static __device__ __forceinline__ float at(const V& v, int) { return v; }
+};
+template <>
+struct Cols<2> {
+    using V = float2;
+    static __device__ __forceinline__ V load(const float* p) { return ldg2(p); }
+    static __device__ __forceinline__ float at(const V& v, int c) { return c ? v.y : v.x; }
+};
+
+// Rows [r0, r1) of the product for the thread's two column groups of CPL
+// columns each: LO / HI say which of the groups (at pl / ph) take part.  r0
+// and r1 are multiples of 16.
+template <int CPL, bool LO, bool HI>
 __device__ __forceinline__ void tri_rows(int Np, const float* in, int r0, int r1, const float* pl,
-                                         const float* ph, bool okl, bool okh, float (&al)[GMT][2],
-                                         float (&ah)[GMT][2]) {
+                                         const float* ph, bool okl, bool okh, float (&al)[GMT][CPL],
+                                         float (&ah)[GMT][CPL]) {
+    using C = Cols<CPL>;
+    typename C::V zero;
+    if constexpr (CPL == 1) zero = 0.0f; else zero = make_float2(0.f, 0.f);
     for (int r = r0; r < r1; r += 8) {
-        float2 ml[8], mh[8];
+        typename C::V ml[8], mh[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
-            if (LO) ml[u] = okl ? ldg2(pl + (size_t)(r + u) * Np) : make_float2(0.f, 0.f);
-            if (HI) mh[u] = okh ? ldg2(ph + (size_t)(r + u) * Np) : make_float2(0.f, 0.f);
+            if (LO) ml[u] = okl ? C::load(pl + (size_t)(r + u) * Np) : zero;
+            if (HI) mh[u] = okh ? C::load(ph + (size_t)(r + u) * Np) : zero;
         }
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
@@ -68,66 +87,59 @@ __device__ __forceinline__ void tri_rows(int Np, const float* in, int r0, int r1
             const float4 x1 = *reinterpret_cast<const float4*>(in + (r + u) * GMT + 4);
             const float xs[GMT] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
 #pragma unroll
-            for (int s = 0; s < GMT; ++s) {
-                if (LO) {
-                    al[s][0] = fmaf(xs[s], ml[u].x, al[s][0]);
-                    al[s][1] = fmaf(xs[s], ml[u].y, al[s][1]);
+            for (int s = 0; s < GMT; ++s)
+#pragma unroll
+                for (int c = 0; c < CPL; ++c) {
+                    if (LO) al[s][c] = fmaf(xs[s], C::at(ml[u], c), al[s][c]);
+                    if (HI) ah[s][c] = fmaf(xs[s], C::at(mh[u], c), ah[s][c]);
                 }
-                if (HI) {
-                    ah[s][0] = fmaf(xs[s], mh[u].x, ah[s][0]);
-                    ah[s][1] = fmaf(xs[s], mh[u].y, ah[s][1]);
-                }
-            }
         }
     }
 }
 
-// out[i * GMT + s] = sum_r in[r * GMT + s] * M[r * Np + i] for every column i < Np.
-// LOWER = false: M holds rows of L^-T (M[r][i] = 0 for i < r), so column block
-// [b, b + 64) needs rows [0, b + 64); LOWER = true: M holds rows of L^-1
-// (M[r][i] = 0 for i > r), so it needs rows [b, Np).  Both matrices are
-// zero-padded to Np x Np.  Each pass covers 16 blocks of 64 columns; warp w
-// takes blocks w and 15 - w (lane l their columns 2l, 2l + 1), so that every
-// warp visits the same number of rows of either triangle.  Called by all
-// threads; no barrier inside.
-template <bool LOWER>
-__device__ void tri_product(const float* __restrict__ M, int Np, const float* in, float* out) {
+// The product below with column blocks of 32 CPL columns.
+template <bool LOWER, int CPL>
+__device__ void tri_product_cols(const float* __restrict__ M, int Np, const float* in, float* out) {
     constexpr int NBLK = 2 * (GT / 32);
-    constexpr int BW = 64;
+    constexpr int BW = 32 * CPL;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int c0 = 0; c0 < Np; c0 += NBLK * BW) {
         const int blo = c0 + BW * warp, bhi = c0 + BW * (NBLK - 1 - warp);
         if (blo >= Np) continue;                  // then bhi >= Np too (warp-uniform)
-        const int clo = blo + 2 * lane, chi = bhi + 2 * lane;
+        const int clo = blo + CPL * lane, chi = bhi + CPL * lane;
         const bool okl = clo < Np, okh = chi < Np;
         const bool hi_any = bhi < Np;              // warp-uniform
-        float al[GMT][2], ah[GMT][2];
+        float al[GMT][CPL], ah[GMT][CPL];
 #pragma unroll
-        for (int s = 0; s < GMT; ++s) {
-            al[s][0] = al[s][1] = 0.0f;
-            ah[s][0] = ah[s][1] = 0.0f;
-        }
+        for (int s = 0; s < GMT; ++s)
+#pragma unroll
+            for (int c = 0; c < CPL; ++c) {
+                al[s][c] = 0.0f;
+                ah[s][c] = 0.0f;
+            }
         const float* pl = M + (okl ? clo : 0);
         const float* ph = M + (okh ? chi : 0);
+        // block edges are multiples of 32 and Np of 16: every row range below
+        // starts and ends on a multiple of 16
         if (!LOWER) {
             const int el = min(Np, blo + BW);
             if (hi_any) {
-                tri_rows<true, true>(Np, in, 0, el, pl, ph, okl, okh, al, ah);
-                tri_rows<false, true>(Np, in, el, min(Np, bhi + BW), pl, ph, okl, okh, al, ah);
+                tri_rows<CPL, true, true>(Np, in, 0, el, pl, ph, okl, okh, al, ah);
+                tri_rows<CPL, false, true>(Np, in, el, min(Np, bhi + BW), pl, ph, okl, okh, al, ah);
             } else {
-                tri_rows<true, false>(Np, in, 0, el, pl, ph, okl, okh, al, ah);
+                tri_rows<CPL, true, false>(Np, in, 0, el, pl, ph, okl, okh, al, ah);
             }
         } else {
             if (hi_any) {
-                tri_rows<true, false>(Np, in, blo, bhi, pl, ph, okl, okh, al, ah);
-                tri_rows<true, true>(Np, in, bhi, Np, pl, ph, okl, okh, al, ah);
+                tri_rows<CPL, true, false>(Np, in, blo, bhi, pl, ph, okl, okh, al, ah);
+                tri_rows<CPL, true, true>(Np, in, bhi, Np, pl, ph, okl, okh, al, ah);
             } else {
-                tri_rows<true, false>(Np, in, blo, Np, pl, ph, okl, okh, al, ah);
+                tri_rows<CPL, true, false>(Np, in, blo, Np, pl, ph, okl, okh, al, ah);
             }
         }
         if (okl) {
 #pragma unroll
-            for (int c = 0; c < 2; ++c) {
+            for (int c = 0; c < CPL; ++c) {
                 float4* o = reinterpret_cast<float4*>(out + (clo + c) * GMT);
                 o[0] = make_float4(al[0][c], al[1][c], al[2][c], al[3][c]);
                 o[1] = make_float4(al[4][c], al[5][c], al[6][c], al[7][c]);
@@ -135,7 +147,7 @@ __device__ void tri_product(const float* __restrict__ M, int Np, const float* in
         }
         if (okh) {
 #pragma unroll
-            for (int c = 0; c < 2; ++c) {
+            for (int c = 0; c < CPL; ++c) {
                 float4* o = reinterpret_cast<float4*>(out + (chi + c) * GMT);
                 o[0] = make_float4(ah[0][c], ah[1][c], ah[2][c], ah[3][c]);
                 o[1] = make_float4(ah[4][c], ah[5][c], ah[6][c], ah[7][c]);
@@ -144,8 +156,24 @@ __device__ void tri_product(const float* __restrict__ M, int Np, const float* in
     }
 }
 
-// lambda_max of the 2x2 position covariance and its derivatives with respect
-// to (Sxx, Sxy, Syy); Sxy is the single stored off-diagonal entry.
+// out[i * GMT + s] = sum_r in[r * GMT + s] * M[r * Np + i] for every column i < Np.
+// LOWER = false: M holds rows of L^-T (M[r][i] = 0 for i < r), so a column
+// block [b, b + BW) needs rows [0, b + BW); LOWER = true: M holds rows of L^-1
+// (M[r][i] = 0 for i > r), so it needs rows [b, Np).  Both matrices are
+// zero-padded to Np x Np.  Each pass covers 16 column blocks; warp w takes
+// blocks w and 15 - w (lane l their columns l CPL .. l CPL + CPL - 1), so that
+// every warp visits the same number of rows of either triangle.  Blocks are 64
+// columns wide (CPL = 2, float2 loads) where that keeps the warps balanced
+// (768 < Np <= 1024 or Np >= 2048) and 32 wide elsewhere.  Called by all
+// threads; no barrier inside.
+template <bool LOWER>
+__device__ void tri_product(const float* __restrict__ M, int Np, const float* in, float* out) {
+    if ((Np > 768 && Np <= 1024) || Np >= 2048)
+        tri_product_cols<LOWER, 2>(M, Np, in, out);
+    else
+        tri_product_cols<LOWER, 1>(M, Np, in, out);
+}
+
 struct Lam {
     float lmax, sq;          // clamped eigenvalue and its square root
     float dxx, dxy, dyy;     // d sqrt(lmax) / d (Sxx, Sxy, Syy)
