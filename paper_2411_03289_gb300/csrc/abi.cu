@@ -97,6 +97,7 @@ void free_gp(gpmppi_gp h) {
     for (int f = 0; f < 2; ++f) {
         cudaFree(g.mma_hi[f]);
         cudaFree(g.mma_lo[f]);
+        cudaFree(g.cl_tiles[f]);
     }
     cudaFree(g.Wt);
     cudaFree(g.ubar);
@@ -491,6 +492,27 @@ int mppi_create(const gpmppi_params* p, const float* obstacles, int32_t O, const
                 free_ctrl(c);
                 return fail(GPMPPI_ERR_UNSUPPORTED, "mppi_create: tensor-core rollout does not fit shared memory");
             }
+            // N <= 512: the cluster rollout keeps the factor resident in shared memory
+            const char* no_cl = std::getenv("GPMPPI_NO_CLUSTER");
+            if (g.N > 0 && g.N <= 512 && !(no_cl && no_cl[0] == '1')) {
+                if ((rc = build_cl_tiles(gp->g, c->fmt))) {
+                    free_ctrl(c);
+                    return rc;
+                }
+                ClArgs& cl = c->cla;
+                cl.tiles = gp->g.cl_tiles[c->fmt];
+                cl.npc = gp->g.cl_npc;
+                cl.ns = cl.npc / 64;
+                cl.cs = cl.ns / 2;
+                for (int r = 0; r < 4; ++r) {
+                    cl.base[r] = gp->g.cl_base[r];
+                    cl.bytes[r] = gp->g.cl_bytes[r];
+                }
+                cl.qscale = c->mm.qscale;
+                cl.scene_smem = 1;
+                if (cl_smem_bytes(cl, c->S, O) > smem_optin) cl.scene_smem = 0;
+                c->cl = cl_smem_bytes(cl, c->S, O) <= smem_optin && cl_schedulable(cl, c->S, O, dev);
+            }
         }
         *out = c;
         return GPMPPI_OK;
@@ -516,6 +538,8 @@ int mppi_step(gpmppi_ctrl c, const float state[5], const float* U_nom, float* U_
     if (c->profiling) GPM_CUDA(cudaEventRecord(c->ev[0], st));
     if (c->ens)
         rc = launch_rollout_ens(make_ens_args(c, a), false, st);
+    else if (c->cl)
+        rc = launch_rollout_cl(a, c->cla, c->fmt, false, st);
     else
         rc = (c->fmt < 0) ? launch_rollout_fp32(a, &c->tmW, false, st)
                           : launch_rollout_mma(a, c->mm, c->fmt, false, st);
@@ -565,6 +589,7 @@ int mppi_rollout_trace(gpmppi_ctrl c, const float state[5], const float* U_nom, 
     a.tr_stage = stage;
     a.tr_margin = margins;
     if (c->ens) return launch_rollout_ens(make_ens_args(c, a), true, (cudaStream_t)stream);
+    if (c->cl) return launch_rollout_cl(a, c->cla, c->fmt, true, (cudaStream_t)stream);
     if (c->fmt >= 0) return launch_rollout_mma(a, c->mm, c->fmt, true, (cudaStream_t)stream);
     return launch_rollout_fp32(a, &c->tmW, true, (cudaStream_t)stream);
 }

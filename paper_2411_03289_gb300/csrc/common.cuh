@@ -119,6 +119,13 @@ struct GpDevice {
     uint16_t* mma_lo[2] = {nullptr, nullptr};
     float mma_cB = 0.0f;
     int NpM = 0;
+    // resident tiles of the cluster rollout (N <= 512): per 16-bit format, rank
+    // r's pieces at element offset cl_base[r], cl_bytes[r] bytes; NpC = 128,
+    // 256 or 512 output columns
+    uint16_t* cl_tiles[2] = {nullptr, nullptr};
+    int cl_base[4] = {0, 0, 0, 0};
+    int cl_bytes[4] = {0, 0, 0, 0};
+    int cl_npc = 0;
     // adjoint rollout, built on first use: rows of L^-1 (Np x Np) and the
     // vectors (dK/dl_d) alpha_o (8 x Np)
     float* Wt = nullptr;
@@ -251,6 +258,19 @@ struct GradReduceArgs {
     float ell[4];
 };
 
+// Cluster rollout (N <= 512): CS CTAs share 128 samples; rank r holds its
+// column slices of cB L^-1 resident in shared memory.
+struct ClArgs {
+    const uint16_t* tiles;  // all ranks' pieces (one 16-bit format)
+    int base[4];            // element offset of rank r's pieces
+    int bytes[4];           // their size in bytes
+    int cs;                 // cluster size (CTAs per 128 samples): NS / 2
+    int ns;                 // 64-column slices: NpC / 64
+    int npc;                // padded training-set size (128, 256 or 512)
+    float qscale;           // (sf2 / cB)^2
+    int scene_smem;         // lane segments and obstacles staged in shared memory
+};
+
 struct UpdateArgs {
     const float* costs;     // K
     const float2* u_tilde;  // T x K
@@ -288,6 +308,10 @@ int rollout_fp32_smem_bytes(int Np, int mtp, int stages);
 int launch_rollout_mma(const RolloutArgs& a, const MmaArgs& mm, int fmt, bool trace, cudaStream_t st);
 int rollout_mma_stages(int NpM, int S, int O, int smem_optin);
 int build_mma_tiles(GpDevice& g, int fmt);
+int build_cl_tiles(GpDevice& g, int fmt);
+int cl_smem_bytes(const ClArgs& cl, int S, int O);
+bool cl_schedulable(const ClArgs& cl, int S, int O, int device);
+int launch_rollout_cl(const RolloutArgs& a, const ClArgs& cl, int fmt, bool trace, cudaStream_t st);
 int launch_mma_selftest(int fmt, int N, int K, int variant, const uint16_t* A, const uint16_t* B,
                         float* D, unsigned int* err, cudaStream_t st);
 int rollout_fp32_mtp(int Np);

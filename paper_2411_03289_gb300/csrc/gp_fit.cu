@@ -305,7 +305,79 @@ __global__ void k_pack_mma(const double* __restrict__ Xm, int N, int NpM, int fm
     }
 }
 
+// Resident tiles of the cluster rollout.  Cluster rank r owns the 64-column
+// slices r and NS - 1 - r of cB L^-1 (NS = NpC / 64); chunk c (training points
+// 16c .. 16c + 15) of rank r is one piece: 128 rows (slice r then slice
+// NS - 1 - r) while both slices need it (c < 4 (r + 1)), else 64 rows (slice
+// NS - 1 - r alone, needed while c < 4 (NS - r)).  A piece is its hi part then
+// its lo part, each slab-major: slab sl (points 8 sl .. 8 sl + 7), row rr at
+// element sl * rows * 8 + rr * 8.  Pieces follow each other in chunk order;
+// rank r's pieces start at element offset base[r].
+__global__ void k_pack_cl(const double* __restrict__ Xm, int N, int NS, int fmt, double cB,
+                          const int4* __restrict__ pieces, int npieces, uint16_t* __restrict__ out) {
+    const int p = blockIdx.y;
+    if (p >= npieces) return;
+    const int4 d = pieces[p];            // (element offset, chunk, rank, rows)
+    const int rows = d.w;
+    const int n = rows * 16;             // elements per part
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n) return;
+    const int sl = idx / (rows * 8), rr = (idx / 8) % rows, e = idx % 8;
+    const int c = d.y, r = d.z;
+    const int j = 16 * c + 8 * sl + e;
+    const int i = (rows == 128 && rr < 64) ? 64 * r + rr
+                                           : 64 * (NS - 1 - r) + (rows == 128 ? rr - 64 : rr);
+    double v = 0.0;
+    if (i < N && j < N && j <= i) v = cB * Xm[(size_t)i * N + j];
+    uint16_t h, l;
+    if (fmt == 0) {
+        const __half hh = __double2half(v);
+        h = __half_as_ushort(hh);
+        l = __half_as_ushort(__double2half(v - (double)__half2float(hh)));
+    } else {
+        const __nv_bfloat16 hh = __double2bfloat16(v);
+        h = __bfloat16_as_ushort(hh);
+        l = __bfloat16_as_ushort(__double2bfloat16(v - (double)__bfloat162float(hh)));
+    }
+    out[(size_t)d.x + idx] = h;
+    out[(size_t)d.x + n + idx] = l;
+}
+
 }  // namespace
+
+int build_cl_tiles(GpDevice& g, int fmt) {
+    if (g.cl_tiles[fmt] || g.N == 0) return GPMPPI_OK;
+    int rc = build_mma_tiles(g, fmt);      // sets cB (and the streaming tiles)
+    if (rc) return rc;
+    const int NpC = g.N <= 128 ? 128 : (g.N <= 256 ? 256 : 512);
+    if (g.N > 512) return fail(GPMPPI_ERR_UNSUPPORTED, "cluster tiles: N > 512");
+    const int NS = NpC / 64, CS = NS / 2;
+    std::vector<int4> pieces;
+    size_t off = 0;
+    for (int r = 0; r < CS; ++r) {
+        g.cl_base[r] = (int)off;
+        for (int c = 0; c < 4 * (NS - r); ++c) {
+            const int rows = (c < 4 * (r + 1)) ? 128 : 64;
+            pieces.push_back(make_int4((int)off, c, r, rows));
+            off += (size_t)rows * 16 * 2;
+        }
+        g.cl_bytes[r] = (int)((off - (size_t)g.cl_base[r]) * sizeof(uint16_t));
+    }
+    g.cl_npc = NpC;
+    int4* dp = nullptr;
+    GPM_CUDA(cudaMalloc(&dp, pieces.size() * sizeof(int4)));
+    cudaError_t e = cudaMemcpy(dp, pieces.data(), pieces.size() * sizeof(int4), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&g.cl_tiles[fmt], off * sizeof(uint16_t));
+    if (e == cudaSuccess) {
+        k_pack_cl<<<dim3(8, (unsigned)pieces.size()), 256>>>(g.Linv64[0], g.N, NS, fmt, (double)g.mma_cB, dp,
+                                                           (int)pieces.size(), g.cl_tiles[fmt]);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    cudaFree(dp);
+    if (e != cudaSuccess) return cuda_fail(e, "build_cl_tiles");
+    return GPMPPI_OK;
+}
 
 int build_mma_tiles(GpDevice& g, int fmt) {
     if (g.mma_hi[fmt] || g.N == 0) return GPMPPI_OK;

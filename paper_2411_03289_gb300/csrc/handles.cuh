@@ -34,6 +34,8 @@ struct gpmppi_ctrl_s {
     CUtensorMap tmW;              // TMA map over the GP's W
     gpm::MmaArgs mm{};              // tensor-core tiles (split precisions)
     int fmt = -1;                 // 0 = FP16, 1 = BF16 split, -1 = FP32 path
+    bool cl = false;              // split precisions with N <= 512: the cluster rollout
+    gpm::ClArgs cla{};
     // terrain ensemble (Eq. 3): M >= 2 GPs mixed with weights tw on the
     // ensemble rollout; M = 1 is the single GP `gp`
     int M = 1;

@@ -1,0 +1,680 @@
+// Tensor-core rollout for training sets of up to 512 points: a cluster of CS
+// CTAs (CS = NpC / 128) carries 128 samples through the horizon, each CTA
+// holding its share of the variance factor resident in shared memory.
+//
+// Same method and arithmetic as the streaming tensor-core rollout
+// (Alg. 1 Step 1; V = K* L^-T on the tensor cores with FP16/BF16 hi/lo split
+// operands, |V_m|^2 = |L^-1 k*_m|^2).  What changes is where the operands
+// live.  The output columns of V are cut into 64-column slices and rank r of
+// the cluster owns slices r and NS - 1 - r (equal triangular work for every
+// rank).  Their pieces of cB L^-1 (hi and lo, at most 144 KiB) are copied into
+// shared memory once, before the first step, so a step moves no factor
+// tiles at all: the MMAs read resident B and the kernel-row tiles A that the
+// producer warps write into a three-stage ring.  This matters because a
+// 128 x 128 x 16 MMA reads 8 KiB of operands from shared memory, which is
+// the whole shared-memory bandwidth at the tensor rate; streaming the factor
+// through the same shared memory every step halved the MMA rate.
+//
+// Per step: every rank computes the noise, queries and kernel rows of all 128
+// samples (rank 0 also the GP mean), issues the MMAs of its slices, reads its
+// partial |V_m|^2 from TMEM and exchanges the partials (and rank 0's means)
+// through distributed shared memory, guarded by mbarriers that each peer
+// arrives on remotely.  All ranks then advance the same 128 states
+// identically (same inputs, same order of summation); the cost phase (lane
+// distance, obstacles, Eq. 11-16) is split between the ranks by sample, so
+// rank r scores and writes the samples m = r (mod CS).
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <cfloat>
+
+#include "common.cuh"
+#include "tc05.cuh"
+
+namespace gpm {
+namespace {
+
+constexpr int MT = 128;               // samples per cluster (the MMA M)
+constexpr int NPROD = 256;            // producer threads: two per sample
+constexpr int THREADS = NPROD + 32;   // + the MMA-issuing warp
+constexpr int NSTAGE = 2;             // kernel-row tile ring
+constexpr int GCH = 2;                // chunks per stage: one tcgen05.commit per stage
+constexpr int A_PART = MT * 16 * 2;   // 4 KiB: one 16-bit part of a 128 x 16 tile
+constexpr int A_CHUNK = 2 * A_PART;   // hi + lo of one chunk
+constexpr int A_STAGE = GCH * A_CHUNK;
+constexpr int B_MAX = 144 * 1024;     // largest resident share (NS = 8)
+constexpr uint64_t kWaitNs = 2000000000ull;
+
+struct ClLayout {
+    int b, a, bars, tslot, abort_flag, xq, xm, qloc, mloc, sst, ep, om, xs, al, seg, il2, obs, total;
+};
+
+// shared-memory layout; the resident B share is sized for the largest rank;
+// S lane segments and O obstacles are staged when they fit (else S = O = 0);
+// nown = 128 / CS samples scored per rank
+__host__ __device__ inline ClLayout cl_layout(int npc, int S, int O) {
+    const int nown = MT / (npc / 128);
+    ClLayout L;
+    L.b = 0;
+    L.a = B_MAX;
+    L.bars = L.a + NSTAGE * A_STAGE;             // a_full, empty [NSTAGE], b_res, pass_done, tmem_free, xbar[2]
+    L.tslot = L.bars + 8 * (2 * NSTAGE + 5);
+    L.abort_flag = L.tslot + 4;
+    L.xq = ((L.abort_flag + 4 + 15) / 16) * 16;  // [2][4][MT] floats: partial |V|^2 per rank
+    L.xm = L.xq + 2 * 4 * MT * 4;                // [2][4][MT] float2: GP mean partial per rank
+    L.qloc = L.xm + 2 * 4 * MT * 8;              // [2][MT] floats
+    L.mloc = L.qloc + 2 * MT * 4;                // [2][MT] float2
+    L.sst = L.mloc + 2 * MT * 8;                 // [nown][24] floats: post-step state for the cost phase
+    L.ep = L.sst + nown * 24 * 4;                // [NPROD] floats
+    L.om = L.ep + NPROD * 4;                     // [NPROD] floats
+    L.xs = ((L.om + NPROD * 4 + 127) / 128) * 128;
+    L.al = L.xs + npc * 16;
+    L.seg = L.al + npc * 8;                      // S float4
+    L.il2 = L.seg + S * 16;                      // S floats
+    L.obs = L.il2 + ((S + 3) / 4) * 16;          // O x 3 floats
+    L.total = L.obs + O * 12;
+    return L;
+}
+
+__device__ __forceinline__ void bulk_copy(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            tc::smem_addr(dst)),
+        "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(tc::smem_addr(bar))
+        : "memory");
+}
+
+template <int FMT>
+__device__ __forceinline__ void split2(float a, float b, uint32_t* hi, uint32_t* lo) {
+    if (FMT == 0) {
+        const __half2 h = __floats2half2_rn(a, b);
+        const float2 hf = __half22float2(h);
+        const __half2 l = __floats2half2_rn(a - hf.x, b - hf.y);
+        *hi = *reinterpret_cast<const uint32_t*>(&h);
+        *lo = *reinterpret_cast<const uint32_t*>(&l);
+    } else {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+        const float2 hf = __bfloat1622float2(h);
+        const __nv_bfloat162 l = __floats2bfloat162_rn(a - hf.x, b - hf.y);
+        *hi = *reinterpret_cast<const uint32_t*>(&h);
+        *lo = *reinterpret_cast<const uint32_t*>(&l);
+    }
+}
+
+__device__ __forceinline__ bool try_wait_cluster(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(tc::smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait (CTA-local phases: the tensor pipe, the producers).
+__device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                              unsigned int* err) {
+    if (*abort_flag) return false;
+    if (tc::mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = tc::global_ns();
+    while (!tc::mbar_try_wait(bar, parity)) {
+        if (*abort_flag) return false;
+        if (tc::global_ns() - t0 > kWaitNs) {
+            *abort_flag = 1;
+            if (err) atomicOr(err, 1u);
+            return false;
+        }
+    }
+    return true;
+}
+
+// Bounded wait on a phase completed by remote arrivals (acquire at cluster scope).
+__device__ __forceinline__ bool wait_cluster(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                             unsigned int* err) {
+    if (try_wait_cluster(bar, parity)) return true;
+    const uint64_t t0 = tc::global_ns();
+    while (!try_wait_cluster(bar, parity)) {
+        if (tc::global_ns() - t0 > kWaitNs) {
+            *abort_flag = 1;
+            if (err) atomicOr(err, 1u);
+            return false;
+        }
+    }
+    return true;
+}
+
+__device__ __forceinline__ void producers_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+// address of the same shared-memory object in CTA `peer` of the cluster
+__device__ __forceinline__ uint32_t peer_addr(const void* p, uint32_t peer) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(tc::smem_addr(p)), "r"(peer));
+    return r;
+}
+
+__device__ __forceinline__ void st_peer_f32(uint32_t addr, float v) {
+    asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
+}
+
+__device__ __forceinline__ void st_peer_f32x2(uint32_t addr, float2 v) {
+    asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(addr), "f"(v.x), "f"(v.y) : "memory");
+}
+
+__device__ __forceinline__ void arrive_peer(uint32_t bar_addr) {
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar_addr) : "memory");
+}
+
+__device__ __forceinline__ void fence_cluster() { asm volatile("fence.acq_rel.cluster;" ::: "memory"); }
+
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+template <int FMT, bool TRACE>
+__global__ void __launch_bounds__(THREADS, 1) k_rollout_cl(const RolloutArgs a, const ClArgs cl) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    const ClLayout L = cl_layout(cl.npc, cl.scene_smem ? a.S : 0, cl.scene_smem ? a.O : 0);
+    unsigned char* bres = sm + L.b;
+    uint64_t* a_full = reinterpret_cast<uint64_t*>(sm + L.bars);
+    uint64_t* empty = a_full + NSTAGE;
+    uint64_t* b_res = empty + NSTAGE;
+    uint64_t* pass_done = b_res + 1;
+    uint64_t* tmem_free = pass_done + 1;
+    uint64_t* xbar = tmem_free + 1;             // [2]
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + L.tslot);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + L.abort_flag);
+    float* xq = reinterpret_cast<float*>(sm + L.xq);
+    float2* xm = reinterpret_cast<float2*>(sm + L.xm);
+    float* qloc = reinterpret_cast<float*>(sm + L.qloc);
+    float2* mloc = reinterpret_cast<float2*>(sm + L.mloc);
+    float* sst = reinterpret_cast<float*>(sm + L.sst);
+    float* ep = reinterpret_cast<float*>(sm + L.ep);
+    float* omh = reinterpret_cast<float*>(sm + L.om);
+    float4* xs_s = reinterpret_cast<float4*>(sm + L.xs);
+    float2* al_s = reinterpret_cast<float2*>(sm + L.al);
+    float4* seg_s = reinterpret_cast<float4*>(sm + L.seg);
+    float* il2_s = reinterpret_cast<float*>(sm + L.il2);
+    float* obs_s = reinterpret_cast<float*>(sm + L.obs);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int CS = cl.cs, NS = cl.ns;
+    const uint32_t rank = cluster_rank();
+    const int tile = blockIdx.x / CS;
+    const int nboth = 4 * ((int)rank + 1);      // chunks needed by both of this rank's slices
+    const int nch = 4 * (NS - (int)rank);       // chunks needed by its upper slice
+    const int mspan = (4 * NS) / CS;            // GP-mean chunks per rank
+    const int mc0 = (int)rank * mspan, mc1 = mc0 + mspan;
+    const uint32_t bbytes = (uint32_t)cl.bytes[rank];
+
+    if (tid == 0) {
+        for (int i = 0; i < NSTAGE; ++i) {
+            tc::mbar_init(a_full + i, NPROD / 32);
+            tc::mbar_init(empty + i, 1);
+        }
+        tc::mbar_init(b_res, 1);
+        tc::mbar_init(pass_done, 1);
+        tc::mbar_init(tmem_free, NPROD / 32);
+        tc::mbar_init(xbar, CS > 1 ? CS - 1 : 1);
+        tc::mbar_init(xbar + 1, CS > 1 ? CS - 1 : 1);
+        *abort_flag = 0;
+        tc::fence_mbar_init();
+    }
+    for (int j = tid; j < cl.npc; j += THREADS) {
+        if (j < a.N) {
+            xs_s[j] = __ldg(reinterpret_cast<const float4*>(a.Xs) + j);
+            al_s[j] = __ldg(reinterpret_cast<const float2*>(a.alpha) + j);
+        } else {
+            xs_s[j] = make_float4(1.0e4f, 1.0e4f, 1.0e4f, 1.0e4f);
+            al_s[j] = make_float2(0.0f, 0.0f);
+        }
+    }
+    const int Ssm = cl.scene_smem ? a.S : 0, Osm = cl.scene_smem ? a.O : 0;
+    for (int i = tid; i < Ssm; i += THREADS) {
+        seg_s[i] = __ldg(a.seg + i);
+        il2_s[i] = __ldg(a.seg_il2 + i);
+    }
+    for (int i = tid; i < 3 * Osm; i += THREADS) obs_s[i] = __ldg(a.obst + i);
+    const float4* segp = cl.scene_smem ? seg_s : a.seg;
+    const float* il2p = cl.scene_smem ? il2_s : a.seg_il2;
+    const float* obsp = cl.scene_smem ? obs_s : a.obst;
+    if (warp == 0) tc::tmem_alloc(tslot, 128);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (tid == 0) {
+        // this rank's resident share of the factor, one copy for the whole horizon
+        tc::mbar_expect_tx(b_res, bbytes);
+        bulk_copy(bres, cl.tiles + cl.base[rank], bbytes, b_res);
+    }
+    // every CTA's barriers are initialised before any peer arrives on them
+    cluster_sync_all();
+    const uint32_t taddr = *tslot;
+
+    if (warp == NPROD / 32) {
+        // ======================= MMA issuer (one thread) =====================
+        if (lane == 0) {
+            const uint32_t idesc128 = tc::idesc_f16(FMT, MT, 128);
+            const uint32_t idesc64 = tc::idesc_f16(FMT, MT, 64);
+            bool ok = wait_or_abort(b_res, 0, abort_flag, a.err);
+            tc::fence_after_sync();
+            uint32_t n = 0;
+            for (int k = 0; k < a.T && ok; ++k) {
+                if (k > 0) {
+                    if (!wait_or_abort(tmem_free, (uint32_t)(k - 1) & 1u, abort_flag, a.err)) break;
+                    tc::fence_after_sync();
+                }
+                for (int c = 0; c < nch; c += GCH, ++n) {
+                    const int st = (int)(n % NSTAGE);
+                    const uint32_t use = n / NSTAGE;
+                    if (!wait_or_abort(a_full + st, use & 1u, abort_flag, a.err)) {
+                        ok = false;
+                        break;
+                    }
+                    tc::fence_after_sync();
+#pragma unroll
+                    for (int h = 0; h < GCH; ++h) {
+                        const int cc = c + h;
+                        const uint32_t aHi = tc::smem_addr(sm + L.a + st * A_STAGE + h * A_CHUNK), aLo = aHi + A_PART;
+                        const uint64_t dAh = tc::smem_desc(aHi, MT * 16, 128);
+                        const uint64_t dAl = tc::smem_desc(aLo, MT * 16, 128);
+                        if (cc < nboth) {
+                            // both slices: one 128-row piece, D columns 0 .. 127
+                            const uint32_t bHi = tc::smem_addr(bres) + (uint32_t)cc * 8192u;
+                            const uint64_t dBh = tc::smem_desc(bHi, 128 * 16, 128);
+                            const uint64_t dBl = tc::smem_desc(bHi + 4096u, 128 * 16, 128);
+                            tc::mma_f16(taddr, dAh, dBh, idesc128, cc > 0 ? 1u : 0u);
+                            tc::mma_f16(taddr, dAh, dBl, idesc128, 1u);
+                            tc::mma_f16(taddr, dAl, dBh, idesc128, 1u);
+                        } else {
+                            // the upper slice alone: a 64-row piece, D columns 64 .. 127
+                            const uint32_t bHi = tc::smem_addr(bres) + (uint32_t)nboth * 8192u +
+                                                 (uint32_t)(cc - nboth) * 4096u;
+                            const uint64_t dBh = tc::smem_desc(bHi, 64 * 16, 128);
+                            const uint64_t dBl = tc::smem_desc(bHi + 2048u, 64 * 16, 128);
+                            tc::mma_f16(taddr + 64u, dAh, dBh, idesc64, 1u);
+                            tc::mma_f16(taddr + 64u, dAh, dBl, idesc64, 1u);
+                            tc::mma_f16(taddr + 64u, dAl, dBh, idesc64, 1u);
+                        }
+                    }
+                    // one commit per stage: each tcgen05.commit stalls the tensor pipe
+                    tc::mma_commit(empty + st);
+                }
+                if (!ok) break;
+                tc::mma_commit(pass_done);
+            }
+            // let MMAs in flight land before the shared memory can be released
+            if (!ok) {
+                const uint64_t t0 = tc::global_ns();
+                for (uint32_t i = (n >= (uint32_t)NSTAGE ? n - (uint32_t)NSTAGE : 0); i < n; ++i)
+                    while (!tc::mbar_try_wait(empty + (i % NSTAGE), (i / NSTAGE) & 1u) &&
+                           tc::global_ns() - t0 < 200000000ull) {
+                    }
+            }
+        }
+        __syncwarp();
+    } else {
+        // ========================== producer warps =============================
+        const int m = tid & (MT - 1);          // sample within the cluster
+        const int u = tid >> 7;                // which of its two threads (half of each chunk)
+        const int s_me = tile * MT + m;
+        const bool active = s_me < a.K;
+        const int s_q = active ? s_me : 0;
+        // cost phase: this rank scores samples m = rank (mod CS); RC threads per sample
+        const int nown = MT / CS;
+        const int RC = NPROD / nown;
+        const int ci = tid % nown, cpart = tid / nown;
+        const int mc = (int)rank + CS * ci;
+        const int sc_me = tile * MT + mc;
+        const bool cactive = sc_me < a.K;
+
+        float mu0 = a.x0[0], mu1 = a.x0[1], mu2 = a.x0[2], mu3 = a.x0[3], mu4 = a.x0[4];
+        const uint32_t it0 = a.it0, it1 = a.it1;
+        float S00 = 0, S01 = 0, S02 = 0, S03 = 0, S04 = 0, S11 = 0, S12 = 0, S13 = 0, S14 = 0,
+              S22 = 0, S23 = 0, S24 = 0, S33 = 0, S34 = 0, S44 = 0;
+        float cost = 0.0f, disc = 1.0f;
+        uint32_t n = 0;
+
+        for (int k = 0; k < a.T; ++k) {
+            // ---------------- noise, clamp, query --------------------------------
+            const float2 e = control_eps((uint32_t)k, (uint32_t)s_q, it0, it1, a.key0, a.key1, a.sig_v,
+                                         a.sig_w);
+            float2 ut;
+            ut.x = fminf(fmaxf(__ldg(a.U + 2 * k) + e.x, a.umin0), a.umax0);
+            ut.y = fminf(fmaxf(__ldg(a.U + 2 * k + 1) + e.y, a.umin1), a.umax1);
+            if (u == 0 && active && (m % CS) == (int)rank) a.u_tilde[(size_t)k * a.K + s_me] = ut;
+            const float z0 = mu3 * a.zscale[0], z1 = mu4 * a.zscale[1];
+            const float z2 = ut.x * a.zscale[2], z3 = ut.y * a.zscale[3];
+
+            // ---------------- kernel-row tiles (8 points per thread per chunk) ----
+            // Two chunks per burst (16 independent exp2 in flight).  The GP mean
+            // is split between the ranks: rank r sums chunks [mc0, mc1), the
+            // part of them beyond its own tiles (the highest rank) computed
+            // for the mean alone.
+            float mv = 0.0f, mw = 0.0f, cv = 0.0f, cw = 0.0f;
+            auto kernel_row = [&](int c, float (&av)[8]) {
+                const int jb = c * 16 + u * 8;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const float4 x = xs_s[jb + q];
+                    const float d0 = z0 - x.x, d1 = z1 - x.y, d2 = z2 - x.z, d3 = z3 - x.w;
+                    av[q] = exp2f(-(d0 * d0 + d1 * d1 + d2 * d2 + d3 * d3));
+                }
+            };
+            auto mean_part = [&](int c, const float (&av)[8]) {
+                const int jb = c * 16 + u * 8;
+                float pv = 0.0f, pw = 0.0f;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const float2 al = al_s[jb + q];
+                    pv = fmaf(av[q], al.x, pv);
+                    pw = fmaf(av[q], al.y, pw);
+                }
+                kahan_add(mv, cv, pv);
+                kahan_add(mw, cw, pw);
+            };
+            for (int c = 0; c < nch; c += 2) {
+                float av0[8], av1[8];
+                kernel_row(c, av0);
+                kernel_row(c + 1, av1);
+                if (c >= mc0 && c < mc1) mean_part(c, av0);
+                if (c + 1 >= mc0 && c + 1 < mc1) mean_part(c + 1, av1);
+                uint32_t hw[2][4], lw[2][4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    split2<FMT>(av0[2 * q], av0[2 * q + 1], &hw[0][q], &lw[0][q]);
+                    split2<FMT>(av1[2 * q], av1[2 * q + 1], &hw[1][q], &lw[1][q]);
+                }
+                {
+                    const int st = (int)(n % NSTAGE);
+                    const uint32_t use = n / NSTAGE;
+                    if (n >= (uint32_t)NSTAGE) wait_or_abort(empty + st, (use - 1) & 1u, abort_flag, a.err);
+#pragma unroll
+                    for (int h = 0; h < GCH; ++h) {
+                        // slab u (points 8u .. 8u + 7) of row m of chunk c + h
+                        unsigned char* ph = sm + L.a + st * A_STAGE + h * A_CHUNK + u * (MT * 16) + m * 16;
+                        *reinterpret_cast<uint4*>(ph) = make_uint4(hw[h][0], hw[h][1], hw[h][2], hw[h][3]);
+                        *reinterpret_cast<uint4*>(ph + A_PART) = make_uint4(lw[h][0], lw[h][1], lw[h][2], lw[h][3]);
+                    }
+                    tc::fence_proxy_async();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(a_full + st);
+                    ++n;
+                }
+            }
+            for (int c = (mc0 > nch ? mc0 : nch); c < mc1; ++c) {
+                float av[8];
+                kernel_row(c, av);
+                mean_part(c, av);
+            }
+            // ---------------- this rank's partial |V_m|^2 -------------------------
+            bool ok = wait_or_abort(pass_done, (uint32_t)k & 1u, abort_flag, a.err);
+            ok = __all_sync(0xffffffffu, ok);    // tcgen05.ld is warp-collective
+            tc::fence_after_sync();
+            float qpart = 0.0f;
+            if (ok) {
+                // warp w reads TMEM lanes 32 (w % 4) ..; thread half u its 64 columns
+                const uint32_t row = taddr + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(64 * u);
+#pragma unroll
+                for (int cc = 0; cc < 64; cc += 32) {
+                    float v[32];
+                    tc::tmem_ld32(row + (uint32_t)cc, v);
+                    float p0 = 0.0f, p1 = 0.0f, p2 = 0.0f, p3 = 0.0f;
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        p0 = fmaf(v[i], v[i], p0);
+                        p1 = fmaf(v[8 + i], v[8 + i], p1);
+                        p2 = fmaf(v[16 + i], v[16 + i], p2);
+                        p3 = fmaf(v[24 + i], v[24 + i], p3);
+                    }
+                    qpart += (p0 + p1) + (p2 + p3);
+                }
+            }
+            tc::fence_before_sync();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(tmem_free);
+            qloc[u * MT + m] = qpart;
+            mloc[u * MT + m] = make_float2(mv + cv, mw + cw);
+            producers_sync();
+            // ---------------- exchange between the ranks ---------------------------
+            const int buf = k & 1;
+            if (u == 0) {
+                const float qc = qloc[m] + qloc[MT + m];
+                float* mine = xq + (buf * 4 + (int)rank) * MT + m;
+                *mine = qc;
+                for (int p = 0; p < CS; ++p)
+                    if (p != (int)rank) st_peer_f32(peer_addr(mine, (uint32_t)p), qc);
+                const float2 m0 = mloc[m], m1 = mloc[MT + m];
+                const float2 mm = make_float2(m0.x + m1.x, m0.y + m1.y);
+                float2* mslot = xm + (buf * 4 + (int)rank) * MT + m;
+                *mslot = mm;
+                for (int p = 0; p < CS; ++p)
+                    if (p != (int)rank) st_peer_f32x2(peer_addr(mslot, (uint32_t)p), mm);
+                fence_cluster();
+            }
+            producers_sync();
+            if (CS > 1) {
+                if (tid == 0)
+                    for (int p = 0; p < CS; ++p)
+                        if (p != (int)rank) arrive_peer(peer_addr(xbar + buf, (uint32_t)p));
+                wait_cluster(xbar + buf, (uint32_t)(k >> 1) & 1u, abort_flag, a.err);
+            }
+            float qsum = 0.0f;
+            float2 msum = make_float2(0.0f, 0.0f);
+            for (int p = 0; p < CS; ++p) {      // fixed order: identical on every rank
+                qsum += xq[(buf * 4 + p) * MT + m];
+                const float2 mp = xm[(buf * 4 + p) * MT + m];
+                msum.x += mp.x;
+                msum.y += mp.y;
+            }
+            const float q = qsum * cl.qscale;
+            const float mean_v = a.sf2 * msum.x, mean_w = a.sf2 * msum.y;
+            const float s = fmaxf(0.0f, a.sf2 - q);
+
+            // ---------------- dynamics and covariance (all ranks, all samples) -----
+            float sn, cs;
+            sincosf(mu2, &sn, &cs);
+            const float a02 = -a.dt * mu3 * sn, a03 = a.dt * cs;
+            const float a12 = a.dt * mu3 * cs, a13 = a.dt * sn;
+            const float nX = mu0 + a.dt * mu3 * cs;
+            const float nY = mu1 + a.dt * mu3 * sn;
+            const float nT = mu2 + a.dt * mu4;
+            const float nV = mu3 + a.kv * (ut.x - mu3) + mean_v;
+            const float nW = mu4 + a.kw * (ut.y - mu4) + mean_w;
+            mu0 = nX; mu1 = nY; mu2 = nT; mu3 = nV; mu4 = nW;
+            {
+                const float B00 = S00 + a02 * S02 + a03 * S03, B01 = S01 + a02 * S12 + a03 * S13,
+                            B02 = S02 + a02 * S22 + a03 * S23, B03 = S03 + a02 * S23 + a03 * S33,
+                            B04 = S04 + a02 * S24 + a03 * S34;
+                const float B11 = S11 + a12 * S12 + a13 * S13, B12 = S12 + a12 * S22 + a13 * S23,
+                            B13 = S13 + a12 * S23 + a13 * S33, B14 = S14 + a12 * S24 + a13 * S34;
+                const float B22 = S22 + a.dt * S24, B23 = S23 + a.dt * S34, B24 = S24 + a.dt * S44;
+                const float B33 = a.av * S33, B34 = a.av * S34;
+                const float B44 = a.aw * S44;
+                S00 = B00 + a02 * B02 + a03 * B03;
+                S01 = B01 + a12 * B02 + a13 * B03;
+                S02 = B02 + a.dt * B04;
+                S03 = a.av * B03;
+                S04 = a.aw * B04;
+                S11 = B11 + a12 * B12 + a13 * B13;
+                S12 = B12 + a.dt * B14;
+                S13 = a.av * B13;
+                S14 = a.aw * B14;
+                S22 = B22 + a.dt * B24;
+                S23 = a.av * B23;
+                S24 = a.aw * B24;
+                S33 = a.av * B33 + s;
+                S34 = a.aw * B34;
+                S44 = a.aw * B44 + s;
+            }
+            // the post-step state of sample m for the rank that scores it
+            if (u == 0 && (m % CS) == (int)rank) {
+                float* o = sst + (m / CS) * 24;
+                o[0] = mu0; o[1] = mu1; o[2] = mu2; o[3] = mu3; o[4] = mu4;
+                o[5] = S00; o[6] = S01; o[7] = S02; o[8] = S03; o[9] = S04;
+                o[10] = S11; o[11] = S12; o[12] = S13; o[13] = S14;
+                o[14] = S22; o[15] = S23; o[16] = S24;
+                o[17] = S33; o[18] = S34; o[19] = S44;
+                o[20] = s;
+            }
+            producers_sync();
+            // ---------------- cost phase: RC threads per scored sample -------------
+            {
+                const float* o = sst + ci * 24;
+                const float px = o[0], py = o[1];
+                float sxx = o[5], sxy = o[6], syy = o[10];
+                if (a.nom_sxy) {
+                    sxx = __ldg(a.nom_sxy + 3 * k);
+                    sxy = __ldg(a.nom_sxy + 3 * k + 1);
+                    syy = __ldg(a.nom_sxy + 3 * k + 2);
+                }
+                const float lmax = fmaxf(0.0f, 0.5f * (sxx + syy) + hypotf(0.5f * (sxx - syy), sxy));
+                float om = FLT_MAX;
+                for (int ob = cpart; ob < a.O; ob += RC) {
+                    const float cx = obsp[3 * ob], cy = obsp[3 * ob + 1], R = obsp[3 * ob + 2];
+                    const float dx = px - cx, dy = py - cy;
+                    const float rho = sqrtf(dx * dx + dy * dy);
+                    float spread;
+                    if (rho > 1e-9f) {
+                        const float nx = dx / rho, ny = dy / rho;
+                        spread = sqrtf(fmaxf(0.0f, nx * nx * sxx + 2.0f * nx * ny * sxy + ny * ny * syy));
+                    } else {
+                        spread = sqrtf(lmax);
+                    }
+                    om = fminf(om, (rho - R) - a.phi_inv * spread);
+                }
+                float best = FLT_MAX;
+                for (int gsg = cpart; gsg < a.S; gsg += RC) {
+                    const float4 sg = segp[gsg];
+                    const float il2 = il2p[gsg];
+                    const float qx0 = px - sg.x, qy0 = py - sg.y;
+                    const float t = fminf(fmaxf((qx0 * sg.z + qy0 * sg.w) * il2, 0.0f), 1.0f);
+                    const float qx = qx0 - t * sg.z, qy = qy0 - t * sg.w;
+                    best = fminf(best, qx * qx + qy * qy);
+                }
+                ep[tid] = best;
+                omh[tid] = om;
+                producers_sync();
+                if (cpart == 0) {
+                    float omargin = omh[ci], e2min = ep[ci];
+                    for (int i = 1; i < RC; ++i) {
+                        omargin = fminf(omargin, omh[i * nown + ci]);
+                        e2min = fminf(e2min, ep[i * nown + ci]);
+                    }
+                    const float e_lane = sqrtf(e2min);
+                    const float rbar = a.r - a.sq_chi2 * sqrtf(lmax);
+                    const float sv = o[20], vv = o[3];
+                    float stage = a.c_var * (sv + sv) + a.c_speed * (a.v_des - vv) * (a.v_des - vv);
+                    if (omargin <= 0.0f) stage += a.c_coll;
+                    const float lmargin = e_lane - rbar;
+                    stage += a.c_dev * e_lane;
+                    if (lmargin > 0.0f) stage += a.c_lane * disc;
+                    stage += goal_cost(a, k, px, py);                     // Eq. 12 goal terms
+                    cost += stage;
+                    if (TRACE && cactive) {
+                        const size_t sk = (size_t)sc_me * a.T + k;
+                        if (a.tr_mu)
+                            for (int i = 0; i < 5; ++i) a.tr_mu[sk * 5 + i] = o[i];
+                        if (a.tr_sig)
+                            for (int i = 0; i < 15; ++i) a.tr_sig[sk * 15 + i] = o[5 + i];
+                        if (a.tr_stage) a.tr_stage[sk] = stage;
+                        if (a.tr_margin) {
+                            a.tr_margin[sk * 2] = lmargin;
+                            a.tr_margin[sk * 2 + 1] = (a.O > 0) ? omargin : __int_as_float(0x7f800000);
+                        }
+                    }
+                }
+                disc *= 0.9f;
+            }
+        }
+        if (cpart == 0 && cactive && a.costs) a.costs[sc_me] = cost;
+    }
+    // no CTA leaves while a peer may still write into its shared memory
+    tc::fence_before_sync();
+    __syncthreads();
+    cluster_sync_all();
+    if (warp == 0) tc::tmem_dealloc(taddr, 128);
+}
+
+}  // namespace
+
+int cl_smem_bytes(const ClArgs& cl, int S, int O) {
+    return cl_layout(cl.npc, cl.scene_smem ? S : 0, cl.scene_smem ? O : 0).total;
+}
+
+// whether at least one cluster of this shape fits on the device
+bool cl_schedulable(const ClArgs& cl, int S, int O, int device) {
+    (void)device;
+    const int smem = cl_smem_bytes(cl, S, O);
+    if (cudaFuncSetAttribute(k_rollout_cl<0, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+        cudaSuccess)
+        return false;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)cl.cs);
+    cfg.blockDim = dim3(THREADS);
+    cfg.dynamicSmemBytes = (size_t)smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)cl.cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, k_rollout_cl<0, false>, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return nclusters > 0;
+}
+
+int launch_rollout_cl(const RolloutArgs& a, const ClArgs& cl, int fmt, bool trace, cudaStream_t st) {
+    const int smem = cl_smem_bytes(cl, a.S, a.O);
+    const int ntile = (a.K + MT - 1) / MT;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(ntile * cl.cs));
+    cfg.blockDim = dim3(THREADS);
+    cfg.dynamicSmemBytes = (size_t)smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)cl.cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e;
+    if (fmt == 0) {
+        if (trace) {
+            GPM_CUDA(cudaFuncSetAttribute(k_rollout_cl<0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+            e = cudaLaunchKernelEx(&cfg, k_rollout_cl<0, true>, a, cl);
+        } else {
+            GPM_CUDA(cudaFuncSetAttribute(k_rollout_cl<0, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+            e = cudaLaunchKernelEx(&cfg, k_rollout_cl<0, false>, a, cl);
+        }
+    } else {
+        if (trace) {
+            GPM_CUDA(cudaFuncSetAttribute(k_rollout_cl<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+            e = cudaLaunchKernelEx(&cfg, k_rollout_cl<1, true>, a, cl);
+        } else {
+            GPM_CUDA(cudaFuncSetAttribute(k_rollout_cl<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+            e = cudaLaunchKernelEx(&cfg, k_rollout_cl<1, false>, a, cl);
+        }
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "launch_rollout_cl");
+    GPM_CUDA(cudaGetLastError());
+    return 0;
+}
+
+}  // namespace gpm
