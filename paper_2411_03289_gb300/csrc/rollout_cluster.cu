@@ -267,6 +267,12 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_cl(const RolloutArgs a, 
         if (lane == 0) {
             const uint32_t idesc128 = tc::idesc_f16(FMT, MT, 128);
             const uint32_t idesc64 = tc::idesc_f16(FMT, MT, 64);
+            // base descriptors: A stages (K-major, 128 rows) and the resident B
+            // pieces (128 or 64 rows); all offsets below are multiples of 16 bytes
+            // and stay inside shared memory, so they add to the start-address field
+            const uint64_t dA0 = tc::smem_desc(tc::smem_addr(sm + L.a), MT * 16, 128);
+            const uint64_t dB128 = tc::smem_desc(tc::smem_addr(bres), 128 * 16, 128);
+            const uint64_t dB64 = tc::smem_desc(tc::smem_addr(bres), 64 * 16, 128);
             bool ok = wait_or_abort(b_res, 0, abort_flag, a.err);
             tc::fence_after_sync();
             uint32_t n = 0;
@@ -286,29 +292,27 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_cl(const RolloutArgs a, 
 #pragma unroll
                     for (int h = 0; h < GCH; ++h) {
                         const int cc = c + h;
-                        const uint32_t aHi = tc::smem_addr(sm + L.a + st * A_STAGE + h * A_CHUNK), aLo = aHi + A_PART;
-                        const uint64_t dAh = tc::smem_desc(aHi, MT * 16, 128);
-                        const uint64_t dAl = tc::smem_desc(aLo, MT * 16, 128);
+                        // descriptors by adds on precomputed bases (no per-MMA rebuild:
+                        // the single issuing thread is otherwise the bottleneck)
+                        const uint64_t dAh = dA0 + (uint64_t)((st * A_STAGE + h * A_CHUNK) >> 4);
+                        const uint64_t dAl = dAh + (uint64_t)(A_PART >> 4);
                         if (cc < nboth) {
                             // both slices: one 128-row piece, D columns 0 .. 127
-                            const uint32_t bHi = tc::smem_addr(bres) + (uint32_t)cc * 8192u;
-                            const uint64_t dBh = tc::smem_desc(bHi, 128 * 16, 128);
-                            const uint64_t dBl = tc::smem_desc(bHi + 4096u, 128 * 16, 128);
+                            const uint64_t dBh = dB128 + (uint64_t)((cc * 8192) >> 4);
+                            const uint64_t dBl = dBh + (uint64_t)(4096 >> 4);
                             tc::mma_f16(taddr, dAh, dBh, idesc128, cc > 0 ? 1u : 0u);
                             tc::mma_f16(taddr, dAh, dBl, idesc128, 1u);
                             tc::mma_f16(taddr, dAl, dBh, idesc128, 1u);
                         } else {
                             // the upper slice alone: a 64-row piece, D columns 64 .. 127
-                            const uint32_t bHi = tc::smem_addr(bres) + (uint32_t)nboth * 8192u +
-                                                 (uint32_t)(cc - nboth) * 4096u;
-                            const uint64_t dBh = tc::smem_desc(bHi, 64 * 16, 128);
-                            const uint64_t dBl = tc::smem_desc(bHi + 2048u, 64 * 16, 128);
+                            const uint64_t dBh = dB64 + (uint64_t)((nboth * 8192 + (cc - nboth) * 4096) >> 4);
+                            const uint64_t dBl = dBh + (uint64_t)(2048 >> 4);
                             tc::mma_f16(taddr + 64u, dAh, dBh, idesc64, 1u);
                             tc::mma_f16(taddr + 64u, dAh, dBl, idesc64, 1u);
                             tc::mma_f16(taddr + 64u, dAl, dBh, idesc64, 1u);
                         }
                     }
-                    // one commit per stage: each tcgen05.commit stalls the tensor pipe
+                    // one commit per stage releases both of its chunks
                     tc::mma_commit(empty + st);
                 }
                 if (!ok) break;

@@ -194,6 +194,10 @@ __device__ __forceinline__ void rollout_mma_body(const RolloutArgs& a, const Mma
         if (lane != 0 || NB == 0) return;       // one thread per role
         const bool issuer = (warp == NPROD / 32);
         const uint32_t idesc = tc::idesc_f16(FMT, MT, BLK);
+        // base descriptors of stage 0's A tile (128 rows) and B pieces (128 rows);
+        // stage and block offsets are multiples of 16 bytes inside shared memory
+        const uint64_t dA0 = tc::smem_desc(tc::smem_addr(sm), MT * 16, 128);
+        const uint64_t dB0 = tc::smem_desc(tc::smem_addr(sm), BLK * 16, 128);
         uint32_t n = 0, pc = 0;
         for (int k = 0; k < a.T; ++k) {
             for (int g = 0; g < npass; ++g, ++pc) {
@@ -227,14 +231,15 @@ __device__ __forceinline__ void rollout_mma_body(const RolloutArgs& a, const Mma
                         if (!wait_or_abort(a_full + st, use & 1u, abort_flag, a.err)) continue;
                         if (!wait_or_abort(b_full + st, use & 1u, abort_flag, a.err)) continue;
                         tc::fence_after_sync();
-                        const uint32_t aHi = tc::smem_addr(stage), aLo = aHi + A_PART;
-                        const uint64_t dAh = tc::smem_desc(aHi, MT * 16, 128);
-                        const uint64_t dAl = tc::smem_desc(aLo, MT * 16, 128);
-                        for (int b = b0; b < b1; ++b) {
-                            if (c >= 8 * b + 8) continue;
-                            const uint32_t bHi = aHi + 2 * A_PART + (b - b0) * B_PART;
-                            const uint64_t dBh = tc::smem_desc(bHi, BLK * 16, 128);
-                            const uint64_t dBl = tc::smem_desc(bHi + BLOCKS_PER_PASS * B_PART, BLK * 16, 128);
+                        // descriptors by adds on precomputed bases: rebuilding them per
+                        // MMA makes the single issuing thread the bottleneck
+                        const uint64_t dAh = dA0 + (uint64_t)((st * STAGE) >> 4);
+                        const uint64_t dAl = dAh + (uint64_t)(A_PART >> 4);
+                        int ba = b0;                               // first block active at chunk c
+                        while (ba < b1 && c >= 8 * ba + 8) ++ba;
+                        for (int b = ba; b < b1; ++b) {
+                            const uint64_t dBh = dB0 + (uint64_t)((st * STAGE + 2 * A_PART + (b - b0) * B_PART) >> 4);
+                            const uint64_t dBl = dBh + (uint64_t)((BLOCKS_PER_PASS * B_PART) >> 4);
                             const uint32_t d = taddr + (uint32_t)((b - b0) * BLK);
                             tc::mma_f16(d, dAh, dBh, idesc, c > 0 ? 1u : 0u);
                             tc::mma_f16(d, dAh, dBl, idesc, 1u);
