@@ -10,7 +10,7 @@
 // rank).  Their pieces of cB L^-1 (hi and lo, at most 144 KiB) are copied into
 // shared memory once, before the first step, so a step moves no factor
 // tiles at all: the MMAs read resident B and the kernel-row tiles A that the
-// producer warps write into a three-stage ring.  This matters because a
+// producer warps write into a two-stage ring.  This matters because a
 // 128 x 128 x 16 MMA reads 8 KiB of operands from shared memory, which is
 // the whole shared-memory bandwidth at the tensor rate; streaming the factor
 // through the same shared memory every step halved the MMA rate.
@@ -38,7 +38,8 @@ constexpr int MT = 128;               // samples per cluster (the MMA M)
 constexpr int NPROD = 256;            // producer threads: two per sample
 constexpr int THREADS = NPROD + 32;   // + the MMA-issuing warp
 constexpr int NSTAGE = 2;             // kernel-row tile ring
-constexpr int GCH = 2;                // chunks per stage: one tcgen05.commit per stage
+constexpr int GCH = 2;                // chunks per stage: one hand-off per two chunks
+constexpr int BURST = 2;              // chunks whose kernel rows a thread computes together
 constexpr int A_PART = MT * 16 * 2;   // 4 KiB: one 16-bit part of a 128 x 16 tile
 constexpr int A_CHUNK = 2 * A_PART;   // hi + lo of one chunk
 constexpr int A_STAGE = GCH * A_CHUNK;
@@ -312,7 +313,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_cl(const RolloutArgs a, 
                             tc::mma_f16(taddr + 64u, dAl, dBh, idesc64, 1u);
                         }
                     }
-                    // one commit per stage releases both of its chunks
+                    // the commit releases the stage once its MMAs completed
                     tc::mma_commit(empty + st);
                 }
                 if (!ok) break;
@@ -362,7 +363,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_cl(const RolloutArgs a, 
             const float z2 = ut.x * a.zscale[2], z3 = ut.y * a.zscale[3];
 
             // ---------------- kernel-row tiles (8 points per thread per chunk) ----
-            // Two chunks per burst (16 independent exp2 in flight).  The GP mean
+            // BURST chunks per burst (16 independent exp2 in flight).  The GP mean
             // is split between the ranks: rank r sums chunks [mc0, mc1), the
             // part of them beyond its own tiles (the highest rank) computed
             // for the mean alone.
@@ -388,33 +389,35 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_cl(const RolloutArgs a, 
                 kahan_add(mv, cv, pv);
                 kahan_add(mw, cw, pw);
             };
-            for (int c = 0; c < nch; c += 2) {
-                float av0[8], av1[8];
-                kernel_row(c, av0);
-                kernel_row(c + 1, av1);
-                if (c >= mc0 && c < mc1) mean_part(c, av0);
-                if (c + 1 >= mc0 && c + 1 < mc1) mean_part(c + 1, av1);
-                uint32_t hw[2][4], lw[2][4];
+            for (int c = 0; c < nch; c += BURST) {      // nch is a multiple of 4 (and of BURST)
+                float av[BURST][8];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    split2<FMT>(av0[2 * q], av0[2 * q + 1], &hw[0][q], &lw[0][q]);
-                    split2<FMT>(av1[2 * q], av1[2 * q + 1], &hw[1][q], &lw[1][q]);
-                }
-                {
+                for (int h = 0; h < BURST; ++h) kernel_row(c + h, av[h]);
+#pragma unroll
+                for (int h = 0; h < BURST; ++h)
+                    if (c + h >= mc0 && c + h < mc1) mean_part(c + h, av[h]);
+                uint32_t hw[BURST][4], lw[BURST][4];
+#pragma unroll
+                for (int h = 0; h < BURST; ++h)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) split2<FMT>(av[h][2 * q], av[h][2 * q + 1], &hw[h][q], &lw[h][q]);
+#pragma unroll
+                for (int h = 0; h < BURST; ++h) {
+                    const int slot = (c + h) % GCH;        // chunk's place in its stage
                     const int st = (int)(n % NSTAGE);
                     const uint32_t use = n / NSTAGE;
-                    if (n >= (uint32_t)NSTAGE) wait_or_abort(empty + st, (use - 1) & 1u, abort_flag, a.err);
-#pragma unroll
-                    for (int h = 0; h < GCH; ++h) {
-                        // slab u (points 8u .. 8u + 7) of row m of chunk c + h
-                        unsigned char* ph = sm + L.a + st * A_STAGE + h * A_CHUNK + u * (MT * 16) + m * 16;
-                        *reinterpret_cast<uint4*>(ph) = make_uint4(hw[h][0], hw[h][1], hw[h][2], hw[h][3]);
-                        *reinterpret_cast<uint4*>(ph + A_PART) = make_uint4(lw[h][0], lw[h][1], lw[h][2], lw[h][3]);
+                    if (slot == 0 && n >= (uint32_t)NSTAGE)
+                        wait_or_abort(empty + st, (use - 1) & 1u, abort_flag, a.err);
+                    // slab u (points 8u .. 8u + 7) of row m of chunk c + h
+                    unsigned char* ph = sm + L.a + st * A_STAGE + slot * A_CHUNK + u * (MT * 16) + m * 16;
+                    *reinterpret_cast<uint4*>(ph) = make_uint4(hw[h][0], hw[h][1], hw[h][2], hw[h][3]);
+                    *reinterpret_cast<uint4*>(ph + A_PART) = make_uint4(lw[h][0], lw[h][1], lw[h][2], lw[h][3]);
+                    if (slot == GCH - 1) {
+                        tc::fence_proxy_async();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(a_full + st);
+                        ++n;
                     }
-                    tc::fence_proxy_async();
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(a_full + st);
-                    ++n;
                 }
             }
             for (int c = (mc0 > nch ? mc0 : nch); c < mc1; ++c) {
