@@ -23,7 +23,8 @@ LIB_PATH = os.path.join(LIB_DIR, "libgpmppi.so")
 
 SOURCES = ["abi.cu", "gp_fit.cu", "rollout_fp32.cu", "rollout_mma.cu", "mma_selftest.cu",
            "mppi_aux.cu", "update_noalloc.cu", "batch.cu", "adjoint.cu",
-           "ensemble.cu", "terrain_qp.cu", "rollout_cluster.cu"]
+           "ensemble.cu", "terrain_qp.cu", "rollout_cluster.cu",
+           "lane_grid.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "-I", INCLUDE, "-I", CSRC]

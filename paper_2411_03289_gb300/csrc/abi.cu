@@ -120,6 +120,8 @@ void free_ctrl(gpmppi_ctrl c) {
     cudaFree(c->partial);
     cudaFree(c->counter);
     cudaFree(c->nom_sxy);
+    cudaFree(c->gcell);
+    cudaFree(c->gidx);
     cudaFree(c->err);
     cudaFree(c->grad_scr);
     for (cudaEvent_t e : c->ev)
@@ -222,6 +224,13 @@ RolloutArgs gpm::make_rollout_args(gpmppi_ctrl c, const float* state, const floa
     a.v_des = p.v_desired;
     a.sq_chi2 = (float)c->sq_chi2;
     a.phi_inv = (float)c->phi_inv;
+    a.gcell = c->gcell;
+    a.gidx = c->gidx;
+    a.gx0 = c->gx0;
+    a.gy0 = c->gy0;
+    a.ginv = c->ginv;
+    a.gnx = c->gnx;
+    a.gny = c->gny;
     a.c_goal = p.beta[2];
     a.c_term = (float)((double)p.beta[3] * p.P_goal);
     a.goal_x = p.goal[0];
@@ -454,6 +463,31 @@ int mppi_create(const gpmppi_params* p, const float* obstacles, int32_t O, const
         if (e != cudaSuccess) {
             free_ctrl(c);
             return cuda_fail(e, "mppi_create: upload");
+        }
+        {
+            // candidate segments per cell of a grid over the path (exact nearest-segment search)
+            LaneGridHost lg;
+            if ((rc = build_lane_grid(path, P, lg))) {
+                free_ctrl(c);
+                return rc;
+            }
+            if (!lg.cells.empty()) {
+                cudaError_t e2 = cudaMalloc(&c->gcell, sizeof(int2) * lg.cells.size());
+                if (e2 == cudaSuccess) e2 = cudaMalloc(&c->gidx, sizeof(int) * (lg.idx.empty() ? 1 : lg.idx.size()));
+                if (e2 == cudaSuccess)
+                    e2 = cudaMemcpy(c->gcell, lg.cells.data(), sizeof(int2) * lg.cells.size(), cudaMemcpyHostToDevice);
+                if (e2 == cudaSuccess && !lg.idx.empty())
+                    e2 = cudaMemcpy(c->gidx, lg.idx.data(), sizeof(int) * lg.idx.size(), cudaMemcpyHostToDevice);
+                if (e2 != cudaSuccess) {
+                    free_ctrl(c);
+                    return cuda_fail(e2, "mppi_create: lane grid");
+                }
+                c->gx0 = lg.x0;
+                c->gy0 = lg.y0;
+                c->ginv = lg.inv_h;
+                c->gnx = lg.nx;
+                c->gny = lg.ny;
+            }
         }
         if (gp->g.Np > 0 && (rc = make_w_tensor_map(&c->tmW, gp->g.W[0], gp->g.Np))) {
             free_ctrl(c);

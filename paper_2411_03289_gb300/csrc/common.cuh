@@ -10,6 +10,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "gpmppi.h"
 
@@ -167,6 +168,11 @@ struct RolloutArgs {
     float c_speed;          // alpha_4
     float c_coll;           // beta_1 * P_coll
     float r, v_des, sq_chi2, phi_inv;
+    // candidate segments of the lane-distance grid (lane_grid.cu); gcell null: scan all
+    const int2* gcell;      // gny x gnx cells: (offset into gidx, count)
+    const int* gidx;
+    float gx0, gy0, ginv;   // grid origin and 1 / cell size
+    int gnx, gny;
     float c_goal;           // beta_2: weight of the distance to the goal (every stage)
     float c_term;           // beta_3 * P_goal: terminal miss penalty
     float goal_x, goal_y, goal_r;
@@ -192,6 +198,24 @@ struct MmaArgs {
     int scene_smem;         // lane segments and obstacles staged in shared memory
 };
 
+// The lane segments to scan for the point (px, py): (offset into gidx, count),
+// or (-1, S) for every segment when the point lies outside the grid.
+__device__ __forceinline__ int2 lane_cands(const RolloutArgs& a, float px, float py) {
+    if (a.gcell) {
+        const float fx = (px - a.gx0) * a.ginv, fy = (py - a.gy0) * a.ginv;
+        if (fx >= 0.0f && fy >= 0.0f && fx < (float)a.gnx && fy < (float)a.gny) {
+            const int ix = min((int)fx, a.gnx - 1), iy = min((int)fy, a.gny - 1);
+            return __ldg(a.gcell + iy * a.gnx + ix);
+        }
+    }
+    return make_int2(-1, a.S);
+}
+
+// i-th segment of a candidate range from lane_cands
+__device__ __forceinline__ int lane_seg(const RolloutArgs& a, int2 oc, int i) {
+    return oc.x < 0 ? i : __ldg(a.gidx + oc.x + i);
+}
+
 // Goal terms of Eq. 12 at stage k (0-based) for the mean position (x, y):
 // c_goal |p - goal| at every stage, plus c_term on the last stage when the
 // mean is farther than goal_r from the goal.
@@ -203,6 +227,15 @@ __device__ __forceinline__ float goal_cost(const RolloutArgs& a, int k, float x,
     if (k == a.T - 1 && d > a.goal_r) c += a.c_term;
     return c;
 }
+
+// Host side of the lane-distance grid (built once per controller).
+struct LaneGridHost {
+    float x0 = 0, y0 = 0, inv_h = 0;
+    int nx = 0, ny = 0;
+    std::vector<int2> cells;
+    std::vector<int> idx;
+};
+int build_lane_grid(const float* path, int P, LaneGridHost& g);
 
 // One terrain GP of an ensemble (Eq. 3) as the ensemble rollout reads it.
 struct TerrainGp {

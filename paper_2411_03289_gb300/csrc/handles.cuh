@@ -29,6 +29,10 @@ struct gpmppi_ctrl_s {
     float* partial = nullptr;     // n_upd x T x 2
     unsigned int* counter = nullptr;
     float* nom_sxy = nullptr;     // T x 3
+    int2* gcell = nullptr;        // lane-distance grid (null: scan every segment)
+    int* gidx = nullptr;
+    float gx0 = 0, gy0 = 0, ginv = 0;
+    int gnx = 0, gny = 0;
     unsigned int* err = nullptr;  // device status word written by the rollout
     int stages = 2;               // per-warp TMA pipeline depth
     CUtensorMap tmW;              // TMA map over the GP's W

@@ -562,7 +562,9 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_cl(const RolloutArgs a, 
                     om = fminf(om, (rho - R) - a.phi_inv * spread);
                 }
                 float best = FLT_MAX;
-                for (int gsg = cpart; gsg < a.S; gsg += RC) {
+                const int2 oc = lane_cands(a, px, py);     // candidate segments of this position
+                for (int i = cpart; i < oc.y; i += RC) {
+                    const int gsg = lane_seg(a, oc, i);
                     const float4 sg = segp[gsg];
                     const float il2 = il2p[gsg];
                     const float qx0 = px - sg.x, qy0 = py - sg.y;

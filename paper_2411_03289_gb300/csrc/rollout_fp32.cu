@@ -410,7 +410,9 @@ __global__ void __launch_bounds__(THREADS, 1)
             const int m = lane % MTP;
             const float2 pp = pos[m];
             float best = FLT_MAX;
-            for (int g = warp * SUB + lane / MTP; g < a.S; g += THREADS / MTP) {
+            const int2 oc = lane_cands(a, pp.x, pp.y);     // candidate segments of this position
+            for (int i = warp * SUB + lane / MTP; i < oc.y; i += THREADS / MTP) {
+                const int g = lane_seg(a, oc, i);
                 const float4 sg = __ldg(a.seg + g);
                 const float il2 = __ldg(a.seg_il2 + g);
                 const float px = pp.x - sg.x, py = pp.y - sg.y;

@@ -445,7 +445,9 @@ __device__ __forceinline__ void rollout_mma_body(const RolloutArgs& a, const Mma
         }
         // ---------------- P5: lane distance (segments split by half) -------
         float best = FLT_MAX;
-        for (int gsg = u; gsg < a.S; gsg += R) {
+        const int2 oc = lane_cands(a, mu0, mu1);           // candidate segments of this position
+        for (int i = u; i < oc.y; i += R) {
+            const int gsg = lane_seg(a, oc, i);
             const float4 sg = segp[gsg];
             const float il2 = il2p[gsg];
             const float px = mu0 - sg.x, py = mu1 - sg.y;

@@ -203,7 +203,9 @@ __device__ __forceinline__ void lane_nearest(const RolloutArgs& a, float px, flo
     const int lane = threadIdx.x & 31;
     best = FLT_MAX;
     bi = 0x7fffffff;
-    for (int gI = lane; gI < a.S; gI += 32) {
+    const int2 oc = lane_cands(a, px, py);                 // candidate segments of this position
+    for (int i = lane; i < oc.y; i += 32) {
+        const int gI = lane_seg(a, oc, i);
         const float4 sg = __ldg(a.seg + gI);
         const float il2 = __ldg(a.seg_il2 + gI);
         const float qx0 = px - sg.x, qy0 = py - sg.y;
