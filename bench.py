@@ -389,8 +389,12 @@ def run_ours(args):
         flops = rollout_flops_per_sample_step(sc.N, sc.obstacles.shape[0], S_seg) * P.K * P.T
     r_avg = sum(rollout_ms) / len(rollout_ms)
     achieved = flops / (r_avg / 1e3) / 1e12
-    traffic = committed_traffic("ensemble" if terrain else ("rollout_fp32" if P.precision == 0 else "rollout_mma"),
-                                args.workload)
+    kind = gp.mppi_rollout_kind(ctrl)
+    src, kname = {gp.GPMPPI_KERNEL_FP32: ("rollout_fp32", "k_rollout_fp32"),
+                  gp.GPMPPI_KERNEL_TC_STREAM: ("rollout_mma", "k_rollout_mma"),
+                  gp.GPMPPI_KERNEL_TC_CLUSTER: ("rollout_cluster", "k_rollout_cl"),
+                  gp.GPMPPI_KERNEL_ENSEMBLE: ("ensemble", "k_rollout_ens")}[kind]
+    traffic = committed_traffic(src, args.workload)
     if terrain:
         roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak_tflops(2070.0), "unit": "TFLOP/s",
                 "traffic": traffic, "kernel": "k_rollout_ens",
@@ -403,7 +407,7 @@ def run_ours(args):
     else:
         peak, note = measured_tensor_peak()
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "traffic": traffic, "kernel": "k_rollout_mma", "peak_note": note}
+                "traffic": traffic, "kernel": kname, "peak_note": note}
     roof["frac"] = roof["achieved"] / roof["peak"]
     fp32 = None
     if P.precision != 0 and not args.no_fp32_path:

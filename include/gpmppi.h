@@ -179,6 +179,17 @@ int mppi_get_iteration(gpmppi_ctrl c, uint64_t* it);
  * (Alg. 1 Step 2), T x 3 floats (Sxx, Sxy, Syy) of Sigma_XY(k+1), device. */
 int mppi_nominal_sxy(gpmppi_ctrl c, float* sxy, void* stream);
 
+/* Which rollout kernel mppi_step runs for this controller (host int32):
+ * GPMPPI_KERNEL_FP32 (CUDA cores), GPMPPI_KERNEL_TC_STREAM (tensor cores,
+ * factor tiles streamed per step), GPMPPI_KERNEL_TC_CLUSTER (tensor cores,
+ * factor resident in a CTA cluster; split precisions with N <= 512 when the
+ * cluster fits the device) or GPMPPI_KERNEL_ENSEMBLE (terrain ensemble). */
+#define GPMPPI_KERNEL_FP32 0
+#define GPMPPI_KERNEL_TC_STREAM 1
+#define GPMPPI_KERNEL_TC_CLUSTER 2
+#define GPMPPI_KERNEL_ENSEMBLE 3
+int mppi_rollout_kind(gpmppi_ctrl c, int32_t* kind);
+
 /* Per-kernel timing of mppi_step.  When enabled, mppi_step records CUDA
  * events on its stream around the rollout kernel and around the update
  * kernel(s); mppi_last_profile waits for the last step's events and returns

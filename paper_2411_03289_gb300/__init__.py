@@ -31,11 +31,15 @@ GPMPPI_VAR_NOMINAL = 1
 GPMPPI_FP32 = 0
 GPMPPI_BF16_SPLIT = 1
 GPMPPI_FP16_SPLIT = 2
+GPMPPI_KERNEL_FP32 = 0
+GPMPPI_KERNEL_TC_STREAM = 1
+GPMPPI_KERNEL_TC_CLUSTER = 2
+GPMPPI_KERNEL_ENSEMBLE = 3
 
 # names every build of the library exports (checked by the CPU test suite)
 EXPORTS = ("gp_fit", "gp_destroy", "gp_factors", "gp_predict", "mppi_create", "mppi_step",
            "mppi_rollout_trace", "mppi_set_iteration", "mppi_get_iteration", "mppi_nominal_sxy",
-           "mppi_destroy", "mppi_set_profiling", "mppi_last_profile", "mppi_device_status", "mppi_grad",
+           "mppi_destroy", "mppi_rollout_kind", "mppi_set_profiling", "mppi_last_profile", "mppi_device_status", "mppi_grad",
            "mppi_create_ensemble", "mppi_set_terrain_weights", "terrain_weights",
            "mppi_update_noalloc", "mppi_batch_create",
            "mppi_batch_buffers", "mppi_batch_step", "mppi_batch_graph", "mppi_batch_autotune",
@@ -93,6 +97,7 @@ def load():
         "mppi_get_iteration": [vp, ctypes.POINTER(u64)],
         "mppi_nominal_sxy": [vp, vp, vp],
         "mppi_destroy": [vp],
+        "mppi_rollout_kind": [vp, vp],
         "mppi_set_profiling": [vp, i32],
         "mppi_last_profile": [vp, vp, vp],
         "mppi_device_status": [vp],
@@ -343,6 +348,13 @@ def mppi_get_iteration(ctrl: Ctrl) -> int:
 def mppi_nominal_sxy(ctrl: Ctrl, out, stream=None):
     _check(load().mppi_nominal_sxy(ctrl.handle, _dptr(out, numel=3 * ctrl.T, name="sxy"),
                                    _stream(stream)))
+
+
+def mppi_rollout_kind(ctrl: Ctrl) -> int:
+    """GPMPPI_KERNEL_* of the rollout kernel mppi_step runs for this controller."""
+    v = ctypes.c_int32()
+    _check(load().mppi_rollout_kind(ctrl.handle, ctypes.byref(v)))
+    return v.value
 
 
 def mppi_set_profiling(ctrl: Ctrl, on: bool):

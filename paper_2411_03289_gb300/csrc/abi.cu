@@ -829,6 +829,14 @@ int mppi_nominal_sxy(gpmppi_ctrl c, float* sxy, void* stream) {
     return GPMPPI_OK;
 }
 
+int mppi_rollout_kind(gpmppi_ctrl c, int32_t* kind) {
+    if (!valid_ctrl(c)) return fail(GPMPPI_ERR_INVALID_ARG, "mppi_rollout_kind: invalid handle");
+    if (!kind) return fail(GPMPPI_ERR_INVALID_ARG, "mppi_rollout_kind: kind is NULL");
+    *kind = c->ens ? GPMPPI_KERNEL_ENSEMBLE
+                   : (c->cl ? GPMPPI_KERNEL_TC_CLUSTER : (c->fmt >= 0 ? GPMPPI_KERNEL_TC_STREAM : GPMPPI_KERNEL_FP32));
+    return GPMPPI_OK;
+}
+
 int mppi_set_profiling(gpmppi_ctrl c, int32_t on) {
     if (!valid_ctrl(c)) return fail(GPMPPI_ERR_INVALID_ARG, "mppi_set_profiling: invalid handle");
     if (on && !c->ev[0])

@@ -116,6 +116,7 @@ def test_mma_threads_per_sample_layouts(lib, rps, monkeypatch):
     """Every producer layout (128, 64 or 32 samples per CTA) gives the same
     parity; K = 300 spans several CTAs with a ragged tail in each layout."""
     monkeypatch.setenv("GPMPPI_MMA_THREADS_PER_SAMPLE", str(rps))
+    monkeypatch.setenv("GPMPPI_NO_CLUSTER", "1")      # the streaming kernel's layouts
     sc = _sc("small", 2, K=300, N=333, T=6)
     g, ctrl = make_ctrl(lib, sc)
     fits = O.gp_fit(sc.X, sc.Y, sc.hyper)
@@ -133,6 +134,58 @@ def test_mma_scene_too_large_for_shared_memory(lib):
     t = np.linspace(0, 2 * np.pi, 6000)
     sc = sc.replace(path=np.stack([6 * np.cos(t), 3 * np.sin(t)], axis=1))
     g, ctrl = make_ctrl(lib, sc)
+    fits = O.gp_fit(sc.X, sc.Y, sc.hyper)
+    ro = O.rollout(sc, fits, sc.x0, sc.U0, 1)
+    tr = gpu_trace(lib, ctrl, sc, sc.x0, sc.U0, it=1)
+    check_trace(sc, ro, tr)
+
+
+def test_rollout_kind_per_workload(lib):
+    """Split precisions with N <= 512 take the cluster kernel (its factor share
+    resident in shared memory), larger N the streaming kernel, FP32 the CUDA
+    cores and terrain ensembles their own rollout."""
+    cases = [(_sc("small", 2, N=500), lib.GPMPPI_KERNEL_TC_CLUSTER),
+             (_sc("small", 1, N=100), lib.GPMPPI_KERNEL_TC_CLUSTER),
+             (_sc("small", 2, N=700), lib.GPMPPI_KERNEL_TC_STREAM),
+             (_sc("small", 0), lib.GPMPPI_KERNEL_FP32),
+             (S.terrain_scenario("small", M=2, N=30), lib.GPMPPI_KERNEL_ENSEMBLE)]
+    for sc, kind in cases:
+        _, ctrl = make_ctrl(lib, sc)
+        assert lib.mppi_rollout_kind(ctrl) == kind
+
+
+@pytest.mark.parametrize("N", [100, 200, 333, 512])
+@pytest.mark.parametrize("precision", [2, 1])
+def test_cluster_kernel_parity_and_streaming_agreement(lib, N, precision, monkeypatch):
+    """Cluster sizes 1, 2, 4 (N <= 128, <= 256, <= 512) against the oracle, and
+    the same controller on the streaming kernel: same costs and update."""
+    sc = _sc("small", precision, K=300, N=N, T=6)
+    g, ctrl = make_ctrl(lib, sc)
+    assert lib.mppi_rollout_kind(ctrl) == lib.GPMPPI_KERNEL_TC_CLUSTER
+    fits = O.gp_fit(sc.X, sc.Y, sc.hyper)
+    U = sc.U0.copy()
+    U[:, 1] = 0.4 * np.sin(np.arange(sc.params.T))
+    ro = O.rollout(sc, fits, sc.x0, U, 3)
+    tr = gpu_trace(lib, ctrl, sc, sc.x0, U, it=3)
+    check_trace(sc, ro, tr)
+    U_new, w, c = gpu_step(lib, ctrl, sc, sc.x0, U, it=3)
+    check_step(sc, ro, U, U_new, w, c)
+    monkeypatch.setenv("GPMPPI_NO_CLUSTER", "1")
+    _, ctrl2 = make_ctrl(lib, sc, g)
+    assert lib.mppi_rollout_kind(ctrl2) == lib.GPMPPI_KERNEL_TC_STREAM
+    U2, w2, c2 = gpu_step(lib, ctrl2, sc, sc.x0, U, it=3)
+    np.testing.assert_allclose(c2, c, rtol=1e-5, atol=1e-5)
+    assert np.max(np.abs(U2 - U_new)) <= TOL_U
+
+
+def test_cluster_kernel_scene_in_global_memory(lib):
+    """A scene too large to stage next to the resident factor share is read
+    from global memory by the cluster kernel: same parity."""
+    sc = _sc("small", 2, K=150, N=400, T=3, O=1500)
+    t = np.linspace(0, 2 * np.pi, 6000)
+    sc = sc.replace(path=np.stack([6 * np.cos(t), 3 * np.sin(t)], axis=1))
+    g, ctrl = make_ctrl(lib, sc)
+    assert lib.mppi_rollout_kind(ctrl) == lib.GPMPPI_KERNEL_TC_CLUSTER
     fits = O.gp_fit(sc.X, sc.Y, sc.hyper)
     ro = O.rollout(sc, fits, sc.x0, sc.U0, 1)
     tr = gpu_trace(lib, ctrl, sc, sc.x0, sc.U0, it=1)
