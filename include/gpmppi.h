@@ -45,7 +45,7 @@ extern "C" {
 #define GPMPPI_ERR_OOM (-4)           /* device allocation failed                 */
 #define GPMPPI_ERR_TIMEOUT (-5)       /* a bounded device wait gave up            */
 #define GPMPPI_ERR_NONFINITE (-6)     /* NaN or Inf in an input                   */
-#define GPMPPI_ERR_UNSUPPORTED (-7)   /* valid request this build does not serve  */
+#define GPMPPI_ERR_UNSUPPORTED (-7)   /* valid request this library does not serve */
 
 /* variance modes (where the tightening covariance comes from) */
 #define GPMPPI_VAR_PER_SAMPLE 0   /* each sample's own propagated Sigma (Eq. 10)     */
@@ -56,7 +56,7 @@ extern "C" {
 #define GPMPPI_BF16_SPLIT 1   /* tensor cores: BF16 hi/lo operands, 3 products, FP32 sums */
 #define GPMPPI_FP16_SPLIT 2   /* tensor cores: FP16 hi/lo operands, 3 products, FP32 sums */
 
-/* limits of this build */
+/* limits of this library */
 #define GPMPPI_MAX_N 4096         /* GP training points      */
 #define GPMPPI_MAX_T 1024         /* horizon                 */
 #define GPMPPI_MAX_K (1 << 24)    /* samples                 */
