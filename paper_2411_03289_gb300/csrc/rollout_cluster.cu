@@ -85,18 +85,59 @@ __device__ __forceinline__ void bulk_copy(void* dst, const void* src, uint32_t b
         : "memory");
 }
 
+// Packed FP32 pairs (f32x2: two lanes per 64-bit register, element 0 in the
+// low half).  The kernel rows are computed two training points at a time, so
+// one packed instruction does the work of two scalar ones.
+__device__ __forceinline__ uint64_t f2pack(float a, float b) {
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void f2unpack(uint64_t v, float& a, float& b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ uint64_t f2sub(uint64_t a, uint64_t b) {
+    uint64_t r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ uint64_t f2mul(uint64_t a, uint64_t b) {
+    uint64_t r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ uint64_t f2fma(uint64_t a, uint64_t b, uint64_t c) {
+    uint64_t r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+// 2^x (the hardware approximation; results below the normal range flush to 0,
+// far below what a 16-bit split operand can carry)
+__device__ __forceinline__ float ex2_ftz(float x) {
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// hi + lo split of the pair (a, b): hi = rn16(a, b), lo = rn16((a, b) - hi)
 template <int FMT>
-__device__ __forceinline__ void split2(float a, float b, uint32_t* hi, uint32_t* lo) {
+__device__ __forceinline__ void split2(uint64_t ab, uint32_t* hi, uint32_t* lo) {
+    float a, b;
+    f2unpack(ab, a, b);
     if (FMT == 0) {
         const __half2 h = __floats2half2_rn(a, b);
         const float2 hf = __half22float2(h);
-        const __half2 l = __floats2half2_rn(a - hf.x, b - hf.y);
+        float ra, rb;
+        f2unpack(f2sub(ab, f2pack(hf.x, hf.y)), ra, rb);
+        const __half2 l = __floats2half2_rn(ra, rb);
         *hi = *reinterpret_cast<const uint32_t*>(&h);
         *lo = *reinterpret_cast<const uint32_t*>(&l);
     } else {
         const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
         const float2 hf = __bfloat1622float2(h);
-        const __nv_bfloat162 l = __floats2bfloat162_rn(a - hf.x, b - hf.y);
+        float ra, rb;
+        f2unpack(f2sub(ab, f2pack(hf.x, hf.y)), ra, rb);
+        const __nv_bfloat162 l = __floats2bfloat162_rn(ra, rb);
         *hi = *reinterpret_cast<const uint32_t*>(&h);
         *lo = *reinterpret_cast<const uint32_t*>(&l);
     }
@@ -204,7 +245,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_cl(const RolloutArgs a, 
     float* ep = reinterpret_cast<float*>(sm + L.ep);
     float* omh = reinterpret_cast<float*>(sm + L.om);
     float4* xs_s = reinterpret_cast<float4*>(sm + L.xs);
-    float2* al_s = reinterpret_cast<float2*>(sm + L.al);
+    float4* al_s = reinterpret_cast<float4*>(sm + L.al);
     float4* seg_s = reinterpret_cast<float4*>(sm + L.seg);
     float* il2_s = reinterpret_cast<float*>(sm + L.il2);
     float* obs_s = reinterpret_cast<float*>(sm + L.obs);
@@ -232,14 +273,24 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_cl(const RolloutArgs a, 
         *abort_flag = 0;
         tc::fence_mbar_init();
     }
+    // training inputs and alpha in pair layout: for points 2p and 2p + 1,
+    // xs_s[2p] = (x0, x0', x1, x1'), xs_s[2p + 1] = (x2, x2', x3, x3') and
+    // al_s[p] = (a_v, a_v', a_w, a_w'), primes marking point 2p + 1
     for (int j = tid; j < cl.npc; j += THREADS) {
+        float4 x = make_float4(1.0e4f, 1.0e4f, 1.0e4f, 1.0e4f);
+        float2 al = make_float2(0.0f, 0.0f);
         if (j < a.N) {
-            xs_s[j] = __ldg(reinterpret_cast<const float4*>(a.Xs) + j);
-            al_s[j] = __ldg(reinterpret_cast<const float2*>(a.alpha) + j);
-        } else {
-            xs_s[j] = make_float4(1.0e4f, 1.0e4f, 1.0e4f, 1.0e4f);
-            al_s[j] = make_float2(0.0f, 0.0f);
+            x = __ldg(reinterpret_cast<const float4*>(a.Xs) + j);
+            al = __ldg(reinterpret_cast<const float2*>(a.alpha) + j);
         }
+        float* xp = reinterpret_cast<float*>(xs_s + 2 * (j >> 1)) + (j & 1);
+        xp[0] = x.x;
+        xp[2] = x.y;
+        xp[4] = x.z;
+        xp[6] = x.w;
+        float* ap = reinterpret_cast<float*>(al_s + (j >> 1)) + (j & 1);
+        ap[0] = al.x;
+        ap[2] = al.y;
     }
     const int Ssm = cl.scene_smem ? a.S : 0, Osm = cl.scene_smem ? a.O : 0;
     for (int i = tid; i < Ssm; i += THREADS) {
@@ -368,29 +419,44 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_cl(const RolloutArgs a, 
             // part of them beyond its own tiles (the highest rank) computed
             // for the mean alone.
             float mv = 0.0f, mw = 0.0f, cv = 0.0f, cw = 0.0f;
-            auto kernel_row = [&](int c, float (&av)[8]) {
-                const int jb = c * 16 + u * 8;
+            const uint64_t zz0 = f2pack(z0, z0), zz1 = f2pack(z1, z1);
+            const uint64_t zz2 = f2pack(z2, z2), zz3 = f2pack(z3, z3);
+            // kernel-row entries of the thread's 8 points of chunk c, as 4 packed
+            // pairs: av[q] = (2^-d(z, x_2p), 2^-d(z, x_2p+1)) for pair p = pb + q
+            auto kernel_row = [&](int c, uint64_t (&av)[4]) {
+                const int pb = c * 8 + u * 4;
 #pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    const float4 x = xs_s[jb + q];
-                    const float d0 = z0 - x.x, d1 = z1 - x.y, d2 = z2 - x.z, d3 = z3 - x.w;
-                    av[q] = exp2f(-(d0 * d0 + d1 * d1 + d2 * d2 + d3 * d3));
+                for (int q = 0; q < 4; ++q) {
+                    const ulonglong2 xa = *reinterpret_cast<const ulonglong2*>(xs_s + 2 * (pb + q));
+                    const ulonglong2 xb = *reinterpret_cast<const ulonglong2*>(xs_s + 2 * (pb + q) + 1);
+                    const uint64_t d0 = f2sub(zz0, xa.x), d1 = f2sub(zz1, xa.y);
+                    const uint64_t d2 = f2sub(zz2, xb.x), d3 = f2sub(zz3, xb.y);
+                    uint64_t t = f2mul(d0, d0);
+                    t = f2fma(d1, d1, t);
+                    t = f2fma(d2, d2, t);
+                    t = f2fma(d3, d3, t);
+                    float t0, t1;
+                    f2unpack(t, t0, t1);
+                    av[q] = f2pack(ex2_ftz(-t0), ex2_ftz(-t1));
                 }
             };
-            auto mean_part = [&](int c, const float (&av)[8]) {
-                const int jb = c * 16 + u * 8;
-                float pv = 0.0f, pw = 0.0f;
+            auto mean_part = [&](int c, const uint64_t (&av)[4]) {
+                const int pb = c * 8 + u * 4;
+                uint64_t pv = 0ull, pw = 0ull;     // (even, odd) partial sums
 #pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    const float2 al = al_s[jb + q];
-                    pv = fmaf(av[q], al.x, pv);
-                    pw = fmaf(av[q], al.y, pw);
+                for (int q = 0; q < 4; ++q) {
+                    const ulonglong2 al = *reinterpret_cast<const ulonglong2*>(al_s + pb + q);
+                    pv = f2fma(av[q], al.x, pv);
+                    pw = f2fma(av[q], al.y, pw);
                 }
-                kahan_add(mv, cv, pv);
-                kahan_add(mw, cw, pw);
+                float pv0, pv1, pw0, pw1;
+                f2unpack(pv, pv0, pv1);
+                f2unpack(pw, pw0, pw1);
+                kahan_add(mv, cv, pv0 + pv1);
+                kahan_add(mw, cw, pw0 + pw1);
             };
             for (int c = 0; c < nch; c += BURST) {      // nch is a multiple of 4 (and of BURST)
-                float av[BURST][8];
+                uint64_t av[BURST][4];
 #pragma unroll
                 for (int h = 0; h < BURST; ++h) kernel_row(c + h, av[h]);
 #pragma unroll
@@ -400,7 +466,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_cl(const RolloutArgs a, 
 #pragma unroll
                 for (int h = 0; h < BURST; ++h)
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) split2<FMT>(av[h][2 * q], av[h][2 * q + 1], &hw[h][q], &lw[h][q]);
+                    for (int q = 0; q < 4; ++q) split2<FMT>(av[h][q], &hw[h][q], &lw[h][q]);
 #pragma unroll
                 for (int h = 0; h < BURST; ++h) {
                     const int slot = (c + h) % GCH;        // chunk's place in its stage
@@ -421,7 +487,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_cl(const RolloutArgs a, 
                 }
             }
             for (int c = (mc0 > nch ? mc0 : nch); c < mc1; ++c) {
-                float av[8];
+                uint64_t av[4];
                 kernel_row(c, av);
                 mean_part(c, av);
             }
