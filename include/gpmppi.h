@@ -341,7 +341,8 @@ int gpmppi_control_noise(uint64_t seed, int32_t K, int32_t T, uint64_t it, const
  *   N        64, 128 or 256 (rows of B, columns of D); K 16, 32, 48 or 64
  *   variant  0 = the library's descriptor convention; 1 = leading and stride
  *            byte offsets exchanged (N <= 128), to show which one the
- *            hardware expects
+ *            hardware expects; 2 = A written to tensor memory (one row per
+ *            lane, tcgen05.st) and read from there by the MMA
  *   A device 128 x K, B device N x K (16-bit, row-major), D device 128 x N floats
  * Blocking; GPMPPI_ERR_TIMEOUT if the MMA completion did not arrive. */
 int gpmppi_mma_selftest(int32_t fmt, int32_t N, int32_t K, int32_t variant, const uint16_t* A,

@@ -904,7 +904,7 @@ int gpmppi_mma_selftest(int32_t fmt, int32_t N, int32_t K, int32_t variant, cons
     if (fmt != 0 && fmt != 1) return fail(GPMPPI_ERR_INVALID_ARG, "gpmppi_mma_selftest: fmt must be 0 or 1");
     if (N != 64 && N != 128 && N != 256) return fail(GPMPPI_ERR_INVALID_ARG, "gpmppi_mma_selftest: N must be 64, 128 or 256");
     if (K != 16 && K != 32 && K != 48 && K != 64) return fail(GPMPPI_ERR_INVALID_ARG, "gpmppi_mma_selftest: K must be 16, 32, 48 or 64");
-    if (variant != 0 && variant != 1) return fail(GPMPPI_ERR_INVALID_ARG, "gpmppi_mma_selftest: variant must be 0 or 1");
+    if (variant < 0 || variant > 2) return fail(GPMPPI_ERR_INVALID_ARG, "gpmppi_mma_selftest: variant must be 0, 1 or 2");
     if (variant == 1 && N > 128) return fail(GPMPPI_ERR_INVALID_ARG, "gpmppi_mma_selftest: variant 1 needs N <= 128");
     int rc;
     if ((rc = check_dev_ptr(A, "gpmppi_mma_selftest: A", false))) return rc;

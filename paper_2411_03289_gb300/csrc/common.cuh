@@ -122,7 +122,10 @@ struct GpDevice {
     int NpM = 0;
     // resident tiles of the cluster rollout (N <= 512): per 16-bit format, rank
     // r's pieces at element offset cl_base[r], cl_bytes[r] bytes; NpC = 128,
-    // 256 or 512 output columns
+    // 256 or 512 output columns.  A piece holds one 16-point chunk of the
+    // rank's output rows, hi and lo parts as one slab-major operand: rows
+    // [hi lower | hi upper | lo upper | lo lower] slice (256) while both
+    // slices need the chunk, [hi upper | lo upper] (128) after
     uint16_t* cl_tiles[2] = {nullptr, nullptr};
     int cl_base[4] = {0, 0, 0, 0};
     int cl_bytes[4] = {0, 0, 0, 0};

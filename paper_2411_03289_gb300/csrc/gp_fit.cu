@@ -317,30 +317,38 @@ __global__ void k_pack_cl(const double* __restrict__ Xm, int N, int NS, int fmt,
                           const int4* __restrict__ pieces, int npieces, uint16_t* __restrict__ out) {
     const int p = blockIdx.y;
     if (p >= npieces) return;
-    const int4 d = pieces[p];            // (element offset, chunk, rank, rows)
-    const int rows = d.w;
-    const int n = rows * 16;             // elements per part
+    const int4 d = pieces[p];            // (element offset, chunk, rank, rows per part)
+    const int rows = d.w, R2 = 2 * rows; // the piece holds the hi and the lo rows
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= n) return;
-    const int sl = idx / (rows * 8), rr = (idx / 8) % rows, e = idx % 8;
+    if (idx >= R2 * 16) return;
+    const int sl = idx / (R2 * 8), rr = (idx / 8) % R2, e = idx % 8;
     const int c = d.y, r = d.z;
     const int j = 16 * c + 8 * sl + e;
-    const int i = (rows == 128 && rr < 64) ? 64 * r + rr
-                                           : 64 * (NS - 1 - r) + (rows == 128 ? rr - 64 : rr);
+    const int lo_row = 64 * r, up_row = 64 * (NS - 1 - r);
+    // row order: [hi lower | hi upper | lo upper | lo lower] while both slices
+    // need the chunk (rows = 128), [hi upper | lo upper] after (rows = 64)
+    int i;
+    bool lo;
+    if (rows == 128) {
+        const int q = rr >> 6, o = rr & 63;
+        i = (q == 0 || q == 3) ? lo_row + o : up_row + o;
+        lo = q >= 2;
+    } else {
+        i = up_row + (rr & 63);
+        lo = rr >= 64;
+    }
     double v = 0.0;
     if (i < N && j < N && j <= i) v = cB * Xm[(size_t)i * N + j];
-    uint16_t h, l;
+    uint16_t h;
     if (fmt == 0) {
         const __half hh = __double2half(v);
-        h = __half_as_ushort(hh);
-        l = __half_as_ushort(__double2half(v - (double)__half2float(hh)));
+        h = lo ? __half_as_ushort(__double2half(v - (double)__half2float(hh))) : __half_as_ushort(hh);
     } else {
         const __nv_bfloat16 hh = __double2bfloat16(v);
-        h = __bfloat16_as_ushort(hh);
-        l = __bfloat16_as_ushort(__double2bfloat16(v - (double)__bfloat162float(hh)));
+        h = lo ? __bfloat16_as_ushort(__double2bfloat16(v - (double)__bfloat162float(hh)))
+               : __bfloat16_as_ushort(hh);
     }
     out[(size_t)d.x + idx] = h;
-    out[(size_t)d.x + n + idx] = l;
 }
 
 }  // namespace
@@ -369,7 +377,7 @@ int build_cl_tiles(GpDevice& g, int fmt) {
     cudaError_t e = cudaMemcpy(dp, pieces.data(), pieces.size() * sizeof(int4), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMalloc(&g.cl_tiles[fmt], off * sizeof(uint16_t));
     if (e == cudaSuccess) {
-        k_pack_cl<<<dim3(8, (unsigned)pieces.size()), 256>>>(g.Linv64[0], g.N, NS, fmt, (double)g.mma_cB, dp,
+        k_pack_cl<<<dim3(16, (unsigned)pieces.size()), 256>>>(g.Linv64[0], g.N, NS, fmt, (double)g.mma_cB, dp,
                                                            (int)pieces.size(), g.cl_tiles[fmt]);
         e = cudaGetLastError();
     }

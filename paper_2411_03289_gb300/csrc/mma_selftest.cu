@@ -4,6 +4,8 @@
 // descriptors, TMEM allocation, tcgen05.commit on an mbarrier and tcgen05.ld,
 // and writes D = A B^T (128 x N, FP32).  The rollout's variance contraction
 // uses exactly these pieces, so this call lets a test pin them in isolation.
+// Variant 2 writes A into tensor memory instead (tcgen05.st, one row per
+// lane) and issues the products with A read from there.
 #include "common.cuh"
 #include "tc05.cuh"
 
@@ -39,25 +41,40 @@ __global__ void __launch_bounds__(ST_THREADS, 1)
         tc::mbar_init(bar, 1);
         tc::fence_mbar_init();
     }
-    if (warp == 0) tc::tmem_alloc(tslot, 256);
+    if (warp == 0) tc::tmem_alloc(tslot, 512);
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t taddr = *tslot;
+    constexpr uint32_t ACOL = 256;      // A in TMEM (variant 2): columns 256 .. 256 + K/2
+    if (variant == 2) {
+        // thread tid = row r of A (lane r); K/2 packed columns in steps of 4
+        const uint32_t lane_addr = taddr + ((uint32_t)(32 * warp) << 16) + ACOL;
+        const uint32_t* row = reinterpret_cast<const uint32_t*>(A + (size_t)tid * K);
+        for (int c = 0; c < K / 2; c += 4)
+            tc::tmem_st4(lane_addr + (uint32_t)c, row[c], row[c + 1], row[c + 2], row[c + 3]);
+        tc::tmem_wait_st();
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+    }
     if (tid == 0) {
         const uint32_t idesc = tc::idesc_f16(fmt, 128, N);
         for (int ks = 0; ks < K / 16; ++ks) {
             const uint32_t a0 = tc::smem_addr(sA) + ks * 2 * 128 * 16;
             const uint32_t b0 = tc::smem_addr(sB) + ks * 2 * N * 16;
             uint64_t ad, bd;
-            if (variant == 0) {
+            if (variant == 0 || variant == 2) {
                 ad = tc::smem_desc(a0, 128 * 16, 128);
                 bd = tc::smem_desc(b0, N * 16, 128);
             } else {
                 ad = tc::smem_desc(a0, 128, 128 * 16);
                 bd = tc::smem_desc(b0, 128, N * 16);
             }
-            tc::mma_f16(taddr, ad, bd, idesc, ks > 0 ? 1u : 0u);
+            if (variant == 2)
+                tc::mma_f16_ta(taddr, taddr + ACOL + 8u * ks, bd, idesc, ks > 0 ? 1u : 0u);
+            else
+                tc::mma_f16(taddr, ad, bd, idesc, ks > 0 ? 1u : 0u);
         }
         tc::mma_commit(bar);
     }
@@ -71,7 +88,7 @@ __global__ void __launch_bounds__(ST_THREADS, 1)
     }
     tc::fence_before_sync();
     __syncthreads();
-    if (warp == 0) tc::tmem_dealloc(taddr, 256);
+    if (warp == 0) tc::tmem_dealloc(taddr, 512);
 }
 
 }  // namespace

@@ -7,17 +7,19 @@
 // operands, |V_m|^2 = |L^-1 k*_m|^2).  What changes is where the operands
 // live.  The output columns of V are cut into 64-column slices and rank r of
 // the cluster owns slices r and NS - 1 - r (equal triangular work for every
-// rank).  Their pieces of cB L^-1 (hi and lo, at most 144 KiB) are copied into
-// shared memory once, before the first step, so a step moves no factor
-// tiles at all: the MMAs read resident B and the kernel-row tiles A that the
-// producer warps write into a two-stage ring.  This matters because a
-// 128 x 128 x 16 MMA reads 8 KiB of operands from shared memory, which is
-// the whole shared-memory bandwidth at the tensor rate; streaming the factor
-// through the same shared memory every step halved the MMA rate.
+// rank).  Their pieces of cB L^-1 (the hi and lo rows of a chunk side by
+// side, at most 144 KiB) are copied into shared memory once, before the first
+// step, so a step moves no factor tiles at all.  The MMAs read that resident
+// B from shared memory and the kernel-row tiles A from tensor memory, where
+// the producer warps write them (tcgen05.st, one sample per TMEM lane) into a
+// four-stage ring.  Shared memory thus carries only B to the tensor core: a
+// 128 x 128 x 16 MMA with both operands there reads 8 KiB per 64 clocks, the
+// whole shared-memory bandwidth, and streaming the factor through it every
+// step halved the MMA rate.
 //
 // Per step: every rank computes the noise, queries and kernel rows of all 128
-// samples (rank 0 also the GP mean), issues the MMAs of its slices, reads its
-// partial |V_m|^2 from TMEM and exchanges the partials (and rank 0's means)
+// samples (and its share of the GP mean), issues the MMAs of its slices, reads
+// its partial |V_m|^2 from TMEM and exchanges the partials and mean shares
 // through distributed shared memory, guarded by mbarriers that each peer
 // arrives on remotely.  All ranks then advance the same 128 states
 // identically (same inputs, same order of summation); the cost phase (lane
@@ -37,17 +39,23 @@ namespace {
 constexpr int MT = 128;               // samples per cluster (the MMA M)
 constexpr int NPROD = 256;            // producer threads: two per sample
 constexpr int THREADS = NPROD + 32;   // + the MMA-issuing warp
-constexpr int NSTAGE = 2;             // kernel-row tile ring
+constexpr int NSTAGE = 4;             // kernel-row tile ring (in tensor memory)
 constexpr int GCH = 2;                // chunks per stage: one hand-off per two chunks
 constexpr int BURST = 2;              // chunks whose kernel rows a thread computes together
-constexpr int A_PART = MT * 16 * 2;   // 4 KiB: one 16-bit part of a 128 x 16 tile
-constexpr int A_CHUNK = 2 * A_PART;   // hi + lo of one chunk
-constexpr int A_STAGE = GCH * A_CHUNK;
+// TMEM columns: the accumulators D in columns [0, 256) (hi.hi + lo.hi of the
+// lower and upper slice in 0-63 and 64-127, hi.lo of the upper slice in
+// 128-191, of the lower in 192-255), the A ring after them; a chunk's A tile
+// takes 16 columns (hi in 8, lo in 8: 16 elements of 16 bits per lane and part)
+constexpr uint32_t TM_COLS = 512;
+constexpr uint32_t A_COL = 256;
+constexpr uint32_t A_CHUNK_COLS = 16;
+constexpr uint32_t A_STAGE_COLS = GCH * A_CHUNK_COLS;
+static_assert(A_COL + NSTAGE * A_STAGE_COLS <= TM_COLS, "A ring exceeds the TMEM allocation");
 constexpr int B_MAX = 144 * 1024;     // largest resident share (NS = 8)
 constexpr uint64_t kWaitNs = 2000000000ull;
 
 struct ClLayout {
-    int b, a, bars, tslot, abort_flag, xq, xm, qloc, mloc, sst, ep, om, xs, al, seg, il2, obs, total;
+    int b, bars, tslot, abort_flag, xq, xm, qloc, mloc, sst, ep, om, xs, al, seg, il2, obs, total;
 };
 
 // shared-memory layout; the resident B share is sized for the largest rank;
@@ -57,8 +65,7 @@ __host__ __device__ inline ClLayout cl_layout(int npc, int S, int O) {
     const int nown = MT / (npc / 128);
     ClLayout L;
     L.b = 0;
-    L.a = B_MAX;
-    L.bars = L.a + NSTAGE * A_STAGE;             // a_full, empty [NSTAGE], b_res, pass_done, tmem_free, xbar[2]
+    L.bars = B_MAX;                              // a_full, empty [NSTAGE], b_res, pass_done, tmem_free, xbar[2]
     L.tslot = L.bars + 8 * (2 * NSTAGE + 5);
     L.abort_flag = L.tslot + 4;
     L.xq = ((L.abort_flag + 4 + 15) / 16) * 16;  // [2][4][MT] floats: partial |V|^2 per rank
@@ -301,7 +308,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_cl(const RolloutArgs a, 
     const float4* segp = cl.scene_smem ? seg_s : a.seg;
     const float* il2p = cl.scene_smem ? il2_s : a.seg_il2;
     const float* obsp = cl.scene_smem ? obs_s : a.obst;
-    if (warp == 0) tc::tmem_alloc(tslot, 128);
+    if (warp == 0) tc::tmem_alloc(tslot, TM_COLS);
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
@@ -315,75 +322,78 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_cl(const RolloutArgs a, 
     const uint32_t taddr = *tslot;
 
     if (warp == NPROD / 32) {
-        // ======================= MMA issuer (one thread) =====================
-        if (lane == 0) {
-            const uint32_t idesc128 = tc::idesc_f16(FMT, MT, 128);
-            const uint32_t idesc64 = tc::idesc_f16(FMT, MT, 64);
-            // base descriptors: A stages (K-major, 128 rows) and the resident B
-            // pieces (128 or 64 rows); all offsets below are multiples of 16 bytes
-            // and stay inside shared memory, so they add to the start-address field
-            const uint64_t dA0 = tc::smem_desc(tc::smem_addr(sm + L.a), MT * 16, 128);
-            const uint64_t dB128 = tc::smem_desc(tc::smem_addr(bres), 128 * 16, 128);
-            const uint64_t dB64 = tc::smem_desc(tc::smem_addr(bres), 64 * 16, 128);
-            bool ok = wait_or_abort(b_res, 0, abort_flag, a.err);
-            tc::fence_after_sync();
-            uint32_t n = 0;
-            for (int k = 0; k < a.T && ok; ++k) {
-                if (k > 0) {
-                    if (!wait_or_abort(tmem_free, (uint32_t)(k - 1) & 1u, abort_flag, a.err)) break;
-                    tc::fence_after_sync();
+        // ================= MMA issuer (one warp, one elected lane) ==============
+        // The whole warp runs the loop (its operand arithmetic stays
+        // warp-uniform); elect.sync picks the lane that issues each instruction.
+        // Per chunk two MMAs: A_hi x [B_hi | B_lo] (N doubled: the hi.hi and
+        // hi.lo products land in separate TMEM columns) and A_lo x B_hi
+        // (accumulated onto hi.hi); the pass-end read adds the two column sets.
+        const uint32_t idesc256 = tc::idesc_f16(FMT, MT, 256);
+        const uint32_t idesc128 = tc::idesc_f16(FMT, MT, 128);
+        const uint32_t idesc64 = tc::idesc_f16(FMT, MT, 64);
+        // base descriptors of the resident B pieces (256 rows while both slices
+        // need a chunk, 128 rows after); all offsets below are multiples of 16
+        // bytes inside shared memory, so they add to the start-address field
+        const uint64_t dB256 = tc::smem_desc(tc::smem_addr(bres), 256 * 16, 128);
+        const uint64_t dB128 = tc::smem_desc(tc::smem_addr(bres), 128 * 16, 128);
+        bool ok = __all_sync(0xffffffffu, wait_or_abort(b_res, 0, abort_flag, a.err));
+        tc::fence_after_sync();
+        uint32_t n = 0;
+        for (int k = 0; k < a.T && ok; ++k) {
+            if (k > 0) {
+                if (!__all_sync(0xffffffffu, wait_or_abort(tmem_free, (uint32_t)(k - 1) & 1u, abort_flag, a.err))) {
+                    ok = false;
+                    break;
                 }
-                for (int c = 0; c < nch; c += GCH, ++n) {
-                    const int st = (int)(n % NSTAGE);
-                    const uint32_t use = n / NSTAGE;
-                    if (!wait_or_abort(a_full + st, use & 1u, abort_flag, a.err)) {
-                        ok = false;
-                        break;
-                    }
-                    tc::fence_after_sync();
+                tc::fence_after_sync();
+            }
+            for (int c = 0; c < nch; c += GCH, ++n) {
+                const int st = (int)(n % NSTAGE);
+                const uint32_t use = n / NSTAGE;
+                if (!__all_sync(0xffffffffu, wait_or_abort(a_full + st, use & 1u, abort_flag, a.err))) {
+                    ok = false;
+                    break;
+                }
+                tc::fence_after_sync();
+                const uint32_t aS = taddr + A_COL + (uint32_t)st * A_STAGE_COLS;
 #pragma unroll
-                    for (int h = 0; h < GCH; ++h) {
-                        const int cc = c + h;
-                        // descriptors by adds on precomputed bases (no per-MMA rebuild:
-                        // the single issuing thread is otherwise the bottleneck)
-                        const uint64_t dAh = dA0 + (uint64_t)((st * A_STAGE + h * A_CHUNK) >> 4);
-                        const uint64_t dAl = dAh + (uint64_t)(A_PART >> 4);
-                        if (cc < nboth) {
-                            // both slices: one 128-row piece, D columns 0 .. 127
-                            const uint64_t dBh = dB128 + (uint64_t)((cc * 8192) >> 4);
-                            const uint64_t dBl = dBh + (uint64_t)(4096 >> 4);
-                            tc::mma_f16(taddr, dAh, dBh, idesc128, cc > 0 ? 1u : 0u);
-                            tc::mma_f16(taddr, dAh, dBl, idesc128, 1u);
-                            tc::mma_f16(taddr, dAl, dBh, idesc128, 1u);
-                        } else {
-                            // the upper slice alone: a 64-row piece, D columns 64 .. 127
-                            const uint64_t dBh = dB64 + (uint64_t)((nboth * 8192 + (cc - nboth) * 4096) >> 4);
-                            const uint64_t dBl = dBh + (uint64_t)(2048 >> 4);
-                            tc::mma_f16(taddr + 64u, dAh, dBh, idesc64, 1u);
-                            tc::mma_f16(taddr + 64u, dAh, dBl, idesc64, 1u);
-                            tc::mma_f16(taddr + 64u, dAl, dBh, idesc64, 1u);
-                        }
+                for (int h = 0; h < GCH; ++h) {
+                    const int cc = c + h;
+                    const uint32_t aH = aS + (uint32_t)h * A_CHUNK_COLS, aL = aH + 8u;
+                    if (cc < nboth) {
+                        // rows [hi lower | hi upper | lo upper | lo lower]: D columns
+                        // 0-127 hi.hi (+ lo.hi), 128-191 hi.lo upper, 192-255 hi.lo lower
+                        const uint64_t dB = dB256 + (uint64_t)((cc * 8192) >> 4);
+                        tc::mma_f16_ta_elect(taddr, aH, dB, idesc256, cc > 0 ? 1u : 0u);
+                        tc::mma_f16_ta_elect(taddr, aL, dB, idesc128, 1u);
+                    } else {
+                        // rows [hi upper | lo upper]: D columns 64-127 and 128-191
+                        const uint64_t dB = dB128 + (uint64_t)((nboth * 8192 + (cc - nboth) * 4096) >> 4);
+                        tc::mma_f16_ta_elect(taddr + 64u, aH, dB, idesc128, 1u);
+                        tc::mma_f16_ta_elect(taddr + 64u, aL, dB, idesc64, 1u);
                     }
-                    // the commit releases the stage once its MMAs completed
-                    tc::mma_commit(empty + st);
                 }
-                if (!ok) break;
-                tc::mma_commit(pass_done);
+                // the commit releases the stage once its MMAs completed
+                tc::mma_commit_elect(empty + st);
             }
-            // let MMAs in flight land before the shared memory can be released
-            if (!ok) {
-                const uint64_t t0 = tc::global_ns();
-                for (uint32_t i = (n >= (uint32_t)NSTAGE ? n - (uint32_t)NSTAGE : 0); i < n; ++i)
-                    while (!tc::mbar_try_wait(empty + (i % NSTAGE), (i / NSTAGE) & 1u) &&
-                           tc::global_ns() - t0 < 200000000ull) {
-                    }
-            }
+            if (!ok) break;
+            tc::mma_commit_elect(pass_done);
+        }
+        // let MMAs in flight land before the shared memory can be released
+        if (!ok) {
+            const uint64_t t0 = tc::global_ns();
+            for (uint32_t i = (n >= (uint32_t)NSTAGE ? n - (uint32_t)NSTAGE : 0); i < n; ++i)
+                while (!tc::mbar_try_wait(empty + (i % NSTAGE), (i / NSTAGE) & 1u) &&
+                       tc::global_ns() - t0 < 200000000ull) {
+                }
         }
         __syncwarp();
     } else {
         // ========================== producer warps =============================
-        const int m = tid & (MT - 1);          // sample within the cluster
+        const int m = tid & (MT - 1);          // sample within the cluster (= its TMEM lane)
         const int u = tid >> 7;                // which of its two threads (half of each chunk)
+        // this warp's TMEM lanes 32 (warp % 4) .., at the A ring's first column
+        const uint32_t a_lane = taddr + ((uint32_t)(32 * (warp & 3)) << 16) + A_COL;
         const int s_me = tile * MT + m;
         const bool active = s_me < a.K;
         const int s_q = active ? s_me : 0;
@@ -472,14 +482,20 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_cl(const RolloutArgs a, 
                     const int slot = (c + h) % GCH;        // chunk's place in its stage
                     const int st = (int)(n % NSTAGE);
                     const uint32_t use = n / NSTAGE;
-                    if (slot == 0 && n >= (uint32_t)NSTAGE)
+                    if (slot == 0 && n >= (uint32_t)NSTAGE) {
+                        // the MMAs that read this stage's columns have completed
                         wait_or_abort(empty + st, (use - 1) & 1u, abort_flag, a.err);
-                    // slab u (points 8u .. 8u + 7) of row m of chunk c + h
-                    unsigned char* ph = sm + L.a + st * A_STAGE + slot * A_CHUNK + u * (MT * 16) + m * 16;
-                    *reinterpret_cast<uint4*>(ph) = make_uint4(hw[h][0], hw[h][1], hw[h][2], hw[h][3]);
-                    *reinterpret_cast<uint4*>(ph + A_PART) = make_uint4(lw[h][0], lw[h][1], lw[h][2], lw[h][3]);
+                        __syncwarp();                      // tcgen05.st is warp-collective
+                        tc::fence_after_sync();
+                    }
+                    // points 8u .. 8u + 7 of sample m (TMEM lane m) of chunk c + h: four
+                    // packed columns of the hi part, four of the lo part
+                    const uint32_t col = a_lane + (uint32_t)st * A_STAGE_COLS + (uint32_t)slot * A_CHUNK_COLS + 4u * u;
+                    tc::tmem_st4(col, hw[h][0], hw[h][1], hw[h][2], hw[h][3]);
+                    tc::tmem_st4(col + 8u, lw[h][0], lw[h][1], lw[h][2], lw[h][3]);
                     if (slot == GCH - 1) {
-                        tc::fence_proxy_async();
+                        tc::tmem_wait_st();
+                        tc::fence_before_sync();
                         __syncwarp();
                         if (lane == 0) mbar_arrive(a_full + st);
                         ++n;
@@ -497,19 +513,24 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_cl(const RolloutArgs a, 
             tc::fence_after_sync();
             float qpart = 0.0f;
             if (ok) {
-                // warp w reads TMEM lanes 32 (w % 4) ..; thread half u its 64 columns
-                const uint32_t row = taddr + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(64 * u);
+                // warp w reads TMEM lanes 32 (w % 4) ..; thread half u the 64
+                // columns of its slice: V = (hi.hi + lo.hi) + hi.lo
+                const uint32_t row = taddr + ((uint32_t)(32 * (warp & 3)) << 16);
+                const uint32_t c0 = (uint32_t)(64 * u), c1 = u ? 128u : 192u;
 #pragma unroll
                 for (int cc = 0; cc < 64; cc += 32) {
-                    float v[32];
-                    tc::tmem_ld32(row + (uint32_t)cc, v);
+                    float v[32], w[32];
+                    tc::tmem_ld32(row + c0 + (uint32_t)cc, v);
+                    tc::tmem_ld32(row + c1 + (uint32_t)cc, w);
                     float p0 = 0.0f, p1 = 0.0f, p2 = 0.0f, p3 = 0.0f;
 #pragma unroll
                     for (int i = 0; i < 8; ++i) {
-                        p0 = fmaf(v[i], v[i], p0);
-                        p1 = fmaf(v[8 + i], v[8 + i], p1);
-                        p2 = fmaf(v[16 + i], v[16 + i], p2);
-                        p3 = fmaf(v[24 + i], v[24 + i], p3);
+                        const float x0 = v[i] + w[i], x1 = v[8 + i] + w[8 + i];
+                        const float x2 = v[16 + i] + w[16 + i], x3 = v[24 + i] + w[24 + i];
+                        p0 = fmaf(x0, x0, p0);
+                        p1 = fmaf(x1, x1, p1);
+                        p2 = fmaf(x2, x2, p2);
+                        p3 = fmaf(x3, x3, p3);
                     }
                     qpart += (p0 + p1) + (p2 + p3);
                 }
@@ -679,7 +700,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_cl(const RolloutArgs a, 
     tc::fence_before_sync();
     __syncthreads();
     cluster_sync_all();
-    if (warp == 0) tc::tmem_dealloc(taddr, 128);
+    if (warp == 0) tc::tmem_dealloc(taddr, TM_COLS);
 }
 
 }  // namespace

@@ -25,12 +25,16 @@ def _operands(fmt, rows, K, seed):
 
 @pytest.mark.parametrize("fmt", [0, 1])
 @pytest.mark.parametrize("N,K", [(64, 16), (128, 32), (256, 64), (64, 48)])
-def test_mma_selftest(lib, fmt, N, K):
+@pytest.mark.parametrize("variant", [0, 2])
+def test_mma_selftest(lib, fmt, N, K, variant):
+    """D = A B^T on the tensor cores, A from shared memory (variant 0) or from
+    tensor memory (variant 2, the cluster rollout's kernel-row operand)."""
     import torch
     A16, A = _operands(fmt, 128, K, 1)
     B16, B = _operands(fmt, N, K, 2)
     D = torch.empty(128, N, device="cuda")
-    lib.gpmppi_mma_selftest(fmt, A16.cuda().view(torch.int16), B16.cuda().view(torch.int16), D)
+    lib.gpmppi_mma_selftest(fmt, A16.cuda().view(torch.int16), B16.cuda().view(torch.int16), D,
+                            variant=variant)
     ref = (A @ B.T).numpy()
     got = D.cpu().double().numpy()
     assert np.max(np.abs(got - ref)) <= 1e-5 * (1 + np.max(np.abs(ref)))
