@@ -40,8 +40,9 @@ constexpr int MT = 128;               // samples per cluster (the MMA M)
 constexpr int NPROD = 256;            // producer threads: two per sample
 constexpr int THREADS = NPROD + 32;   // + the MMA-issuing warp
 constexpr int NSTAGE = 4;             // kernel-row tile ring (in tensor memory)
-constexpr int GCH = 2;                // chunks per stage: one hand-off per two chunks
-constexpr int BURST = 2;              // chunks whose kernel rows a thread computes together
+constexpr int GCH = 4;                // chunks per stage: one hand-off per four chunks
+static_assert(GCH == 4, "the issue loop issues a stage as four chunks");
+constexpr int BURST = 4;              // chunks whose kernel rows a thread computes together
 // TMEM columns: the accumulators D in columns [0, 256) (hi.hi + lo.hi of the
 // lower and upper slice in 0-63 and 64-127, hi.lo of the upper slice in
 // 128-191, of the lower in 192-255), the A ring after them; a chunk's A tile
@@ -356,25 +357,18 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_cl(const RolloutArgs a, 
                 }
                 tc::fence_after_sync();
                 const uint32_t aS = taddr + A_COL + (uint32_t)st * A_STAGE_COLS;
-#pragma unroll
-                for (int h = 0; h < GCH; ++h) {
-                    const int cc = c + h;
-                    const uint32_t aH = aS + (uint32_t)h * A_CHUNK_COLS, aL = aH + 8u;
-                    if (cc < nboth) {
-                        // rows [hi lower | hi upper | lo upper | lo lower]: D columns
-                        // 0-127 hi.hi (+ lo.hi), 128-191 hi.lo upper, 192-255 hi.lo lower
-                        const uint64_t dB = dB256 + (uint64_t)((cc * 8192) >> 4);
-                        tc::mma_f16_ta_elect(taddr, aH, dB, idesc256, cc > 0 ? 1u : 0u);
-                        tc::mma_f16_ta_elect(taddr, aL, dB, idesc128, 1u);
-                    } else {
-                        // rows [hi upper | lo upper]: D columns 64-127 and 128-191
-                        const uint64_t dB = dB128 + (uint64_t)((nboth * 8192 + (cc - nboth) * 4096) >> 4);
-                        tc::mma_f16_ta_elect(taddr + 64u, aH, dB, idesc128, 1u);
-                        tc::mma_f16_ta_elect(taddr + 64u, aL, dB, idesc64, 1u);
-                    }
+                // a stage's four chunks are all below nboth or all above (nboth is a
+                // multiple of 4)
+                if (c < nboth) {
+                    // rows [hi lower | hi upper | lo upper | lo lower]: D columns
+                    // 0-127 hi.hi (+ lo.hi), 128-191 hi.lo upper, 192-255 hi.lo lower
+                    const uint64_t b0 = dB256 + (uint64_t)((c * 8192) >> 4);
+                    tc::mma_stage4_elect(taddr, aS, b0, 8192 >> 4, empty + st, c > 0 ? 1u : 0u, idesc256, idesc128);
+                } else {
+                    // rows [hi upper | lo upper]: D columns 64-127 and 128-191
+                    const uint64_t b0 = dB128 + (uint64_t)((nboth * 8192 + (c - nboth) * 4096) >> 4);
+                    tc::mma_stage4_elect(taddr + 64u, aS, b0, 4096 >> 4, empty + st, 1u, idesc128, idesc64);
                 }
-                // the commit releases the stage once its MMAs completed
-                tc::mma_commit_elect(empty + st);
             }
             if (!ok) break;
             tc::mma_commit_elect(pass_done);
@@ -424,7 +418,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_cl(const RolloutArgs a, 
             const float z2 = ut.x * a.zscale[2], z3 = ut.y * a.zscale[3];
 
             // ---------------- kernel-row tiles (8 points per thread per chunk) ----
-            // BURST chunks per burst (16 independent exp2 in flight).  The GP mean
+            // BURST chunks per burst (32 independent exp2 in flight).  The GP mean
             // is split between the ranks: rank r sums chunks [mc0, mc1), the
             // part of them beyond its own tiles (the highest rank) computed
             // for the mean alone.

@@ -66,27 +66,48 @@ __device__ __forceinline__ void mma_f16_ta(uint32_t d_tmem, uint32_t a_tmem, uin
         : "memory");
 }
 
-// Warp-collective forms of the two calls above and of the commit below: the
-// whole (converged) warp executes them and one lane, chosen by elect.sync,
-// issues the instruction.  Running the issue loop on a converged warp lets the
-// operand arithmetic stay warp-uniform, which keeps the single issue slot from
-// becoming the bottleneck of a chain of small MMAs.
-__device__ __forceinline__ void mma_f16_ta_elect(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc,
-                                                 uint32_t idesc, uint32_t accumulate) {
-    asm volatile(
-        "{\n\t.reg .pred p, e;\n\t"
-        "elect.sync _|e, 0xffffffff;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accumulate)
-        : "memory");
-}
+// Warp-collective commit: the whole (converged) warp executes it and one lane,
+// chosen by elect.sync, issues it.
 __device__ __forceinline__ void mma_commit_elect(uint64_t* bar) {
     asm volatile(
         "{\n\t.reg .pred e;\n\t"
         "elect.sync _|e, 0xffffffff;\n\t"
         "@e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n\t}" ::"r"(
             smem_addr(bar))
+        : "memory");
+}
+
+// One ring stage of four 16-point chunks, A from tensor memory: for chunk
+// j = 0 .. 3 the products A_hi,j x B_j (instruction descriptor i_hi) and
+// A_lo,j x B_j (i_lo), all into d_tmem, then the commit that arrives on bar
+// once they completed.  A_hi,j and A_lo,j start at TMEM columns a + 16 j and
+// a + 16 j + 8; B_j's descriptor is b0 + j * bstep.  The first product
+// accumulates only if acc0 != 0.  Warp-collective: one elect.sync picks the
+// lane that issues all nine instructions, which keeps the issue cost per MMA
+// below the tensor pipe's time for these small shapes.
+__device__ __forceinline__ void mma_stage4_elect(uint32_t d_tmem, uint32_t a, uint64_t b0, uint64_t bstep,
+                                                 uint64_t* bar, uint32_t acc0, uint32_t i_hi, uint32_t i_lo) {
+    asm volatile(
+        "{\n\t.reg .pred e, p0, p1;\n\t"
+        ".reg .b32 a1, a2, a3, a4, a5, a6, a7;\n\t"
+        ".reg .b64 b1, b2, b3;\n\t"
+        "add.u32 a1, %1, 8;\n\tadd.u32 a2, %1, 16;\n\tadd.u32 a3, %1, 24;\n\t"
+        "add.u32 a4, %1, 32;\n\tadd.u32 a5, %1, 40;\n\tadd.u32 a6, %1, 48;\n\t"
+        "add.u32 a7, %1, 56;\n\t"
+        "add.u64 b1, %2, %3;\n\tadd.u64 b2, b1, %3;\n\tadd.u64 b3, b2, %3;\n\t"
+        "elect.sync _|e, 0xffffffff;\n\t"
+        "setp.ne.b32 p0, %5, 0;\n\t"
+        "setp.ne.b32 p1, 1, 0;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %6, p0;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], [a1], %2, %7, p1;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], [a2], b1, %6, p1;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], [a3], b1, %7, p1;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], [a4], b2, %6, p1;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], [a5], b2, %7, p1;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], [a6], b3, %6, p1;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], [a7], b3, %7, p1;\n\t"
+        "@e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%4];\n\t}" ::"r"(d_tmem),
+        "r"(a), "l"(b0), "l"(bstep), "r"(smem_addr(bar)), "r"(acc0), "r"(i_hi), "r"(i_lo)
         : "memory");
 }
 
