@@ -56,7 +56,7 @@ constexpr int B_MAX = 144 * 1024;     // largest resident share (NS = 8)
 constexpr uint64_t kWaitNs = 2000000000ull;
 
 struct ClLayout {
-    int b, bars, tslot, abort_flag, xq, xm, qloc, mloc, sst, ep, om, xs, al, seg, il2, obs, total;
+    int b, bars, tslot, abort_flag, xx, sst, xs, al, seg, il2, obs, total;
 };
 
 // shared-memory layout; the resident B share is sized for the largest rank;
@@ -69,14 +69,11 @@ __host__ __device__ inline ClLayout cl_layout(int npc, int S, int O) {
     L.bars = B_MAX;                              // a_full, empty [NSTAGE], b_res, pass_done, tmem_free, xbar[2]
     L.tslot = L.bars + 8 * (2 * NSTAGE + 5);
     L.abort_flag = L.tslot + 4;
-    L.xq = ((L.abort_flag + 4 + 15) / 16) * 16;  // [2][4][MT] floats: partial |V|^2 per rank
-    L.xm = L.xq + 2 * 4 * MT * 4;                // [2][4][MT] float2: GP mean partial per rank
-    L.qloc = L.xm + 2 * 4 * MT * 8;              // [2][MT] floats
-    L.mloc = L.qloc + 2 * MT * 4;                // [2][MT] float2
-    L.sst = L.mloc + 2 * MT * 8;                 // [nown][24] floats: post-step state for the cost phase
-    L.ep = L.sst + nown * 24 * 4;                // [NPROD] floats
-    L.om = L.ep + NPROD * 4;                     // [NPROD] floats
-    L.xs = ((L.om + NPROD * 4 + 127) / 128) * 128;
+    // exchange buffers [2 (step parity)][8 (rank, thread half)][MT] float4:
+    // (partial |V|^2, GP mean partial v, w, 0) of every producer thread
+    L.xx = ((L.abort_flag + 4 + 15) / 16) * 16;
+    L.sst = L.xx + 2 * 8 * MT * 16;              // [2][nown][24] floats: post-step state for the cost phase
+    L.xs = ((L.sst + 2 * nown * 24 * 4 + 127) / 128) * 128;
     L.al = L.xs + npc * 16;
     L.seg = L.al + npc * 8;                      // S float4
     L.il2 = L.seg + S * 16;                      // S floats
@@ -214,19 +211,14 @@ __device__ __forceinline__ uint32_t peer_addr(const void* p, uint32_t peer) {
     return r;
 }
 
-__device__ __forceinline__ void st_peer_f32(uint32_t addr, float v) {
-    asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
+// asynchronous 16-byte store into a cluster CTA's shared memory that completes
+// 16 transaction bytes on the mbarrier at bar (same CTA as addr)
+__device__ __forceinline__ void st_async_f32x4(uint32_t addr, float4 v, uint32_t bar) {
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.f32 [%0], {%1, %2, %3, %4}, [%5];" ::"r"(
+                     addr),
+                 "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "r"(bar)
+                 : "memory");
 }
-
-__device__ __forceinline__ void st_peer_f32x2(uint32_t addr, float2 v) {
-    asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(addr), "f"(v.x), "f"(v.y) : "memory");
-}
-
-__device__ __forceinline__ void arrive_peer(uint32_t bar_addr) {
-    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar_addr) : "memory");
-}
-
-__device__ __forceinline__ void fence_cluster() { asm volatile("fence.acq_rel.cluster;" ::: "memory"); }
 
 __device__ __forceinline__ void cluster_sync_all() {
     asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
@@ -245,13 +237,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_cl(const RolloutArgs a, 
     uint64_t* xbar = tmem_free + 1;             // [2]
     uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + L.tslot);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + L.abort_flag);
-    float* xq = reinterpret_cast<float*>(sm + L.xq);
-    float2* xm = reinterpret_cast<float2*>(sm + L.xm);
-    float* qloc = reinterpret_cast<float*>(sm + L.qloc);
-    float2* mloc = reinterpret_cast<float2*>(sm + L.mloc);
+    float4* xx = reinterpret_cast<float4*>(sm + L.xx);
     float* sst = reinterpret_cast<float*>(sm + L.sst);
-    float* ep = reinterpret_cast<float*>(sm + L.ep);
-    float* omh = reinterpret_cast<float*>(sm + L.om);
     float4* xs_s = reinterpret_cast<float4*>(sm + L.xs);
     float4* al_s = reinterpret_cast<float4*>(sm + L.al);
     float4* seg_s = reinterpret_cast<float4*>(sm + L.seg);
@@ -276,8 +263,10 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_cl(const RolloutArgs a, 
         tc::mbar_init(b_res, 1);
         tc::mbar_init(pass_done, 1);
         tc::mbar_init(tmem_free, NPROD / 32);
-        tc::mbar_init(xbar, CS > 1 ? CS - 1 : 1);
-        tc::mbar_init(xbar + 1, CS > 1 ? CS - 1 : 1);
+        // one local arrival (with the expected bytes) per phase; the partials
+        // arrive as transaction bytes
+        tc::mbar_init(xbar, 1);
+        tc::mbar_init(xbar + 1, 1);
         *abort_flag = 0;
         tc::fence_mbar_init();
     }
@@ -391,10 +380,11 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_cl(const RolloutArgs a, 
         const int s_me = tile * MT + m;
         const bool active = s_me < a.K;
         const int s_q = active ? s_me : 0;
-        // cost phase: this rank scores samples m = rank (mod CS); RC threads per sample
+        // cost phase: this rank scores samples m = rank (mod CS); RC consecutive
+        // lanes per sample (RC = 2, 4 or 8 divides the warp)
         const int nown = MT / CS;
         const int RC = NPROD / nown;
-        const int ci = tid % nown, cpart = tid / nown;
+        const int ci = tid / RC, cpart = tid % RC;
         const int mc = (int)rank + CS * ci;
         const int sc_me = tile * MT + mc;
         const bool cactive = sc_me < a.K;
@@ -532,39 +522,27 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_cl(const RolloutArgs a, 
             tc::fence_before_sync();
             __syncwarp();
             if (lane == 0) mbar_arrive(tmem_free);
-            qloc[u * MT + m] = qpart;
-            mloc[u * MT + m] = make_float2(mv + cv, mw + cw);
-            producers_sync();
             // ---------------- exchange between the ranks ---------------------------
+            // every producer thread sends (its |V_m|^2 partial, its GP mean share)
+            // to slot (rank, u) of sample m in every rank's buffer, its own
+            // included, as asynchronous stores that complete transaction bytes on
+            // the receiver's exchange barrier; no CTA barrier is needed
             const int buf = k & 1;
-            if (u == 0) {
-                const float qc = qloc[m] + qloc[MT + m];
-                float* mine = xq + (buf * 4 + (int)rank) * MT + m;
-                *mine = qc;
+            if (tid == 0) tc::mbar_expect_tx(xbar + buf, (uint32_t)(CS * 2 * MT * 16));
+            {
+                const float4 mine = make_float4(qpart, mv + cv, mw + cw, 0.0f);
+                const float4* slot = xx + (buf * 8 + 2 * (int)rank + u) * MT + m;
                 for (int p = 0; p < CS; ++p)
-                    if (p != (int)rank) st_peer_f32(peer_addr(mine, (uint32_t)p), qc);
-                const float2 m0 = mloc[m], m1 = mloc[MT + m];
-                const float2 mm = make_float2(m0.x + m1.x, m0.y + m1.y);
-                float2* mslot = xm + (buf * 4 + (int)rank) * MT + m;
-                *mslot = mm;
-                for (int p = 0; p < CS; ++p)
-                    if (p != (int)rank) st_peer_f32x2(peer_addr(mslot, (uint32_t)p), mm);
-                fence_cluster();
+                    st_async_f32x4(peer_addr(slot, (uint32_t)p), mine, peer_addr(xbar + buf, (uint32_t)p));
             }
-            producers_sync();
-            if (CS > 1) {
-                if (tid == 0)
-                    for (int p = 0; p < CS; ++p)
-                        if (p != (int)rank) arrive_peer(peer_addr(xbar + buf, (uint32_t)p));
-                wait_cluster(xbar + buf, (uint32_t)(k >> 1) & 1u, abort_flag, a.err);
-            }
+            wait_cluster(xbar + buf, (uint32_t)(k >> 1) & 1u, abort_flag, a.err);
             float qsum = 0.0f;
             float2 msum = make_float2(0.0f, 0.0f);
-            for (int p = 0; p < CS; ++p) {      // fixed order: identical on every rank
-                qsum += xq[(buf * 4 + p) * MT + m];
-                const float2 mp = xm[(buf * 4 + p) * MT + m];
-                msum.x += mp.x;
-                msum.y += mp.y;
+            for (int p = 0; p < 2 * CS; ++p) {      // fixed order: identical on every rank
+                const float4 v = xx[(buf * 8 + p) * MT + m];
+                qsum += v.x;
+                msum.x += v.y;
+                msum.y += v.z;
             }
             const float q = qsum * cl.qscale;
             const float mean_v = a.sf2 * msum.x, mean_w = a.sf2 * msum.y;
@@ -607,8 +585,9 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_cl(const RolloutArgs a, 
                 S44 = a.aw * B44 + s;
             }
             // the post-step state of sample m for the rank that scores it
+            float* sstk = sst + (k & 1) * nown * 24;     // double-buffered by step parity
             if (u == 0 && (m % CS) == (int)rank) {
-                float* o = sst + (m / CS) * 24;
+                float* o = sstk + (m / CS) * 24;
                 o[0] = mu0; o[1] = mu1; o[2] = mu2; o[3] = mu3; o[4] = mu4;
                 o[5] = S00; o[6] = S01; o[7] = S02; o[8] = S03; o[9] = S04;
                 o[10] = S11; o[11] = S12; o[12] = S13; o[13] = S14;
@@ -619,7 +598,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_cl(const RolloutArgs a, 
             producers_sync();
             // ---------------- cost phase: RC threads per scored sample -------------
             {
-                const float* o = sst + ci * 24;
+                const float* o = sstk + ci * 24;
                 const float px = o[0], py = o[1];
                 float sxx = o[5], sxy = o[6], syy = o[10];
                 if (a.nom_sxy) {
@@ -653,15 +632,12 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_cl(const RolloutArgs a, 
                     const float qx = qx0 - t * sg.z, qy = qy0 - t * sg.w;
                     best = fminf(best, qx * qx + qy * qy);
                 }
-                ep[tid] = best;
-                omh[tid] = om;
-                producers_sync();
+                for (int o2 = RC >> 1; o2 > 0; o2 >>= 1) {       // within the sample's lanes
+                    om = fminf(om, __shfl_xor_sync(0xffffffffu, om, o2));
+                    best = fminf(best, __shfl_xor_sync(0xffffffffu, best, o2));
+                }
                 if (cpart == 0) {
-                    float omargin = omh[ci], e2min = ep[ci];
-                    for (int i = 1; i < RC; ++i) {
-                        omargin = fminf(omargin, omh[i * nown + ci]);
-                        e2min = fminf(e2min, ep[i * nown + ci]);
-                    }
+                    const float omargin = om, e2min = best;
                     const float e_lane = sqrtf(e2min);
                     const float rbar = a.r - a.sq_chi2 * sqrtf(lmax);
                     const float sv = o[20], vv = o[3];
