@@ -38,7 +38,8 @@ namespace {
 
 constexpr int MT = 128;               // samples per cluster (the MMA M)
 constexpr int NPROD = 256;            // producer threads: two per sample
-constexpr int THREADS = NPROD + 32;   // + the MMA-issuing warp
+constexpr int NCOST = 64;             // scoring threads (two warps)
+constexpr int THREADS = NPROD + 32 + NCOST;   // + the MMA-issuing warp and the scoring warps
 constexpr int NSTAGE = 4;             // kernel-row tile ring (in tensor memory)
 constexpr int GCH = 4;                // chunks per stage: one hand-off per four chunks
 static_assert(GCH == 4, "the issue loop issues a stage as four chunks");
@@ -66,8 +67,9 @@ __host__ __device__ inline ClLayout cl_layout(int npc, int S, int O) {
     const int nown = MT / (npc / 128);
     ClLayout L;
     L.b = 0;
-    L.bars = B_MAX;                              // a_full, empty [NSTAGE], b_res, pass_done, tmem_free, xbar[2]
-    L.tslot = L.bars + 8 * (2 * NSTAGE + 5);
+    // a_full, empty [NSTAGE], b_res, pass_done, tmem_free, xbar[2], st_full[2], st_empty[2]
+    L.bars = B_MAX;
+    L.tslot = L.bars + 8 * (2 * NSTAGE + 9);
     L.abort_flag = L.tslot + 4;
     // exchange buffers [2 (step parity)][8 (rank, thread half)][MT] float4:
     // (partial |V|^2, GP mean partial v, w, 0) of every producer thread
@@ -192,8 +194,6 @@ __device__ __forceinline__ bool wait_cluster(uint64_t* bar, uint32_t parity, vol
     return true;
 }
 
-__device__ __forceinline__ void producers_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
-
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_addr(bar)) : "memory");
 }
@@ -235,6 +235,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_cl(const RolloutArgs a, 
     uint64_t* pass_done = b_res + 1;
     uint64_t* tmem_free = pass_done + 1;
     uint64_t* xbar = tmem_free + 1;             // [2]
+    uint64_t* st_full = xbar + 2;               // [2] post-step states handed to the scoring warps
+    uint64_t* st_empty = st_full + 2;           // [2] ... and released by them
     uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + L.tslot);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + L.abort_flag);
     float4* xx = reinterpret_cast<float4*>(sm + L.xx);
@@ -267,6 +269,10 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_cl(const RolloutArgs a, 
         // arrive as transaction bytes
         tc::mbar_init(xbar, 1);
         tc::mbar_init(xbar + 1, 1);
+        for (int i = 0; i < 2; ++i) {
+            tc::mbar_init(st_full + i, 4);             // the four warps holding the writers
+            tc::mbar_init(st_empty + i, NCOST / 32);
+        }
         *abort_flag = 0;
         tc::fence_mbar_init();
     }
@@ -371,7 +377,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_cl(const RolloutArgs a, 
                 }
         }
         __syncwarp();
-    } else {
+    } else if (warp < NPROD / 32) {
         // ========================== producer warps =============================
         const int m = tid & (MT - 1);          // sample within the cluster (= its TMEM lane)
         const int u = tid >> 7;                // which of its two threads (half of each chunk)
@@ -380,29 +386,24 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_cl(const RolloutArgs a, 
         const int s_me = tile * MT + m;
         const bool active = s_me < a.K;
         const int s_q = active ? s_me : 0;
-        // cost phase: this rank scores samples m = rank (mod CS); RC consecutive
-        // lanes per sample (RC = 2, 4 or 8 divides the warp)
-        const int nown = MT / CS;
-        const int RC = NPROD / nown;
-        const int ci = tid / RC, cpart = tid % RC;
-        const int mc = (int)rank + CS * ci;
-        const int sc_me = tile * MT + mc;
-        const bool cactive = sc_me < a.K;
+        const int nown = MT / CS;              // samples scored by this rank
 
         float mu0 = a.x0[0], mu1 = a.x0[1], mu2 = a.x0[2], mu3 = a.x0[3], mu4 = a.x0[4];
         const uint32_t it0 = a.it0, it1 = a.it1;
         float S00 = 0, S01 = 0, S02 = 0, S03 = 0, S04 = 0, S11 = 0, S12 = 0, S13 = 0, S14 = 0,
               S22 = 0, S23 = 0, S24 = 0, S33 = 0, S34 = 0, S44 = 0;
-        float cost = 0.0f, disc = 1.0f;
         uint32_t n = 0;
+        // the noise and nominal control of step k are fetched one step ahead (the
+        // noise while the last MMAs of the previous step complete)
+        float2 e = control_eps(0u, (uint32_t)s_q, it0, it1, a.key0, a.key1, a.sig_v, a.sig_w);
+        float2 un = make_float2(__ldg(a.U), __ldg(a.U + 1));     // (U may be only 4-byte aligned)
 
         for (int k = 0; k < a.T; ++k) {
             // ---------------- noise, clamp, query --------------------------------
-            const float2 e = control_eps((uint32_t)k, (uint32_t)s_q, it0, it1, a.key0, a.key1, a.sig_v,
-                                         a.sig_w);
             float2 ut;
-            ut.x = fminf(fmaxf(__ldg(a.U + 2 * k) + e.x, a.umin0), a.umax0);
-            ut.y = fminf(fmaxf(__ldg(a.U + 2 * k + 1) + e.y, a.umin1), a.umax1);
+            ut.x = fminf(fmaxf(un.x + e.x, a.umin0), a.umax0);
+            ut.y = fminf(fmaxf(un.y + e.y, a.umin1), a.umax1);
+            if (k + 1 < a.T) un = make_float2(__ldg(a.U + 2 * k + 2), __ldg(a.U + 2 * k + 3));
             if (u == 0 && active && (m % CS) == (int)rank) a.u_tilde[(size_t)k * a.K + s_me] = ut;
             const float z0 = mu3 * a.zscale[0], z1 = mu4 * a.zscale[1];
             const float z2 = ut.x * a.zscale[2], z3 = ut.y * a.zscale[3];
@@ -491,6 +492,9 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_cl(const RolloutArgs a, 
                 kernel_row(c, av);
                 mean_part(c, av);
             }
+            // the next step's noise, while the last MMAs complete
+            if (k + 1 < a.T)
+                e = control_eps((uint32_t)(k + 1), (uint32_t)s_q, it0, it1, a.key0, a.key1, a.sig_v, a.sig_w);
             // ---------------- this rank's partial |V_m|^2 -------------------------
             bool ok = wait_or_abort(pass_done, (uint32_t)k & 1u, abort_flag, a.err);
             ok = __all_sync(0xffffffffu, ok);    // tcgen05.ld is warp-collective
@@ -584,20 +588,51 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_cl(const RolloutArgs a, 
                 S34 = a.aw * B34;
                 S44 = a.aw * B44 + s;
             }
-            // the post-step state of sample m for the rank that scores it
-            float* sstk = sst + (k & 1) * nown * 24;     // double-buffered by step parity
-            if (u == 0 && (m % CS) == (int)rank) {
-                float* o = sstk + (m / CS) * 24;
-                o[0] = mu0; o[1] = mu1; o[2] = mu2; o[3] = mu3; o[4] = mu4;
-                o[5] = S00; o[6] = S01; o[7] = S02; o[8] = S03; o[9] = S04;
-                o[10] = S11; o[11] = S12; o[12] = S13; o[13] = S14;
-                o[14] = S22; o[15] = S23; o[16] = S24;
-                o[17] = S33; o[18] = S34; o[19] = S44;
-                o[20] = s;
+            // ---------------- hand the post-step state to the scoring warps --------
+            // (rank r scores the samples m = r mod CS; the buffer of step k is
+            // reused at step k + 2, once the scoring warps released it)
+            if (warp < 4) {
+                float* sstk = sst + (k & 1) * nown * 24;
+                if (k >= 2) {
+                    wait_or_abort(st_empty + (k & 1), (uint32_t)((k >> 1) - 1) & 1u, abort_flag, a.err);
+                    __syncwarp();
+                }
+                if ((m % CS) == (int)rank) {
+                    float* o = sstk + (m / CS) * 24;
+                    o[0] = mu0; o[1] = mu1; o[2] = mu2; o[3] = mu3; o[4] = mu4;
+                    o[5] = S00; o[6] = S01; o[7] = S02; o[8] = S03; o[9] = S04;
+                    o[10] = S11; o[11] = S12; o[12] = S13; o[13] = S14;
+                    o[14] = S22; o[15] = S23; o[16] = S24;
+                    o[17] = S33; o[18] = S34; o[19] = S44;
+                    o[20] = s;
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(st_full + (k & 1));
             }
-            producers_sync();
-            // ---------------- cost phase: RC threads per scored sample -------------
-            {
+        }
+    } else {
+        // ======================= scoring warps (Eq. 11-16) ======================
+        // the cost of step k of the samples this rank scores, one step behind the
+        // producers; RC lanes per sample (2 with CS = 4, else 1, two passes of 64
+        // samples with CS = 1)
+        const int nown = MT / CS;
+        const int ct = tid - (NPROD + 32);
+        const int RC = nown >= NCOST ? 1 : NCOST / nown;
+        const int spp = NCOST / RC;                 // samples per pass
+        const int cpart = ct % RC;
+        float cost[2] = {0.0f, 0.0f};
+        float disc = 1.0f;
+        for (int k = 0; k < a.T; ++k) {
+            wait_or_abort(st_full + (k & 1), (uint32_t)(k >> 1) & 1u, abort_flag, a.err);
+            __syncwarp();
+            const float* sstk = sst + (k & 1) * nown * 24;
+#pragma unroll
+            for (int js = 0; js < 2; ++js) {
+                const int ci = ct / RC + js * spp;
+                if (js * spp >= nown) break;            // warp-uniform
+                const int mc = (int)rank + CS * ci;
+                const int sc_me = tile * MT + mc;
+                const bool cactive = sc_me < a.K;
                 const float* o = sstk + ci * 24;
                 const float px = o[0], py = o[1];
                 float sxx = o[5], sxy = o[6], syy = o[10];
@@ -606,6 +641,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_cl(const RolloutArgs a, 
                     sxy = __ldg(a.nom_sxy + 3 * k + 1);
                     syy = __ldg(a.nom_sxy + 3 * k + 2);
                 }
+                const int2 oc = lane_cands(a, px, py);     // candidate segments of this position
                 const float lmax = fmaxf(0.0f, 0.5f * (sxx + syy) + hypotf(0.5f * (sxx - syy), sxy));
                 float om = FLT_MAX;
                 for (int ob = cpart; ob < a.O; ob += RC) {
@@ -622,15 +658,25 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_cl(const RolloutArgs a, 
                     om = fminf(om, (rho - R) - a.phi_inv * spread);
                 }
                 float best = FLT_MAX;
-                const int2 oc = lane_cands(a, px, py);     // candidate segments of this position
-                for (int i = cpart; i < oc.y; i += RC) {
-                    const int gsg = lane_seg(a, oc, i);
-                    const float4 sg = segp[gsg];
-                    const float il2 = il2p[gsg];
-                    const float qx0 = px - sg.x, qy0 = py - sg.y;
-                    const float t = fminf(fmaxf((qx0 * sg.z + qy0 * sg.w) * il2, 0.0f), 1.0f);
-                    const float qx = qx0 - t * sg.z, qy = qy0 - t * sg.w;
-                    best = fminf(best, qx * qx + qy * qy);
+                // candidates in groups of four per lane, their indices fetched
+                // together (one memory latency per group instead of one per candidate)
+                for (int i0 = cpart; i0 < oc.y; i0 += 4 * RC) {
+                    int gsg[4];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const int i = i0 + j * RC;
+                        gsg[j] = i < oc.y ? lane_seg(a, oc, i) : -1;
+                    }
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        if (gsg[j] < 0) continue;
+                        const float4 sg = segp[gsg[j]];
+                        const float il2 = il2p[gsg[j]];
+                        const float qx0 = px - sg.x, qy0 = py - sg.y;
+                        const float t = fminf(fmaxf((qx0 * sg.z + qy0 * sg.w) * il2, 0.0f), 1.0f);
+                        const float qx = qx0 - t * sg.z, qy = qy0 - t * sg.w;
+                        best = fminf(best, qx * qx + qy * qy);
+                    }
                 }
                 for (int o2 = RC >> 1; o2 > 0; o2 >>= 1) {       // within the sample's lanes
                     om = fminf(om, __shfl_xor_sync(0xffffffffu, om, o2));
@@ -647,7 +693,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_cl(const RolloutArgs a, 
                     stage += a.c_dev * e_lane;
                     if (lmargin > 0.0f) stage += a.c_lane * disc;
                     stage += goal_cost(a, k, px, py);                     // Eq. 12 goal terms
-                    cost += stage;
+                    cost[js] += stage;
                     if (TRACE && cactive) {
                         const size_t sk = (size_t)sc_me * a.T + k;
                         if (a.tr_mu)
@@ -661,10 +707,18 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_cl(const RolloutArgs a, 
                         }
                     }
                 }
-                disc *= 0.9f;
             }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(st_empty + (k & 1));
+            disc *= 0.9f;
         }
-        if (cpart == 0 && cactive && a.costs) a.costs[sc_me] = cost;
+#pragma unroll
+        for (int js = 0; js < 2; ++js) {
+            const int ci = ct / RC + js * spp;
+            if (js * spp >= nown) break;
+            const int sc_me = tile * MT + (int)rank + CS * ci;
+            if (cpart == 0 && sc_me < a.K && a.costs) a.costs[sc_me] = cost[js];
+        }
     }
     // no CTA leaves while a peer may still write into its shared memory
     tc::fence_before_sync();
