@@ -44,6 +44,7 @@ constexpr int NSTAGE = 4;             // kernel-row tile ring (in tensor memory)
 constexpr int GCH = 4;                // chunks per stage: one hand-off per four chunks
 static_assert(GCH == 4, "the issue loop issues a stage as four chunks");
 constexpr int BURST = 4;              // chunks whose kernel rows a thread computes together
+static_assert(BURST == GCH, "a producer burst fills exactly one stage");
 // TMEM columns: the accumulators D in columns [0, 256) (hi.hi + lo.hi of the
 // lower and upper slice in 0-63 and 64-127, hi.lo of the upper slice in
 // 128-191, of the lower in 192-255), the A ring after them; a chunk's A tile
@@ -55,9 +56,12 @@ constexpr uint32_t A_STAGE_COLS = GCH * A_CHUNK_COLS;
 static_assert(A_COL + NSTAGE * A_STAGE_COLS <= TM_COLS, "A ring exceeds the TMEM allocation");
 constexpr int B_MAX = 144 * 1024;     // largest resident share (NS = 8)
 constexpr uint64_t kWaitNs = 2000000000ull;
+// hand-off record of one scored sample and step: post-step mean (5), pre-step
+// speed, sin and cos of the pre-step heading, GP variance s
+constexpr int SST = 12;
 
 struct ClLayout {
-    int b, bars, tslot, abort_flag, xx, sst, xs, al, seg, il2, obs, total;
+    int b, bars, tslot, abort_flag, xx, sst, nz, xs, al, seg, il2, obs, total;
 };
 
 // shared-memory layout; the resident B share is sized for the largest rank;
@@ -67,15 +71,16 @@ __host__ __device__ inline ClLayout cl_layout(int npc, int S, int O) {
     const int nown = MT / (npc / 128);
     ClLayout L;
     L.b = 0;
-    // a_full, empty [NSTAGE], b_res, pass_done, tmem_free, xbar[2], st_full[2], st_empty[2]
+    // a_full, empty [NSTAGE], b_res, pass_done, tmem_free, xbar[2], st_full[2], st_empty[2], nz_full[2]
     L.bars = B_MAX;
-    L.tslot = L.bars + 8 * (2 * NSTAGE + 9);
+    L.tslot = L.bars + 8 * (2 * NSTAGE + 11);
     L.abort_flag = L.tslot + 4;
     // exchange buffers [2 (step parity)][8 (rank, thread half)][MT] float4:
     // (partial |V|^2, GP mean partial v, w, 0) of every producer thread
     L.xx = ((L.abort_flag + 4 + 15) / 16) * 16;
-    L.sst = L.xx + 2 * 8 * MT * 16;              // [2][nown][24] floats: post-step state for the cost phase
-    L.xs = ((L.sst + 2 * nown * 24 * 4 + 127) / 128) * 128;
+    L.sst = L.xx + 2 * 8 * MT * 16;              // [2][nown][SST] floats: per-step hand-off to the scoring warps
+    L.nz = L.sst + 2 * nown * SST * 4;           // [2][MT] float2: control noise, computed two steps ahead
+    L.xs = ((L.nz + 2 * MT * 8 + 127) / 128) * 128;
     L.al = L.xs + npc * 16;
     L.seg = L.al + npc * 8;                      // S float4
     L.il2 = L.seg + S * 16;                      // S floats
@@ -165,8 +170,8 @@ __device__ __forceinline__ bool try_wait_cluster(uint64_t* bar, uint32_t parity)
 // Bounded wait (CTA-local phases: the tensor pipe, the producers).
 __device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
                                               unsigned int* err) {
-    if (*abort_flag) return false;
     if (tc::mbar_try_wait(bar, parity)) return true;
+    if (*abort_flag) return false;
     const uint64_t t0 = tc::global_ns();
     while (!tc::mbar_try_wait(bar, parity)) {
         if (*abort_flag) return false;
@@ -237,10 +242,12 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_cl(const RolloutArgs a, 
     uint64_t* xbar = tmem_free + 1;             // [2]
     uint64_t* st_full = xbar + 2;               // [2] post-step states handed to the scoring warps
     uint64_t* st_empty = st_full + 2;           // [2] ... and released by them
+    uint64_t* nz_full = st_empty + 2;           // [2] noise of a step, written by the scoring warps
     uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + L.tslot);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + L.abort_flag);
     float4* xx = reinterpret_cast<float4*>(sm + L.xx);
     float* sst = reinterpret_cast<float*>(sm + L.sst);
+    float2* nz = reinterpret_cast<float2*>(sm + L.nz);
     float4* xs_s = reinterpret_cast<float4*>(sm + L.xs);
     float4* al_s = reinterpret_cast<float4*>(sm + L.al);
     float4* seg_s = reinterpret_cast<float4*>(sm + L.seg);
@@ -272,6 +279,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_cl(const RolloutArgs a, 
         for (int i = 0; i < 2; ++i) {
             tc::mbar_init(st_full + i, 4);             // the four warps holding the writers
             tc::mbar_init(st_empty + i, NCOST / 32);
+            tc::mbar_init(nz_full + i, NCOST / 32);
         }
         *abort_flag = 0;
         tc::fence_mbar_init();
@@ -385,26 +393,28 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_cl(const RolloutArgs a, 
         const uint32_t a_lane = taddr + ((uint32_t)(32 * (warp & 3)) << 16) + A_COL;
         const int s_me = tile * MT + m;
         const bool active = s_me < a.K;
-        const int s_q = active ? s_me : 0;
         const int nown = MT / CS;              // samples scored by this rank
 
         float mu0 = a.x0[0], mu1 = a.x0[1], mu2 = a.x0[2], mu3 = a.x0[3], mu4 = a.x0[4];
-        const uint32_t it0 = a.it0, it1 = a.it1;
-        float S00 = 0, S01 = 0, S02 = 0, S03 = 0, S04 = 0, S11 = 0, S12 = 0, S13 = 0, S14 = 0,
-              S22 = 0, S23 = 0, S24 = 0, S33 = 0, S34 = 0, S44 = 0;
         uint32_t n = 0;
-        // the noise and nominal control of step k are fetched one step ahead (the
-        // noise while the last MMAs of the previous step complete)
-        float2 e = control_eps(0u, (uint32_t)s_q, it0, it1, a.key0, a.key1, a.sig_v, a.sig_w);
-        float2 un = make_float2(__ldg(a.U), __ldg(a.U + 1));     // (U may be only 4-byte aligned)
+        // the perturbed control of step k (Alg. 1: nominal plus noise, clamped);
+        // the noise comes from the scoring warps, which compute it two steps
+        // ahead, and the control of step k + 1 is prepared while the MMAs of step
+        // k complete
+        auto control = [&](int kk) {
+            wait_or_abort(nz_full + (kk & 1), (uint32_t)(kk >> 1) & 1u, abort_flag, a.err);
+            const float2 e = nz[(kk & 1) * MT + m];
+            float2 uk;
+            uk.x = fminf(fmaxf(__ldg(a.U + 2 * kk) + e.x, a.umin0), a.umax0);
+            uk.y = fminf(fmaxf(__ldg(a.U + 2 * kk + 1) + e.y, a.umin1), a.umax1);
+            if (u == 0 && active && (m % CS) == (int)rank) a.u_tilde[(size_t)kk * a.K + s_me] = uk;
+            return uk;
+        };
+        float2 ut_next = control(0);
 
         for (int k = 0; k < a.T; ++k) {
-            // ---------------- noise, clamp, query --------------------------------
-            float2 ut;
-            ut.x = fminf(fmaxf(un.x + e.x, a.umin0), a.umax0);
-            ut.y = fminf(fmaxf(un.y + e.y, a.umin1), a.umax1);
-            if (k + 1 < a.T) un = make_float2(__ldg(a.U + 2 * k + 2), __ldg(a.U + 2 * k + 3));
-            if (u == 0 && active && (m % CS) == (int)rank) a.u_tilde[(size_t)k * a.K + s_me] = ut;
+            // ---------------- query ------------------------------------------------
+            const float2 ut = ut_next;
             const float z0 = mu3 * a.zscale[0], z1 = mu4 * a.zscale[1];
             const float z2 = ut.x * a.zscale[2], z3 = ut.y * a.zscale[3];
 
@@ -416,12 +426,12 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_cl(const RolloutArgs a, 
             float mv = 0.0f, mw = 0.0f, cv = 0.0f, cw = 0.0f;
             const uint64_t zz0 = f2pack(z0, z0), zz1 = f2pack(z1, z1);
             const uint64_t zz2 = f2pack(z2, z2), zz3 = f2pack(z3, z3);
-            // kernel-row entries of the thread's 8 points of chunk c, as 4 packed
-            // pairs: av[q] = (2^-d(z, x_2p), 2^-d(z, x_2p+1)) for pair p = pb + q
-            auto kernel_row = [&](int c, uint64_t (&av)[4]) {
-                const int pb = c * 8 + u * 4;
+            // kernel-row entries of the 16 points of chunk c, as 8 packed pairs:
+            // av[q] = (2^-d(z, x_2p), 2^-d(z, x_2p+1)) for pair p = 8 c + q
+            auto kernel_row = [&](int c, uint64_t (&av)[8]) {
+                const int pb = c * 8;
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
+                for (int q = 0; q < 8; ++q) {
                     const ulonglong2 xa = *reinterpret_cast<const ulonglong2*>(xs_s + 2 * (pb + q));
                     const ulonglong2 xb = *reinterpret_cast<const ulonglong2*>(xs_s + 2 * (pb + q) + 1);
                     const uint64_t d0 = f2sub(zz0, xa.x), d1 = f2sub(zz1, xa.y);
@@ -435,11 +445,11 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_cl(const RolloutArgs a, 
                     av[q] = f2pack(ex2_ftz(-t0), ex2_ftz(-t1));
                 }
             };
-            auto mean_part = [&](int c, const uint64_t (&av)[4]) {
-                const int pb = c * 8 + u * 4;
+            auto mean_part = [&](int c, const uint64_t (&av)[8]) {
+                const int pb = c * 8;
                 uint64_t pv = 0ull, pw = 0ull;     // (even, odd) partial sums
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
+                for (int q = 0; q < 8; ++q) {
                     const ulonglong2 al = *reinterpret_cast<const ulonglong2*>(al_s + pb + q);
                     pv = f2fma(av[q], al.x, pv);
                     pw = f2fma(av[q], al.y, pw);
@@ -451,50 +461,50 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_cl(const RolloutArgs a, 
                 kahan_add(mw, cw, pw0 + pw1);
             };
             for (int c = 0; c < nch; c += BURST) {      // nch is a multiple of 4 (and of BURST)
-                uint64_t av[BURST][4];
+                // the sample's two threads take alternate chunks of the burst:
+                // thread half u the chunks c + u and c + 2 + u, all 16 points each
+                uint64_t av[2][8];
 #pragma unroll
-                for (int h = 0; h < BURST; ++h) kernel_row(c + h, av[h]);
+                for (int j = 0; j < 2; ++j) kernel_row(c + 2 * j + u, av[j]);
 #pragma unroll
-                for (int h = 0; h < BURST; ++h)
-                    if (c + h >= mc0 && c + h < mc1) mean_part(c + h, av[h]);
-                uint32_t hw[BURST][4], lw[BURST][4];
+                for (int j = 0; j < 2; ++j)
+                    if (c + 2 * j + u >= mc0 && c + 2 * j + u < mc1) mean_part(c + 2 * j + u, av[j]);
+                // per chunk: hi parts in columns 0-7, lo parts in 8-15
+                uint32_t hl[2][16];
 #pragma unroll
-                for (int h = 0; h < BURST; ++h)
+                for (int j = 0; j < 2; ++j)
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) split2<FMT>(av[h][q], &hw[h][q], &lw[h][q]);
-#pragma unroll
-                for (int h = 0; h < BURST; ++h) {
-                    const int slot = (c + h) % GCH;        // chunk's place in its stage
-                    const int st = (int)(n % NSTAGE);
-                    const uint32_t use = n / NSTAGE;
-                    if (slot == 0 && n >= (uint32_t)NSTAGE) {
-                        // the MMAs that read this stage's columns have completed
-                        wait_or_abort(empty + st, (use - 1) & 1u, abort_flag, a.err);
-                        __syncwarp();                      // tcgen05.st is warp-collective
-                        tc::fence_after_sync();
-                    }
-                    // points 8u .. 8u + 7 of sample m (TMEM lane m) of chunk c + h: four
-                    // packed columns of the hi part, four of the lo part
-                    const uint32_t col = a_lane + (uint32_t)st * A_STAGE_COLS + (uint32_t)slot * A_CHUNK_COLS + 4u * u;
-                    tc::tmem_st4(col, hw[h][0], hw[h][1], hw[h][2], hw[h][3]);
-                    tc::tmem_st4(col + 8u, lw[h][0], lw[h][1], lw[h][2], lw[h][3]);
-                    if (slot == GCH - 1) {
-                        tc::tmem_wait_st();
-                        tc::fence_before_sync();
-                        __syncwarp();
-                        if (lane == 0) mbar_arrive(a_full + st);
-                        ++n;
-                    }
+                    for (int q = 0; q < 8; ++q) split2<FMT>(av[j][q], &hl[j][q], &hl[j][8 + q]);
+                // a burst fills one stage (BURST == GCH)
+                const int st = (int)(n % NSTAGE);
+                const uint32_t use = n / NSTAGE;
+                if (n >= (uint32_t)NSTAGE) {
+                    // the MMAs that read this stage's columns have completed
+                    wait_or_abort(empty + st, (use - 1) & 1u, abort_flag, a.err);
+                    __syncwarp();                      // tcgen05.st is warp-collective
+                    tc::fence_after_sync();
                 }
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    // chunk c + 2 j + u of sample m (TMEM lane m): 16 packed columns
+                    const uint32_t col =
+                        a_lane + (uint32_t)st * A_STAGE_COLS + (uint32_t)(2 * j + u) * A_CHUNK_COLS;
+                    tc::tmem_st16(col, hl[j]);
+                }
+                // hand the stage to the MMA warp once the stores have landed
+                tc::tmem_wait_st();
+                tc::fence_before_sync();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(a_full + st);
+                ++n;
             }
-            for (int c = (mc0 > nch ? mc0 : nch); c < mc1; ++c) {
-                uint64_t av[4];
+            // chunks needed for the GP mean alone, alternate between the two threads
+            for (int c = (mc0 > nch ? mc0 : nch) + u; c < mc1; c += 2) {
+                uint64_t av[8];
                 kernel_row(c, av);
                 mean_part(c, av);
             }
-            // the next step's noise, while the last MMAs complete
-            if (k + 1 < a.T)
-                e = control_eps((uint32_t)(k + 1), (uint32_t)s_q, it0, it1, a.key0, a.key1, a.sig_v, a.sig_w);
+            if (k + 1 < a.T) ut_next = control(k + 1);
             // ---------------- this rank's partial |V_m|^2 -------------------------
             bool ok = wait_or_abort(pass_done, (uint32_t)k & 1u, abort_flag, a.err);
             ok = __all_sync(0xffffffffu, ok);    // tcgen05.ld is warp-collective
@@ -508,8 +518,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_cl(const RolloutArgs a, 
 #pragma unroll
                 for (int cc = 0; cc < 64; cc += 32) {
                     float v[32], w[32];
-                    tc::tmem_ld32(row + c0 + (uint32_t)cc, v);
-                    tc::tmem_ld32(row + c1 + (uint32_t)cc, w);
+                    tc::tmem_ld32x2(row + c0 + (uint32_t)cc, row + c1 + (uint32_t)cc, v, w);
                     float p0 = 0.0f, p1 = 0.0f, p2 = 0.0f, p3 = 0.0f;
 #pragma unroll
                     for (int i = 0; i < 8; ++i) {
@@ -542,90 +551,91 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_cl(const RolloutArgs a, 
             wait_cluster(xbar + buf, (uint32_t)(k >> 1) & 1u, abort_flag, a.err);
             float qsum = 0.0f;
             float2 msum = make_float2(0.0f, 0.0f);
-            for (int p = 0; p < 2 * CS; ++p) {      // fixed order: identical on every rank
-                const float4 v = xx[(buf * 8 + p) * MT + m];
-                qsum += v.x;
-                msum.x += v.y;
-                msum.y += v.z;
-            }
+            float4 part[8];
+#pragma unroll
+            for (int p = 0; p < 8; ++p)
+                if (p < 2 * CS) part[p] = xx[(buf * 8 + p) * MT + m];
+#pragma unroll
+            for (int p = 0; p < 8; ++p)              // fixed order: identical on every rank
+                if (p < 2 * CS) {
+                    qsum += part[p].x;
+                    msum.x += part[p].y;
+                    msum.y += part[p].z;
+                }
             const float q = qsum * cl.qscale;
             const float mean_v = a.sf2 * msum.x, mean_w = a.sf2 * msum.y;
             const float s = fmaxf(0.0f, a.sf2 - q);
 
-            // ---------------- dynamics and covariance (all ranks, all samples) -----
+            // ---------------- mean dynamics (all ranks, all samples) ---------------
+            // (the covariance recursion, which the mean never reads, runs in the
+            // scoring warps)
             float sn, cs;
             sincosf(mu2, &sn, &cs);
-            const float a02 = -a.dt * mu3 * sn, a03 = a.dt * cs;
-            const float a12 = a.dt * mu3 * cs, a13 = a.dt * sn;
+            const float v_pre = mu3;
             const float nX = mu0 + a.dt * mu3 * cs;
             const float nY = mu1 + a.dt * mu3 * sn;
             const float nT = mu2 + a.dt * mu4;
             const float nV = mu3 + a.kv * (ut.x - mu3) + mean_v;
             const float nW = mu4 + a.kw * (ut.y - mu4) + mean_w;
             mu0 = nX; mu1 = nY; mu2 = nT; mu3 = nV; mu4 = nW;
-            {
-                const float B00 = S00 + a02 * S02 + a03 * S03, B01 = S01 + a02 * S12 + a03 * S13,
-                            B02 = S02 + a02 * S22 + a03 * S23, B03 = S03 + a02 * S23 + a03 * S33,
-                            B04 = S04 + a02 * S24 + a03 * S34;
-                const float B11 = S11 + a12 * S12 + a13 * S13, B12 = S12 + a12 * S22 + a13 * S23,
-                            B13 = S13 + a12 * S23 + a13 * S33, B14 = S14 + a12 * S24 + a13 * S34;
-                const float B22 = S22 + a.dt * S24, B23 = S23 + a.dt * S34, B24 = S24 + a.dt * S44;
-                const float B33 = a.av * S33, B34 = a.av * S34;
-                const float B44 = a.aw * S44;
-                S00 = B00 + a02 * B02 + a03 * B03;
-                S01 = B01 + a12 * B02 + a13 * B03;
-                S02 = B02 + a.dt * B04;
-                S03 = a.av * B03;
-                S04 = a.aw * B04;
-                S11 = B11 + a12 * B12 + a13 * B13;
-                S12 = B12 + a.dt * B14;
-                S13 = a.av * B13;
-                S14 = a.aw * B14;
-                S22 = B22 + a.dt * B24;
-                S23 = a.av * B23;
-                S24 = a.aw * B24;
-                S33 = a.av * B33 + s;
-                S34 = a.aw * B34;
-                S44 = a.aw * B44 + s;
-            }
-            // ---------------- hand the post-step state to the scoring warps --------
+            // ---------------- hand the step to the scoring warps -------------------
             // (rank r scores the samples m = r mod CS; the buffer of step k is
             // reused at step k + 2, once the scoring warps released it)
             if (warp < 4) {
-                float* sstk = sst + (k & 1) * nown * 24;
+                float* sstk = sst + (k & 1) * nown * SST;
                 if (k >= 2) {
                     wait_or_abort(st_empty + (k & 1), (uint32_t)((k >> 1) - 1) & 1u, abort_flag, a.err);
                     __syncwarp();
                 }
                 if ((m % CS) == (int)rank) {
-                    float* o = sstk + (m / CS) * 24;
+                    float* o = sstk + (m / CS) * SST;
                     o[0] = mu0; o[1] = mu1; o[2] = mu2; o[3] = mu3; o[4] = mu4;
-                    o[5] = S00; o[6] = S01; o[7] = S02; o[8] = S03; o[9] = S04;
-                    o[10] = S11; o[11] = S12; o[12] = S13; o[13] = S14;
-                    o[14] = S22; o[15] = S23; o[16] = S24;
-                    o[17] = S33; o[18] = S34; o[19] = S44;
-                    o[20] = s;
+                    o[5] = v_pre; o[6] = sn; o[7] = cs; o[8] = s;
                 }
                 __syncwarp();
                 if (lane == 0) mbar_arrive(st_full + (k & 1));
             }
         }
     } else {
-        // ======================= scoring warps (Eq. 11-16) ======================
-        // the cost of step k of the samples this rank scores, one step behind the
-        // producers; RC lanes per sample (2 with CS = 4, else 1, two passes of 64
-        // samples with CS = 1)
+        // ======================= scoring warps (Eq. 10-16) ======================
+        // One step behind the producers: the covariance recursion (Eq. 10) and
+        // the chance-constrained cost of the samples this rank scores, RC lanes
+        // per sample (2 with CS = 4, else 1; two passes of 64 samples with
+        // CS = 1).  Also the control noise of every sample, two steps ahead.
         const int nown = MT / CS;
         const int ct = tid - (NPROD + 32);
         const int RC = nown >= NCOST ? 1 : NCOST / nown;
         const int spp = NCOST / RC;                 // samples per pass
         const int cpart = ct % RC;
+        const uint32_t it0 = a.it0, it1 = a.it1;
+        // noise of step kk for the samples ct and ct + 64 of this cluster tile
+        auto noise = [&](int kk) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int mm = ct + h * NCOST;
+                const int sq = tile * MT + mm < a.K ? tile * MT + mm : 0;
+                nz[(kk & 1) * MT + mm] =
+                    control_eps((uint32_t)kk, (uint32_t)sq, it0, it1, a.key0, a.key1, a.sig_v, a.sig_w);
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(nz_full + (kk & 1));
+        };
+        noise(0);
+        if (a.T > 1) noise(1);
         float cost[2] = {0.0f, 0.0f};
+        float Sg[2][15];                            // covariance upper triangles (sidx order)
+#pragma unroll
+        for (int js = 0; js < 2; ++js)
+#pragma unroll
+            for (int i = 0; i < 15; ++i) Sg[js][i] = 0.0f;
         float disc = 1.0f;
         for (int k = 0; k < a.T; ++k) {
             wait_or_abort(st_full + (k & 1), (uint32_t)(k >> 1) & 1u, abort_flag, a.err);
             __syncwarp();
-            const float* sstk = sst + (k & 1) * nown * 24;
+            // the producers read the noise slot of step k before they handed step k
+            // over, so it is free for step k + 2
+            if (k + 2 < a.T) noise(k + 2);
+            const float* sstk = sst + (k & 1) * nown * SST;
 #pragma unroll
             for (int js = 0; js < 2; ++js) {
                 const int ci = ct / RC + js * spp;
@@ -633,9 +643,43 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_cl(const RolloutArgs a, 
                 const int mc = (int)rank + CS * ci;
                 const int sc_me = tile * MT + mc;
                 const bool cactive = sc_me < a.K;
-                const float* o = sstk + ci * 24;
+                const float* o = sstk + ci * SST;
                 const float px = o[0], py = o[1];
-                float sxx = o[5], sxy = o[6], syy = o[10];
+                // Eq. 10: Sigma' = A Sigma A^T + diag(0, 0, 0, s, s), A the Jacobian
+                // of the unicycle step at the pre-step state
+                {
+                    const float vp = o[5], sn = o[6], cs = o[7], sv = o[8];
+                    const float a02 = -a.dt * vp * sn, a03 = a.dt * cs;
+                    const float a12 = a.dt * vp * cs, a13 = a.dt * sn;
+                    float* S = Sg[js];
+                    const float S00 = S[0], S01 = S[1], S02 = S[2], S03 = S[3], S04 = S[4], S11 = S[5],
+                                S12 = S[6], S13 = S[7], S14 = S[8], S22 = S[9], S23 = S[10], S24 = S[11],
+                                S33 = S[12], S34 = S[13], S44 = S[14];
+                    const float B00 = S00 + a02 * S02 + a03 * S03, B01 = S01 + a02 * S12 + a03 * S13,
+                                B02 = S02 + a02 * S22 + a03 * S23, B03 = S03 + a02 * S23 + a03 * S33,
+                                B04 = S04 + a02 * S24 + a03 * S34;
+                    const float B11 = S11 + a12 * S12 + a13 * S13, B12 = S12 + a12 * S22 + a13 * S23,
+                                B13 = S13 + a12 * S23 + a13 * S33, B14 = S14 + a12 * S24 + a13 * S34;
+                    const float B22 = S22 + a.dt * S24, B23 = S23 + a.dt * S34, B24 = S24 + a.dt * S44;
+                    const float B33 = a.av * S33, B34 = a.av * S34;
+                    const float B44 = a.aw * S44;
+                    S[0] = B00 + a02 * B02 + a03 * B03;
+                    S[1] = B01 + a12 * B02 + a13 * B03;
+                    S[2] = B02 + a.dt * B04;
+                    S[3] = a.av * B03;
+                    S[4] = a.aw * B04;
+                    S[5] = B11 + a12 * B12 + a13 * B13;
+                    S[6] = B12 + a.dt * B14;
+                    S[7] = a.av * B13;
+                    S[8] = a.aw * B14;
+                    S[9] = B22 + a.dt * B24;
+                    S[10] = a.av * B23;
+                    S[11] = a.aw * B24;
+                    S[12] = a.av * B33 + sv;
+                    S[13] = a.aw * B34;
+                    S[14] = a.aw * B44 + sv;
+                }
+                float sxx = Sg[js][0], sxy = Sg[js][1], syy = Sg[js][5];
                 if (a.nom_sxy) {
                     sxx = __ldg(a.nom_sxy + 3 * k);
                     sxy = __ldg(a.nom_sxy + 3 * k + 1);
@@ -686,7 +730,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_cl(const RolloutArgs a, 
                     const float omargin = om, e2min = best;
                     const float e_lane = sqrtf(e2min);
                     const float rbar = a.r - a.sq_chi2 * sqrtf(lmax);
-                    const float sv = o[20], vv = o[3];
+                    const float sv = o[8], vv = o[3];
                     float stage = a.c_var * (sv + sv) + a.c_speed * (a.v_des - vv) * (a.v_des - vv);
                     if (omargin <= 0.0f) stage += a.c_coll;
                     const float lmargin = e_lane - rbar;
@@ -699,7 +743,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_cl(const RolloutArgs a, 
                         if (a.tr_mu)
                             for (int i = 0; i < 5; ++i) a.tr_mu[sk * 5 + i] = o[i];
                         if (a.tr_sig)
-                            for (int i = 0; i < 15; ++i) a.tr_sig[sk * 15 + i] = o[5 + i];
+                            for (int i = 0; i < 15; ++i) a.tr_sig[sk * 15 + i] = Sg[js][i];
                         if (a.tr_stage) a.tr_stage[sk] = stage;
                         if (a.tr_margin) {
                             a.tr_margin[sk * 2] = lmargin;
