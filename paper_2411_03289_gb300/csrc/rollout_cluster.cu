@@ -504,6 +504,17 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_cl(const RolloutArgs a, 
                 kernel_row(c, av);
                 mean_part(c, av);
             }
+            // ---------------- the part of the step that needs no GP result ---------
+            // (unicycle with velocity lag; the covariance recursion, which the mean
+            // never reads, runs in the scoring warps), while the MMAs finish
+            float sn, cs;
+            sincosf(mu2, &sn, &cs);
+            const float v_pre = mu3;
+            const float nX = mu0 + a.dt * mu3 * cs;
+            const float nY = mu1 + a.dt * mu3 * sn;
+            const float nT = mu2 + a.dt * mu4;
+            const float nV0 = mu3 + a.kv * (ut.x - mu3);
+            const float nW0 = mu4 + a.kw * (ut.y - mu4);
             if (k + 1 < a.T) ut_next = control(k + 1);
             // ---------------- this rank's partial |V_m|^2 -------------------------
             bool ok = wait_or_abort(pass_done, (uint32_t)k & 1u, abort_flag, a.err);
@@ -566,18 +577,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_cl(const RolloutArgs a, 
             const float mean_v = a.sf2 * msum.x, mean_w = a.sf2 * msum.y;
             const float s = fmaxf(0.0f, a.sf2 - q);
 
-            // ---------------- mean dynamics (all ranks, all samples) ---------------
-            // (the covariance recursion, which the mean never reads, runs in the
-            // scoring warps)
-            float sn, cs;
-            sincosf(mu2, &sn, &cs);
-            const float v_pre = mu3;
-            const float nX = mu0 + a.dt * mu3 * cs;
-            const float nY = mu1 + a.dt * mu3 * sn;
-            const float nT = mu2 + a.dt * mu4;
-            const float nV = mu3 + a.kv * (ut.x - mu3) + mean_v;
-            const float nW = mu4 + a.kw * (ut.y - mu4) + mean_w;
-            mu0 = nX; mu1 = nY; mu2 = nT; mu3 = nV; mu4 = nW;
+            // ---------------- mean dynamics: add the GP mean -----------------------
+            mu0 = nX; mu1 = nY; mu2 = nT; mu3 = nV0 + mean_v; mu4 = nW0 + mean_w;
             // ---------------- hand the step to the scoring warps -------------------
             // (rank r scores the samples m = r mod CS; the buffer of step k is
             // reused at step k + 2, once the scoring warps released it)
