@@ -260,8 +260,15 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_cl(const RolloutArgs a, 
     const int tile = blockIdx.x / CS;
     const int nboth = 4 * ((int)rank + 1);      // chunks needed by both of this rank's slices
     const int nch = 4 * (NS - (int)rank);       // chunks needed by its upper slice
-    const int mspan = (4 * NS) / CS;            // GP-mean chunks per rank
-    const int mc0 = (int)rank * mspan, mc1 = mc0 + mspan;
+    // GP-mean chunks [mc0, mc1) of this rank: rank 0 (the most kernel-row
+    // chunks) the last four, each further rank the eight below, the last rank
+    // all the rest; every range lies inside the rank's own kernel-row chunks
+    int mc1 = 4 * NS, mc0 = 4 * (NS - 1);
+    for (int r = 1; r <= (int)rank; ++r) {
+        mc1 = mc0;
+        mc0 = mc1 - 8;
+    }
+    if ((int)rank == CS - 1) mc0 = 0;
     const uint32_t bbytes = (uint32_t)cl.bytes[rank];
 
     if (tid == 0) {
@@ -420,9 +427,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_cl(const RolloutArgs a, 
 
             // ---------------- kernel-row tiles (8 points per thread per chunk) ----
             // BURST chunks per burst (32 independent exp2 in flight).  The GP mean
-            // is split between the ranks: rank r sums chunks [mc0, mc1), the
-            // part of them beyond its own tiles (the highest rank) computed
-            // for the mean alone.
+            // is split between the ranks: rank r sums chunks [mc0, mc1).
             float mv = 0.0f, mw = 0.0f, cv = 0.0f, cw = 0.0f;
             const uint64_t zz0 = f2pack(z0, z0), zz1 = f2pack(z1, z1);
             const uint64_t zz2 = f2pack(z2, z2), zz3 = f2pack(z3, z3);
