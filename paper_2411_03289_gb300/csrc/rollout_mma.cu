@@ -119,6 +119,14 @@ __device__ __forceinline__ void producers_sync() {
     asm volatile("bar.sync 1, 256;" ::: "memory");
 }
 
+// 2^x (the hardware approximation; results below the normal range flush to 0,
+// far below what a 16-bit split operand can carry)
+__device__ __forceinline__ float ex2_ftz(float x) {
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_addr(bar)) : "memory");
 }
@@ -191,8 +199,11 @@ __device__ __forceinline__ void rollout_mma_body(const RolloutArgs& a, const Mma
 
     if (warp >= NPROD / 32) {
         // ======================= control warps ===============================
-        if (lane != 0 || NB == 0) return;       // one thread per role
+        if (NB == 0) return;
         const bool issuer = (warp == NPROD / 32);
+        // one loader thread; the issuer is a converged warp whose elected lane
+        // issues the MMAs (its operand arithmetic stays warp-uniform)
+        if (!issuer && lane != 0) return;
         const uint32_t idesc = tc::idesc_f16(FMT, MT, BLK);
         // base descriptors of stage 0's A tile (128 rows) and B pieces (128 rows);
         // stage and block offsets are multiples of 16 bytes inside shared memory
@@ -206,6 +217,7 @@ __device__ __forceinline__ void rollout_mma_body(const RolloutArgs& a, const Mma
                 const int nchunk = 8 * b1;               // block b needs chunks 0 .. 8b+7
                 if (issuer && pc > 0) {
                     wait_or_abort(tmem_free, (pc - 1) & 1u, abort_flag, a.err);
+                    __syncwarp();
                     tc::fence_after_sync();
                 }
                 for (int c = 0; c < nchunk; ++c, ++n) {
@@ -228,8 +240,9 @@ __device__ __forceinline__ void rollout_mma_body(const RolloutArgs& a, const Mma
                         bulk_copy(dst, mm.Bhi + off, bytes, b_full + st);
                         bulk_copy(dst + BLOCKS_PER_PASS * B_PART, mm.Blo + off, bytes, b_full + st);
                     } else {
-                        if (!wait_or_abort(a_full + st, use & 1u, abort_flag, a.err)) continue;
-                        if (!wait_or_abort(b_full + st, use & 1u, abort_flag, a.err)) continue;
+                        bool ok = wait_or_abort(a_full + st, use & 1u, abort_flag, a.err);
+                        ok = ok && wait_or_abort(b_full + st, use & 1u, abort_flag, a.err);
+                        if (!__all_sync(0xffffffffu, ok)) continue;
                         tc::fence_after_sync();
                         // descriptors by adds on precomputed bases: rebuilding them per
                         // MMA makes the single issuing thread the bottleneck
@@ -241,12 +254,10 @@ __device__ __forceinline__ void rollout_mma_body(const RolloutArgs& a, const Mma
                             const uint64_t dBh = dB0 + (uint64_t)((st * STAGE + 2 * A_PART + (b - b0) * B_PART) >> 4);
                             const uint64_t dBl = dBh + (uint64_t)((BLOCKS_PER_PASS * B_PART) >> 4);
                             const uint32_t d = taddr + (uint32_t)((b - b0) * BLK);
-                            tc::mma_f16(d, dAh, dBh, idesc, c > 0 ? 1u : 0u);
-                            tc::mma_f16(d, dAh, dBl, idesc, 1u);
-                            tc::mma_f16(d, dAl, dBh, idesc, 1u);
+                            tc::mma3_split_elect(d, dAh, dAl, dBh, dBl, idesc, c > 0 ? 1u : 0u);
                         }
-                        tc::mma_commit(empty + st);
-                        if (c == nchunk - 1) tc::mma_commit(pass_done);
+                        tc::mma_commit_elect(empty + st);
+                        if (c == nchunk - 1) tc::mma_commit_elect(pass_done);
                     }
                 }
             }
@@ -312,7 +323,7 @@ __device__ __forceinline__ void rollout_mma_body(const RolloutArgs& a, const Mma
                 for (int e = 0; e < KPT; ++e) {
                     const float4 x = xs_s[jb + e];
                     const float d0 = z0 - x.x, d1 = z1 - x.y, d2 = z2 - x.z, d3 = z3 - x.w;
-                    av[e] = exp2f(-(d0 * d0 + d1 * d1 + d2 * d2 + d3 * d3));
+                    av[e] = ex2_ftz(-(d0 * d0 + d1 * d1 + d2 * d2 + d3 * d3));
                 }
                 if (last_pass) {
 #pragma unroll

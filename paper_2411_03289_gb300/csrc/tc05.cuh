@@ -66,6 +66,24 @@ __device__ __forceinline__ void mma_f16_ta(uint32_t d_tmem, uint32_t a_tmem, uin
         : "memory");
 }
 
+// The three products of one 16-point chunk and one output block of the split
+// contraction, A and B in shared memory: A_hi B_hi (accumulating only if
+// acc0 != 0), A_hi B_lo, A_lo B_hi, all into d_tmem.  Warp-collective: one
+// elect.sync picks the lane that issues them.
+__device__ __forceinline__ void mma3_split_elect(uint32_t d_tmem, uint64_t a_hi, uint64_t a_lo, uint64_t b_hi,
+                                                 uint64_t b_lo, uint32_t idesc, uint32_t acc0) {
+    asm volatile(
+        "{\n\t.reg .pred e, p0, p1;\n\t"
+        "elect.sync _|e, 0xffffffff;\n\t"
+        "setp.ne.b32 p0, %6, 0;\n\t"
+        "setp.ne.b32 p1, 1, 0;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %3, %5, p0;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %4, %5, p1;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %2, %3, %5, p1;\n\t}" ::"r"(d_tmem),
+        "l"(a_hi), "l"(a_lo), "l"(b_hi), "l"(b_lo), "r"(idesc), "r"(acc0)
+        : "memory");
+}
+
 // Warp-collective commit: the whole (converged) warp executes it and one lane,
 // chosen by elect.sync, issues it.
 __device__ __forceinline__ void mma_commit_elect(uint64_t* bar) {
