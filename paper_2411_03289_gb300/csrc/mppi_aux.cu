@@ -4,8 +4,8 @@
 // Update (Alg. 1, "weights" and "weighted sum"): every CTA reduces the K
 // costs to rho = min S and Z = sum_s exp(-(S_s - rho)/lambda) in one fixed
 // order (so all CTAs agree bit for bit), writes w_s for its own samples, and
-// reduces sum_s w_s (u~_s,k - U_k) over them for every step k with warp
-// shuffles.  The per-CTA partials go to a scratch array; the CTA that
+// reduces sum_s w_s (u~_s,k - U_k) over them for every step k (one warp per
+// step, coalesced reads of u~, warp shuffles).  The per-CTA partials go to a scratch array; the CTA that
 // finishes last (atomic ticket) sums them in CTA order and writes U_new.
 #include <cfloat>
 
@@ -29,18 +29,34 @@ __device__ __forceinline__ float warp_min(float v) {
     return v;
 }
 
+// loads of the K costs in groups of eight per thread, all in flight together
+template <typename F>
+__device__ __forceinline__ void for_costs(const float* __restrict__ costs, int K, F&& f) {
+    const int tid = threadIdx.x;
+    for (int s0 = tid; s0 < K; s0 += 8 * UPD_THREADS) {
+        float c[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int s = s0 + j * UPD_THREADS;
+            c[j] = s < K ? __ldg(costs + s) : FLT_MAX;
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            if (s0 + j * UPD_THREADS < K) f(c[j]);
+    }
+}
+
 __device__ __forceinline__ void update_body(const UpdateArgs& a, int cta, int n_cta,
-                                            unsigned long long* it_dev, unsigned char* smem_raw) {
-    float2* wpart = reinterpret_cast<float2*>(smem_raw);   // UPD_WARPS x T
+                                            unsigned long long* it_dev) {
     __shared__ float red[UPD_WARPS];
     __shared__ float bcast[2];
+    __shared__ float wsh[UPD_THREADS];
     __shared__ unsigned int is_last;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int K = a.K, T = a.T;
-
     // rho = min_s S_s
     float mn = FLT_MAX;
-    for (int s = tid; s < K; s += UPD_THREADS) mn = fminf(mn, __ldg(a.costs + s));
+    for_costs(a.costs, K, [&](float c) { mn = fminf(mn, c); });
     mn = warp_min(mn);
     if (lane == 0) red[warp] = mn;
     __syncthreads();
@@ -53,7 +69,7 @@ __device__ __forceinline__ void update_body(const UpdateArgs& a, int cta, int n_
     const float rho = bcast[0];
     // Z = sum_s exp(-(S_s - rho)/lambda), fixed summation order
     float z = 0.0f;
-    for (int s = tid; s < K; s += UPD_THREADS) z += expf((rho - __ldg(a.costs + s)) * a.inv_lambda);
+    for_costs(a.costs, K, [&](float c) { z += expf((rho - c) * a.inv_lambda); });
     z = warp_sum(z);
     if (lane == 0) red[warp] = z;
     __syncthreads();
@@ -64,33 +80,34 @@ __device__ __forceinline__ void update_body(const UpdateArgs& a, int cta, int n_
     }
     __syncthreads();
     const float inv_z = 1.0f / bcast[1];
-
-    // own samples
-    const int s = cta * a.per_cta + tid;
+    // own samples' weights
+    const int s_base = cta * a.per_cta;
+    const int s = s_base + tid;
     const bool act = (tid < a.per_cta) && (s < K);
     const float w = act ? expf((rho - __ldg(a.costs + s)) * a.inv_lambda) * inv_z : 0.0f;
     if (act && a.weights) a.weights[s] = w;
-    for (int k = 0; k < T; ++k) {
+    wsh[tid] = w;
+    __syncthreads();
+    // sum_s w_s (u~_s,k - U_k) over the CTA's samples: warp w takes the steps
+    // k = w, w + 8, ..., lane l the samples l, l + 32, ... (coalesced reads of
+    // u~, all of a lane's loads in flight together)
+    const int ns = min(a.per_cta, K - s_base);
+    for (int k = warp; k < T; k += UPD_WARPS) {
+        const float uv = __ldg(a.U + 2 * k), uw = __ldg(a.U + 2 * k + 1);
+        const float2* ut = a.u_tilde + (size_t)k * K + s_base;
         float dv = 0.0f, dw = 0.0f;
-        if (act) {
-            const float2 u = __ldg(a.u_tilde + (size_t)k * K + s);
-            dv = w * (u.x - __ldg(a.U + 2 * k));
-            dw = w * (u.y - __ldg(a.U + 2 * k + 1));
+#pragma unroll 8
+        for (int i = lane; i < ns; i += 32) {
+            const float2 u = __ldg(ut + i);
+            dv = fmaf(wsh[i], u.x - uv, dv);
+            dw = fmaf(wsh[i], u.y - uw, dw);
         }
         dv = warp_sum(dv);
         dw = warp_sum(dw);
-        if (lane == 0) wpart[warp * T + k] = make_float2(dv, dw);
-    }
-    __syncthreads();
-    for (int k = tid; k < T; k += UPD_THREADS) {
-        float sv = 0.0f, sw = 0.0f;
-        for (int ww = 0; ww < UPD_WARPS; ++ww) {
-            const float2 p = wpart[ww * T + k];
-            sv += p.x;
-            sw += p.y;
+        if (lane == 0) {
+            a.partial[((size_t)cta * T + k) * 2] = dv;
+            a.partial[((size_t)cta * T + k) * 2 + 1] = dw;
         }
-        a.partial[((size_t)cta * T + k) * 2] = sv;
-        a.partial[((size_t)cta * T + k) * 2 + 1] = sw;
     }
     // last CTA combines the partials in CTA order
     __threadfence();
@@ -111,8 +128,7 @@ __device__ __forceinline__ void update_body(const UpdateArgs& a, int cta, int n_
 }
 
 __global__ void __launch_bounds__(UPD_THREADS) k_update(const UpdateArgs a) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    update_body(a, blockIdx.x, gridDim.x, nullptr, smem_raw);
+    update_body(a, blockIdx.x, gridDim.x, nullptr);
 }
 
 // Many controllers: CTA i serves CTA items[i].y of controller items[i].x,
@@ -121,9 +137,8 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update(const UpdateArgs a) {
 __global__ void __launch_bounds__(UPD_THREADS)
     k_update_batched(const UpdateArgs* __restrict__ args, const int2* __restrict__ items,
                      const int* __restrict__ ncta, unsigned long long* __restrict__ iters) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     const int2 it = items[blockIdx.x];
-    update_body(args[it.x], it.y, ncta[it.x], iters + it.x, smem_raw);
+    update_body(args[it.x], it.y, ncta[it.x], iters + it.x);
 }
 
 __global__ void k_philox(uint32_t key0, uint32_t key1, const uint4* __restrict__ ctr, int M,
@@ -236,9 +251,7 @@ __global__ void __launch_bounds__(NOM_THREADS) k_nominal(const RolloutArgs a, co
 }  // namespace
 
 int launch_update(const UpdateArgs& a, int n_cta, cudaStream_t st) {
-    const int smem = UPD_WARPS * a.T * (int)sizeof(float2);
-    GPM_CUDA(cudaFuncSetAttribute(k_update, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    k_update<<<n_cta, UPD_THREADS, smem, st>>>(a);
+    k_update<<<n_cta, UPD_THREADS, 0, st>>>(a);
     GPM_CUDA(cudaGetLastError());
     return GPMPPI_OK;
 }
@@ -246,9 +259,8 @@ int launch_update(const UpdateArgs& a, int n_cta, cudaStream_t st) {
 int launch_update_batched(const UpdateArgs* args, const int2* items, const int* ncta,
                           unsigned long long* iters, int nitems, int maxT, cudaStream_t st) {
     if (nitems == 0) return GPMPPI_OK;
-    const int smem = UPD_WARPS * maxT * (int)sizeof(float2);
-    GPM_CUDA(cudaFuncSetAttribute(k_update_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    k_update_batched<<<nitems, UPD_THREADS, smem, st>>>(args, items, ncta, iters);
+    (void)maxT;
+    k_update_batched<<<nitems, UPD_THREADS, 0, st>>>(args, items, ncta, iters);
     GPM_CUDA(cudaGetLastError());
     return GPMPPI_OK;
 }
