@@ -58,10 +58,17 @@ constexpr int B_MAX = 144 * 1024;     // largest resident share (NS = 8)
 constexpr uint64_t kWaitNs = 2000000000ull;
 // hand-off record of one scored sample and step: post-step mean (5), pre-step
 // speed, sin and cos of the pre-step heading, GP variance s
-constexpr int SST = 12;
+constexpr int SST = 9;
+// With four ranks the last rank computes the kernel rows of rank 0's last four
+// chunks and copies them into rank 0's shared memory (hi and lo, 128 rows x 16
+// points each, in the slab-major operand layout): rank 0, the rank every step
+// waits for, computes 28 chunks instead of 32.
+constexpr int AR_CHUNKS = 4;
+constexpr int AR_CHUNK_BYTES = 2 * MT * 16 * 2;     // 8 KiB: hi 4 KiB, then lo
+constexpr int AR_BYTES = AR_CHUNKS * AR_CHUNK_BYTES;
 
 struct ClLayout {
-    int b, bars, tslot, abort_flag, xx, sst, nz, xs, al, seg, il2, obs, total;
+    int b, bars, tslot, abort_flag, xq, xm, ar, sst, nz, xs, al, seg, il2, obs, total;
 };
 
 // shared-memory layout; the resident B share is sized for the largest rank;
@@ -71,14 +78,18 @@ __host__ __device__ inline ClLayout cl_layout(int npc, int S, int O) {
     const int nown = MT / (npc / 128);
     ClLayout L;
     L.b = 0;
-    // a_full, empty [NSTAGE], b_res, pass_done, tmem_free, xbar[2], st_full[2], st_empty[2], nz_full[2]
+    // a_full, empty [NSTAGE], b_res, pass_done, tmem_free, xbar[2], st_full[2], st_empty[2],
+    // nz_full[2], ar_full
     L.bars = B_MAX;
-    L.tslot = L.bars + 8 * (2 * NSTAGE + 11);
+    L.tslot = L.bars + 8 * (2 * NSTAGE + 12);
     L.abort_flag = L.tslot + 4;
-    // exchange buffers [2 (step parity)][8 (rank, thread half)][MT] float4:
-    // (partial |V|^2, GP mean partial v, w, 0) of every producer thread
-    L.xx = ((L.abort_flag + 4 + 15) / 16) * 16;
-    L.sst = L.xx + 2 * 8 * MT * 16;              // [2][nown][SST] floats: per-step hand-off to the scoring warps
+    // exchange buffers [2 (step parity)][8 (rank, thread half)][MT]: partial
+    // |V|^2 (float) and GP mean partial (v, w) of every producer thread
+    L.xq = ((L.abort_flag + 4 + 15) / 16) * 16;
+    L.xm = L.xq + 2 * 8 * MT * 4;
+    // kernel rows received by rank 0 (staged by the last rank) with four ranks
+    L.ar = ((L.xm + 2 * 8 * MT * 8 + 127) / 128) * 128;
+    L.sst = L.ar + (npc == 512 ? AR_BYTES : 0);  // [2][nown][SST] floats: per-step hand-off to the scoring warps
     L.nz = L.sst + 2 * nown * SST * 4;           // [2][MT] float2: control noise, computed two steps ahead
     L.xs = ((L.nz + 2 * MT * 8 + 127) / 128) * 128;
     L.al = L.xs + npc * 16;
@@ -199,6 +210,11 @@ __device__ __forceinline__ bool wait_cluster(uint64_t* bar, uint32_t parity, vol
     return true;
 }
 
+// named barrier over the 128 producer threads of one thread half (u = 0, 1)
+__device__ __forceinline__ void half_sync(int u) {
+    asm volatile("bar.sync %0, 128;" ::"r"(1 + u) : "memory");
+}
+
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_addr(bar)) : "memory");
 }
@@ -216,13 +232,25 @@ __device__ __forceinline__ uint32_t peer_addr(const void* p, uint32_t peer) {
     return r;
 }
 
-// asynchronous 16-byte store into a cluster CTA's shared memory that completes
-// 16 transaction bytes on the mbarrier at bar (same CTA as addr)
-__device__ __forceinline__ void st_async_f32x4(uint32_t addr, float4 v, uint32_t bar) {
-    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.f32 [%0], {%1, %2, %3, %4}, [%5];" ::"r"(
-                     addr),
-                 "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "r"(bar)
+// asynchronous stores into a cluster CTA's shared memory that complete their
+// transaction bytes (4 or 8) on the mbarrier at bar (same CTA as addr)
+__device__ __forceinline__ void st_async_f32(uint32_t addr, float v, uint32_t bar) {
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b32 [%0], %1, [%2];" ::"r"(addr),
+                 "r"(__float_as_uint(v)), "r"(bar)
                  : "memory");
+}
+__device__ __forceinline__ void st_async_f32x2(uint32_t addr, float2 v, uint32_t bar) {
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f32 [%0], {%1, %2}, [%3];" ::"r"(addr),
+                 "f"(v.x), "f"(v.y), "r"(bar)
+                 : "memory");
+}
+// bulk copy from this CTA's shared memory into a cluster CTA's shared memory,
+// completing its bytes on the mbarrier at bar (same CTA as dst)
+__device__ __forceinline__ void bulk_copy_peer(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+        "r"(tc::smem_addr(src)), "r"(bytes), "r"(bar)
+        : "memory");
 }
 
 __device__ __forceinline__ void cluster_sync_all() {
@@ -243,9 +271,12 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_cl(const RolloutArgs a, 
     uint64_t* st_full = xbar + 2;               // [2] post-step states handed to the scoring warps
     uint64_t* st_empty = st_full + 2;           // [2] ... and released by them
     uint64_t* nz_full = st_empty + 2;           // [2] noise of a step, written by the scoring warps
+    uint64_t* ar_full = nz_full + 2;            // rank 0: the kernel rows copied in by the last rank
     uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + L.tslot);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + L.abort_flag);
-    float4* xx = reinterpret_cast<float4*>(sm + L.xx);
+    float* xq = reinterpret_cast<float*>(sm + L.xq);
+    float2* xm = reinterpret_cast<float2*>(sm + L.xm);
+    unsigned char* ar = sm + L.ar;
     float* sst = reinterpret_cast<float*>(sm + L.sst);
     float2* nz = reinterpret_cast<float2*>(sm + L.nz);
     float4* xs_s = reinterpret_cast<float4*>(sm + L.xs);
@@ -269,6 +300,24 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_cl(const RolloutArgs a, 
         mc0 = mc1 - 8;
     }
     if ((int)rank == CS - 1) mc0 = 0;
+    // With four ranks: rank 0 computes no GP-mean terms and not the kernel rows
+    // of its last four chunks; the last rank computes those rows (chunks
+    // [me0, me1), with their GP-mean terms) first in every step and copies them
+    // into rank 0's shared memory; rank 1 sums chunks 24-27, rank 2 12-23, the
+    // last rank 0-11.
+    const bool rows_out = CS == 4 && (int)rank == CS - 1;
+    const bool rows_in = CS == 4 && rank == 0;
+    int me0 = 0, me1 = 0;
+    if (CS == 4) {
+        const int lo[4] = {0, 24, 12, 0}, hi[4] = {0, 28, 24, 12};
+        mc0 = lo[rank];
+        mc1 = hi[rank];
+        if (rows_out) {
+            me0 = 4 * NS - AR_CHUNKS;
+            me1 = 4 * NS;
+        }
+    }
+    const int nch_p = rows_in ? nch - AR_CHUNKS : nch;   // chunks whose rows the producers write to TMEM
     const uint32_t bbytes = (uint32_t)cl.bytes[rank];
 
     if (tid == 0) {
@@ -288,6 +337,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_cl(const RolloutArgs a, 
             tc::mbar_init(st_empty + i, NCOST / 32);
             tc::mbar_init(nz_full + i, NCOST / 32);
         }
+        tc::mbar_init(ar_full, 1);
         *abort_flag = 0;
         tc::fence_mbar_init();
     }
@@ -347,10 +397,17 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_cl(const RolloutArgs a, 
         // bytes inside shared memory, so they add to the start-address field
         const uint64_t dB256 = tc::smem_desc(tc::smem_addr(bres), 256 * 16, 128);
         const uint64_t dB128 = tc::smem_desc(tc::smem_addr(bres), 128 * 16, 128);
+        // the received kernel rows (rank 0 with four ranks): A tiles of 128 rows
+        // in shared memory, chunk positions 0, 2, 1, 3 for chunks me + 0 .. 3
+        const uint64_t dAr = tc::smem_desc(tc::smem_addr(ar), MT * 16, 128);
         bool ok = __all_sync(0xffffffffu, wait_or_abort(b_res, 0, abort_flag, a.err));
         tc::fence_after_sync();
         uint32_t n = 0;
         for (int k = 0; k < a.T && ok; ++k) {
+            if (rows_in) {
+                if (lane == 0) tc::mbar_expect_tx(ar_full, (uint32_t)AR_BYTES);
+                __syncwarp();
+            }
             if (k > 0) {
                 if (!__all_sync(0xffffffffu, wait_or_abort(tmem_free, (uint32_t)(k - 1) & 1u, abort_flag, a.err))) {
                     ok = false;
@@ -358,7 +415,22 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_cl(const RolloutArgs a, 
                 }
                 tc::fence_after_sync();
             }
-            for (int c = 0; c < nch; c += GCH, ++n) {
+            for (int c = 0; c < nch; c += GCH) {
+                if (c >= nch_p) {
+                    // the last stage from the rows the last rank copied in (upper
+                    // slice alone: rank 0's last chunks are above nboth)
+                    if (!__all_sync(0xffffffffu, wait_or_abort(ar_full, (uint32_t)k & 1u, abort_flag, a.err))) {
+                        ok = false;
+                        break;
+                    }
+                    tc::fence_after_sync();
+                    const uint64_t b0 = dB128 + (uint64_t)((nboth * 8192 + (c - nboth) * 4096) >> 4);
+                    tc::mma_stage4_sa_elect(taddr + 64u, dAr, dAr + (uint64_t)((2 * AR_CHUNK_BYTES) >> 4),
+                                            dAr + (uint64_t)(AR_CHUNK_BYTES >> 4),
+                                            dAr + (uint64_t)((3 * AR_CHUNK_BYTES) >> 4),
+                                            (uint64_t)((AR_CHUNK_BYTES / 2) >> 4), b0, 4096 >> 4, idesc128, idesc64);
+                    continue;
+                }
                 const int st = (int)(n % NSTAGE);
                 const uint32_t use = n / NSTAGE;
                 if (!__all_sync(0xffffffffu, wait_or_abort(a_full + st, use & 1u, abort_flag, a.err))) {
@@ -379,6 +451,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_cl(const RolloutArgs a, 
                     const uint64_t b0 = dB128 + (uint64_t)((nboth * 8192 + (c - nboth) * 4096) >> 4);
                     tc::mma_stage4_elect(taddr + 64u, aS, b0, 4096 >> 4, empty + st, 1u, idesc128, idesc64);
                 }
+                ++n;
             }
             if (!ok) break;
             tc::mma_commit_elect(pass_done);
@@ -465,7 +538,32 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_cl(const RolloutArgs a, 
                 kahan_add(mv, cv, pv0 + pv1);
                 kahan_add(mw, cw, pw0 + pw1);
             };
-            for (int c = 0; c < nch; c += BURST) {      // nch is a multiple of 4 (and of BURST)
+            if (rows_out) {
+                // rank 0's last four chunks: rows (and their GP-mean terms) into this
+                // CTA's staging area, then one bulk copy per thread half into rank
+                // 0's shared memory (chunk positions 0, 1 for u = 0, 2, 3 for u = 1)
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    const int cc = me0 + 2 * j + u;
+                    uint64_t av[8];
+                    kernel_row(cc, av);
+                    mean_part(cc, av);
+                    uint32_t h[8], l[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) split2<FMT>(av[q], &h[q], &l[q]);
+                    unsigned char* pc = ar + (2 * u + j) * AR_CHUNK_BYTES + m * 16;
+                    *reinterpret_cast<uint4*>(pc) = make_uint4(h[0], h[1], h[2], h[3]);
+                    *reinterpret_cast<uint4*>(pc + MT * 16) = make_uint4(h[4], h[5], h[6], h[7]);
+                    *reinterpret_cast<uint4*>(pc + AR_CHUNK_BYTES / 2) = make_uint4(l[0], l[1], l[2], l[3]);
+                    *reinterpret_cast<uint4*>(pc + AR_CHUNK_BYTES / 2 + MT * 16) = make_uint4(l[4], l[5], l[6], l[7]);
+                }
+                tc::fence_proxy_async();               // generic writes before the bulk copy reads them
+                half_sync(u);
+                if (m == 0)
+                    bulk_copy_peer(peer_addr(ar + 2 * u * AR_CHUNK_BYTES, 0u), ar + 2 * u * AR_CHUNK_BYTES,
+                                   2u * AR_CHUNK_BYTES, peer_addr(ar_full, 0u));
+            }
+            for (int c = 0; c < nch_p; c += BURST) {    // nch_p is a multiple of 4 (and of BURST)
                 // the sample's two threads take alternate chunks of the burst:
                 // thread half u the chunks c + u and c + 2 + u, all 16 points each
                 uint64_t av[2][8];
@@ -557,26 +655,33 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_cl(const RolloutArgs a, 
             // included, as asynchronous stores that complete transaction bytes on
             // the receiver's exchange barrier; no CTA barrier is needed
             const int buf = k & 1;
-            if (tid == 0) tc::mbar_expect_tx(xbar + buf, (uint32_t)(CS * 2 * MT * 16));
+            if (tid == 0) tc::mbar_expect_tx(xbar + buf, (uint32_t)(CS * 2 * MT * 12));
             {
-                const float4 mine = make_float4(qpart, mv + cv, mw + cw, 0.0f);
-                const float4* slot = xx + (buf * 8 + 2 * (int)rank + u) * MT + m;
-                for (int p = 0; p < CS; ++p)
-                    st_async_f32x4(peer_addr(slot, (uint32_t)p), mine, peer_addr(xbar + buf, (uint32_t)p));
+                const int slot = (buf * 8 + 2 * (int)rank + u) * MT + m;
+                const float2 mm = make_float2(mv + cv, mw + cw);
+                for (int p = 0; p < CS; ++p) {
+                    const uint32_t xb = peer_addr(xbar + buf, (uint32_t)p);
+                    st_async_f32(peer_addr(xq + slot, (uint32_t)p), qpart, xb);
+                    st_async_f32x2(peer_addr(xm + slot, (uint32_t)p), mm, xb);
+                }
             }
             wait_cluster(xbar + buf, (uint32_t)(k >> 1) & 1u, abort_flag, a.err);
             float qsum = 0.0f;
             float2 msum = make_float2(0.0f, 0.0f);
-            float4 part[8];
+            float pq[8];
+            float2 pm[8];
 #pragma unroll
             for (int p = 0; p < 8; ++p)
-                if (p < 2 * CS) part[p] = xx[(buf * 8 + p) * MT + m];
+                if (p < 2 * CS) {
+                    pq[p] = xq[(buf * 8 + p) * MT + m];
+                    pm[p] = xm[(buf * 8 + p) * MT + m];
+                }
 #pragma unroll
             for (int p = 0; p < 8; ++p)              // fixed order: identical on every rank
                 if (p < 2 * CS) {
-                    qsum += part[p].x;
-                    msum.x += part[p].y;
-                    msum.y += part[p].z;
+                    qsum += pq[p];
+                    msum.x += pm[p].x;
+                    msum.y += pm[p].y;
                 }
             const float q = qsum * cl.qscale;
             const float mean_v = a.sf2 * msum.x, mean_w = a.sf2 * msum.y;

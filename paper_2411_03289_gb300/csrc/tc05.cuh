@@ -129,6 +129,30 @@ __device__ __forceinline__ void mma_stage4_elect(uint32_t d_tmem, uint32_t a, ui
         : "memory");
 }
 
+// The same four chunks with A in shared memory: A_hi,j at descriptor a_j,
+// A_lo,j at a_j + lo_off; every product accumulates; no commit.
+__device__ __forceinline__ void mma_stage4_sa_elect(uint32_t d_tmem, uint64_t a0, uint64_t a1, uint64_t a2,
+                                                    uint64_t a3, uint64_t lo_off, uint64_t b0, uint64_t bstep,
+                                                    uint32_t i_hi, uint32_t i_lo) {
+    asm volatile(
+        "{\n\t.reg .pred e, p1;\n\t"
+        ".reg .b64 l0, l1, l2, l3, b1, b2, b3;\n\t"
+        "add.u64 l0, %1, %5;\n\tadd.u64 l1, %2, %5;\n\tadd.u64 l2, %3, %5;\n\tadd.u64 l3, %4, %5;\n\t"
+        "add.u64 b1, %6, %7;\n\tadd.u64 b2, b1, %7;\n\tadd.u64 b3, b2, %7;\n\t"
+        "elect.sync _|e, 0xffffffff;\n\t"
+        "setp.ne.b32 p1, 1, 0;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %6, %8, p1;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], l0, %6, %9, p1;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %2, b1, %8, p1;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], l1, b1, %9, p1;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %3, b2, %8, p1;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], l2, b2, %9, p1;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %4, b3, %8, p1;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], l3, b3, %9, p1;\n\t}" ::"r"(d_tmem),
+        "l"(a0), "l"(a1), "l"(a2), "l"(a3), "l"(lo_off), "l"(b0), "l"(bstep), "r"(i_hi), "r"(i_lo)
+        : "memory");
+}
+
 // Four consecutive 32-bit columns of this thread's TMEM lane (warp-collective;
 // warp w writes lanes 32 (w % 4) .. 32 (w % 4) + 31, encoded in taddr).
 __device__ __forceinline__ void tmem_st4(uint32_t taddr, uint32_t r0, uint32_t r1, uint32_t r2, uint32_t r3) {

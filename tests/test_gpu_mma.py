@@ -182,6 +182,24 @@ def test_cluster_kernel_parity_and_streaming_agreement(lib, N, precision, monkey
     assert np.max(np.abs(U2 - U_new)) <= TOL_U
 
 
+@pytest.mark.parametrize("K,T", [(1, 1), (129, 2), (130, 3), (257, 5)])
+def test_cluster_kernel_edges(lib, K, T):
+    """Four-CTA clusters (N = 500) at the edges of the step pipeline: one step
+    (no noise computed ahead, no record handed over while another is pending),
+    two and three steps (the two-slot rings wrap), one sample (127 idle rows of
+    the MMA tile) and a second sample tile with one or two live samples."""
+    sc = _sc("small", 2, K=K, N=500, T=T)
+    g, ctrl = make_ctrl(lib, sc)
+    assert lib.mppi_rollout_kind(ctrl) == lib.GPMPPI_KERNEL_TC_CLUSTER
+    fits = O.gp_fit(sc.X, sc.Y, sc.hyper)
+    U = sc.U0.copy()
+    ro = O.rollout(sc, fits, sc.x0, U, 5)
+    tr = gpu_trace(lib, ctrl, sc, sc.x0, U, it=5)
+    check_trace(sc, ro, tr)
+    U_new, w, c = gpu_step(lib, ctrl, sc, sc.x0, U, it=5)
+    check_step(sc, ro, U, U_new, w, c)
+
+
 def test_cluster_kernel_scene_in_global_memory(lib):
     """A scene too large to stage next to the resident factor share is read
     from global memory by the cluster kernel: same parity."""
