@@ -415,7 +415,11 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_cl(const RolloutArgs a, 
                 }
                 tc::fence_after_sync();
             }
-            for (int c = 0; c < nch; c += GCH) {
+            // stage order: the first (which initialises the accumulators), then
+            // the stage of received rows (they arrive early: the last rank computes
+            // them first), then the rest
+            for (int si = 0; si < nch / GCH; ++si) {
+                const int c = !rows_in ? GCH * si : (si == 0 ? 0 : (si == 1 ? nch_p : GCH * (si - 1)));
                 if (c >= nch_p) {
                     // the last stage from the rows the last rank copied in (upper
                     // slice alone: rank 0's last chunks are above nboth)
@@ -473,6 +477,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_cl(const RolloutArgs a, 
         const uint32_t a_lane = taddr + ((uint32_t)(32 * (warp & 3)) << 16) + A_COL;
         const int s_me = tile * MT + m;
         const bool active = s_me < a.K;
+        const int s_q = active ? s_me : 0;
         const int nown = MT / CS;              // samples scored by this rank
 
         float mu0 = a.x0[0], mu1 = a.x0[1], mu2 = a.x0[2], mu3 = a.x0[3], mu4 = a.x0[4];
@@ -482,8 +487,14 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_cl(const RolloutArgs a, 
         // ahead, and the control of step k + 1 is prepared while the MMAs of step
         // k complete
         auto control = [&](int kk) {
-            wait_or_abort(nz_full + (kk & 1), (uint32_t)(kk >> 1) & 1u, abort_flag, a.err);
-            const float2 e = nz[(kk & 1) * MT + m];
+            float2 e;
+            if (kk == 0) {
+                e = control_eps(0u, (uint32_t)s_q, a.it0, a.it1, a.key0, a.key1, a.sig_v, a.sig_w);
+            } else {
+                // step kk >= 1 in slot (kk - 1) & 1, its use (kk - 1) >> 1
+                wait_or_abort(nz_full + ((kk - 1) & 1), (uint32_t)((kk - 1) >> 1) & 1u, abort_flag, a.err);
+                e = nz[((kk - 1) & 1) * MT + m];
+            }
             float2 uk;
             uk.x = fminf(fmaxf(__ldg(a.U + 2 * kk) + e.x, a.umin0), a.umax0);
             uk.y = fminf(fmaxf(__ldg(a.U + 2 * kk + 1) + e.y, a.umin1), a.umax1);
@@ -719,19 +730,19 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_cl(const RolloutArgs a, 
         const int spp = NCOST / RC;                 // samples per pass
         const int cpart = ct % RC;
         const uint32_t it0 = a.it0, it1 = a.it1;
-        // noise of step kk for the samples ct and ct + 64 of this cluster tile
+        // noise of step kk >= 1 (slot (kk - 1) & 1) for the samples ct and ct + 64
         auto noise = [&](int kk) {
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int mm = ct + h * NCOST;
                 const int sq = tile * MT + mm < a.K ? tile * MT + mm : 0;
-                nz[(kk & 1) * MT + mm] =
+                nz[((kk - 1) & 1) * MT + mm] =
                     control_eps((uint32_t)kk, (uint32_t)sq, it0, it1, a.key0, a.key1, a.sig_v, a.sig_w);
             }
             __syncwarp();
-            if (lane == 0) mbar_arrive(nz_full + (kk & 1));
+            if (lane == 0) mbar_arrive(nz_full + ((kk - 1) & 1));
         };
-        noise(0);
+        // (the producers draw step 0's noise themselves)
         if (a.T > 1) noise(1);
         float cost[2] = {0.0f, 0.0f};
         float Sg[2][15];                            // covariance upper triangles (sidx order)
@@ -743,8 +754,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_cl(const RolloutArgs a, 
         for (int k = 0; k < a.T; ++k) {
             wait_or_abort(st_full + (k & 1), (uint32_t)(k >> 1) & 1u, abort_flag, a.err);
             __syncwarp();
-            // the producers read the noise slot of step k before they handed step k
-            // over, so it is free for step k + 2
+            // the slot of step k + 2 held step k's noise, which the producers read
+            // during step k - 1, before they handed step k over
             if (k + 2 < a.T) noise(k + 2);
             const float* sstk = sst + (k & 1) * nown * SST;
 #pragma unroll
