@@ -124,6 +124,7 @@ void free_ctrl(gpmppi_ctrl c) {
     cudaFree(c->gidx);
     cudaFree(c->err);
     cudaFree(c->grad_scr);
+    if (c->blas) cublasDestroy(c->blas);
     for (cudaEvent_t e : c->ev)
         if (e) cudaEventDestroy(e);
     if (c->gp && c->gp->magic == kGpMagic) c->gp->g.n_controllers--;
@@ -711,8 +712,6 @@ int mppi_grad(gpmppi_ctrl c, const float state[5], const float* U_nom, const flo
     GPM_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
     if (grad_smem_bytes(Np, C) > optin)
         return fail(GPMPPI_ERR_UNSUPPORTED, "mppi_grad: GP too large for the adjoint kernel's shared memory");
-    int nsm = 0;
-    GPM_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device));
     cudaStream_t st = (cudaStream_t)stream;
     const bool want_l = dlengthscale != nullptr;
     // per-GP factors of the adjoint, built once
@@ -728,10 +727,7 @@ int mppi_grad(gpmppi_ctrl c, const float state[5], const float* U_nom, const flo
     }
     // scratch layout (bytes, each piece 256-aligned)
     const int Q = T * Kpad;
-    int nsplit = 1;
-    const int pairs = gram_trace_blocks(Np, 1);
-    while (pairs * nsplit < 4 * nsm && Q / (nsplit * 2) >= 256) nsplit *= 2;
-    const int nparts = want_l ? gram_trace_blocks(Np, nsplit) : 0;
+    const int nparts = want_l ? gram_trace_dense_blocks(Np) : 0;
     size_t off = 0;
     auto take = [&](size_t bytes) {
         const size_t o = off;
@@ -743,9 +739,11 @@ int mppi_grad(gpmppi_ctrl c, const float state[5], const float* U_nom, const flo
     const size_t o_S = take(sizeof(float) * (size_t)K);
     const size_t o_dU = take(sizeof(float) * (size_t)2 * T * K);
     const size_t o_dl = take(sizeof(float) * (size_t)8 * K);
-    size_t o_B = 0, o_q = 0, o_p = 0;
+    size_t o_B = 0, o_C = 0, o_G = 0, o_q = 0, o_p = 0;
     if (want_l) {
         o_B = take(sizeof(float) * (size_t)Q * Np);
+        o_C = take(sizeof(float) * (size_t)Q * 2 * Np);
+        o_G = take(sizeof(float) * (size_t)2 * Np * Np);
         o_q = take(sizeof(float4) * (size_t)Q);
         o_p = take(sizeof(float) * 8 * (size_t)nparts);
     }
@@ -777,13 +775,30 @@ int mppi_grad(gpmppi_ctrl c, const float state[5], const float* U_nom, const flo
     ga.dl_out = want_l ? reinterpret_cast<float*>(base + o_dl) : nullptr;
     ga.Bq = want_l ? reinterpret_cast<float*>(base + o_B) : nullptr;
     ga.qbar = want_l ? reinterpret_cast<float4*>(base + o_q) : nullptr;
+    ga.Cq = want_l ? reinterpret_cast<float*>(base + o_C) : nullptr;
     if (c->profiling) GPM_CUDA(cudaEventRecord(c->ev[0], st));
     if ((rc = launch_grad(ga, ncta, st))) return rc;
     if (c->profiling) GPM_CUDA(cudaEventRecord(c->ev[1], st));
-    if (want_l &&
-        (rc = launch_gram_trace(ga.Bq, ga.qbar, Q, Np, N, g.Xs[0], g.sf2[0], nsplit,
-                                reinterpret_cast<float*>(base + o_p), st)))
-        return rc;
+    if (want_l) {
+        // G = [G_v; G_w] = C B^T, C = (sbar_v b, sbar_w b) per query: a plain FP32
+        // GEMM over the T K queries (cuBLAS, BF16x9 emulation of FP32 where it is
+        // faster), then the traces against dK/dl_d
+        if (!c->blas) {
+            if (cublasCreate(&c->blas) != CUBLAS_STATUS_SUCCESS) {
+                c->blas = nullptr;
+                return fail(GPMPPI_ERR_CUDA, "mppi_grad: cublasCreate failed");
+            }
+        }
+        float* G = reinterpret_cast<float*>(base + o_G);
+        const float one = 1.0f, zero = 0.0f;
+        if (cublasSetStream(c->blas, st) != CUBLAS_STATUS_SUCCESS ||
+            cublasGemmEx(c->blas, CUBLAS_OP_N, CUBLAS_OP_T, 2 * Np, Np, Q, &one, ga.Cq, CUDA_R_32F, 2 * Np, ga.Bq,
+                         CUDA_R_32F, Np, &zero, G, CUDA_R_32F, 2 * Np, CUBLAS_COMPUTE_32F_EMULATED_16BFX9,
+                         CUBLAS_GEMM_DEFAULT) != CUBLAS_STATUS_SUCCESS)
+            return fail(GPMPPI_ERR_CUDA, "mppi_grad: Gram GEMM failed");
+        if ((rc = launch_gram_trace_dense(G, Np, N, g.Xs[0], g.sf2[0], reinterpret_cast<float*>(base + o_p), st)))
+            return rc;
+    }
     GradReduceArgs rr;
     std::memset(&rr, 0, sizeof(rr));
     rr.dU_out = ga.dU_out;

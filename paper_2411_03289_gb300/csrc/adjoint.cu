@@ -468,10 +468,20 @@ __global__ void __launch_bounds__(GT, 2) k_grad(const GradArgs g) {
             __syncthreads();
             const float sbv2 = save[20], sbw2 = save[21], mbv2 = save[22], mbw2 = save[23];
             if (g.Bq) {
+                // b_q and (sbar_v b_q, sbar_w b_q): the two operands of G = C B^T
                 const size_t q0 = (size_t)k * g.Kpad + (size_t)blockIdx.x * GMT;
                 for (int ws = 0; ws < GMT; ++ws) {
+                    const bool live = blockIdx.x * GMT + ws < g.r.K;
+                    const float sv = live ? saves[ws * SAVE + 20] : 0.0f;
+                    const float sw = live ? saves[ws * SAVE + 21] : 0.0f;
                     float* dst = g.Bq + (q0 + ws) * Np;
-                    for (int j = tid; j < Np; j += GT) dst[j] = bufB[j * GMT + ws];
+                    float* dc = g.Cq + (q0 + ws) * 2 * Np;
+                    for (int j = tid; j < Np; j += GT) {
+                        const float b = bufB[j * GMT + ws];
+                        dst[j] = b;
+                        dc[j] = sv * b;
+                        dc[Np + j] = sw * b;
+                    }
                 }
                 if (lane == 0)
                     g.qbar[q0 + w] = act ? make_float4(mbv2, mbw2, sbv2, sbw2) : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -546,103 +556,44 @@ __global__ void __launch_bounds__(GT, 2) k_grad(const GradArgs g) {
 }
 
 // ---- Gram trace: sum_ij dK/dl_d[i][j] G_o[i][j], G_o = sum_q sbar_o,q b_q b_q^T ----
-constexpr int GTILE = 64;
-constexpr int GQ = 16;
-
-__global__ void __launch_bounds__(256) k_gram_trace(const float* __restrict__ Bq,
-                                                    const float4* __restrict__ qbar, int Q, int Np,
-                                                    int N, const float* __restrict__ Xs, float sf2,
-                                                    int ntile, int qper, float* __restrict__ part) {
-    __shared__ __align__(16) float bi[GQ][GTILE];
-    __shared__ __align__(16) float bj[GQ][GTILE];
-    __shared__ float2 sb[GQ];
+// tr(D_d G_o) for d = 0..3, o = v, w, with D_d[i][j] = sf2 2^-|xs_i - xs_j|^2
+// (xs_id - xs_jd)^2 (dK/dl_d up to the factor 2 ln2 / l_d) and G = [G_v; G_w]
+// (2 Np x Np, column-major, symmetric blocks): warp w of block b takes column
+// j = 8 b + w, lanes the rows i (coalesced); 8 partial sums per block.
+__global__ void __launch_bounds__(256) k_gram_trace_dense(const float* __restrict__ G, int Np, int N,
+                                                          const float* __restrict__ Xs, float sf2,
+                                                          float* __restrict__ part) {
     __shared__ float red[8][8];
-    // tile pair (I, J), I >= J, from the linear index
-    const int tix = blockIdx.x % (ntile * (ntile + 1) / 2);
-    const int split = blockIdx.x / (ntile * (ntile + 1) / 2);
-    int I = 0;
-    while ((I + 1) * (I + 2) / 2 <= tix) ++I;
-    const int J = tix - I * (I + 1) / 2;
-    const int q0 = split * qper, q1 = min(Q, q0 + qper);
-    const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
-    float av[4][4], aw[4][4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            av[i][j] = 0.0f;
-            aw[i][j] = 0.0f;
-        }
-    const int lrow = tid >> 4, lcol = (tid & 15) * 4;
-    for (int qc = q0; qc < q1; qc += GQ) {
-        const int q = qc + lrow;
-        float4 xi = make_float4(0.f, 0.f, 0.f, 0.f), xj = xi;
-        if (q < q1) {
-            const int ci = I * GTILE + lcol, cj = J * GTILE + lcol;
-            if (ci < Np) xi = __ldg(reinterpret_cast<const float4*>(Bq + (size_t)q * Np + ci));
-            if (cj < Np) xj = __ldg(reinterpret_cast<const float4*>(Bq + (size_t)q * Np + cj));
-        }
-        *reinterpret_cast<float4*>(&bi[lrow][lcol]) = xi;
-        *reinterpret_cast<float4*>(&bj[lrow][lcol]) = xj;
-        if (tid < GQ) {
-            const int qq = qc + tid;
-            const float4 qb = (qq < q1) ? __ldg(qbar + qq) : make_float4(0.f, 0.f, 0.f, 0.f);
-            sb[tid] = make_float2(qb.z, qb.w);
-        }
-        __syncthreads();
-#pragma unroll
-        for (int qq = 0; qq < GQ; ++qq) {
-            const float4 x = *reinterpret_cast<const float4*>(&bi[qq][ty * 4]);
-            const float4 y = *reinterpret_cast<const float4*>(&bj[qq][tx * 4]);
-            const float2 w2 = sb[qq];
-            const float xa[4] = {x.x, x.y, x.z, x.w};
-            const float ya[4] = {y.x, y.y, y.z, y.w};
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const float pv = xa[i] * w2.x, pw = xa[i] * w2.y;
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    av[i][j] = fmaf(pv, ya[j], av[i][j]);
-                    aw[i][j] = fmaf(pw, ya[j], aw[i][j]);
-                }
-            }
-        }
-        __syncthreads();
-    }
-    // epilogue: weight each entry of G by dK/dl_d / (2 ln2 / l_d) = Kf_ij (xs_id - xs_jd)^2
-    const float mult = (I != J) ? 2.0f : 1.0f;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int j = blockIdx.x * 8 + warp;
     float tr[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int ii = I * GTILE + ty * 4 + i;
-        if (ii >= N) continue;
-        const float4 xi = ldg4(Xs + 4 * ii);
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int jj = J * GTILE + tx * 4 + j;
-            if (jj >= N) continue;
-            const float4 xj = ldg4(Xs + 4 * jj);
-            const float d[4] = {xi.x - xj.x, xi.y - xj.y, xi.z - xj.z, xi.w - xj.w};
-            const float dd[4] = {d[0] * d[0], d[1] * d[1], d[2] * d[2], d[3] * d[3]};
-            const float kf = mult * sf2 * exp2f(-(dd[0] + dd[1] + dd[2] + dd[3]));
+    if (j < N) {
+        const float4 xj = ldg4(Xs + 4 * j);
+        const float* gv = G + (size_t)j * 2 * Np;
+        const float* gw = gv + Np;
+        for (int i = lane; i < N; i += 32) {
+            const float4 xi = ldg4(Xs + 4 * i);
+            const float d0 = xi.x - xj.x, d1 = xi.y - xj.y, d2 = xi.z - xj.z, d3 = xi.w - xj.w;
+            const float dd[4] = {d0 * d0, d1 * d1, d2 * d2, d3 * d3};
+            const float kf = sf2 * exp2f(-(dd[0] + dd[1] + dd[2] + dd[3]));
+            const float a = __ldg(gv + i), b = __ldg(gw + i);
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-                tr[e] = fmaf(kf * dd[e], av[i][j], tr[e]);
-                tr[4 + e] = fmaf(kf * dd[e], aw[i][j], tr[4 + e]);
+                tr[e] = fmaf(kf * dd[e], a, tr[e]);
+                tr[4 + e] = fmaf(kf * dd[e], b, tr[4 + e]);
             }
         }
     }
-    const int warp = tid >> 5, lane = tid & 31;
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
         const float v = wsum(tr[e]);
         if (lane == 0) red[warp][e] = v;
     }
     __syncthreads();
-    if (tid < 8) {
+    if (threadIdx.x < 8) {
         float v = 0.0f;
-        for (int wI = 0; wI < 8; ++wI) v += red[wI][tid];
-        part[(size_t)blockIdx.x * 8 + tid] = v;
+        for (int w = 0; w < 8; ++w) v += red[w][threadIdx.x];
+        part[(size_t)blockIdx.x * 8 + threadIdx.x] = v;
     }
 }
 
@@ -737,20 +688,13 @@ int launch_grad(const GradArgs& g, int ncta, cudaStream_t st) {
     return 0;
 }
 
-int launch_gram_trace(const float* Bq, const float4* qbar, int Q, int Np, int N, const float* Xs,
-                      float sf2, int nsplit, float* part, cudaStream_t st) {
-    const int ntile = (Np + GTILE - 1) / GTILE;
-    const int pairs = ntile * (ntile + 1) / 2;
-    int qper = (Q + nsplit - 1) / nsplit;
-    qper = ((qper + GQ - 1) / GQ) * GQ;
-    k_gram_trace<<<pairs * nsplit, 256, 0, st>>>(Bq, qbar, Q, Np, N, Xs, sf2, ntile, qper, part);
+int gram_trace_dense_blocks(int Np) { return (Np + 7) / 8; }
+
+int launch_gram_trace_dense(const float* G, int Np, int N, const float* Xs, float sf2, float* part,
+                            cudaStream_t st) {
+    k_gram_trace_dense<<<gram_trace_dense_blocks(Np), 256, 0, st>>>(G, Np, N, Xs, sf2, part);
     GPM_CUDA(cudaGetLastError());
     return 0;
-}
-
-int gram_trace_blocks(int Np, int nsplit) {
-    const int ntile = (Np + GTILE - 1) / GTILE;
-    return ntile * (ntile + 1) / 2 * nsplit;
 }
 
 int launch_dk_alpha(const float* Xs, const float* alpha, int N, int Np, float sf2, float* ubar,

@@ -277,6 +277,7 @@ struct GradArgs {
     float* dl_out;          // 8 x K per-sample lengthscale terms, or null
     float* Bq;              // (T Kpad) x Np: b = K^-1 k* per query, or null
     float4* qbar;           // T Kpad: (mbar_v, mbar_w, sbar_v, sbar_w) per query
+    float* Cq;              // (T Kpad) x 2 Np: (sbar_v b, sbar_w b) per query, or null
 };
 
 struct GradReduceArgs {
@@ -354,9 +355,11 @@ int rollout_fp32_mtp(int Np);
 int grad_smem_bytes(int Np, int C);
 int grad_samples_per_cta();
 int launch_grad(const GradArgs& g, int ncta, cudaStream_t st);
-int launch_gram_trace(const float* Bq, const float4* qbar, int Q, int Np, int N, const float* Xs,
-                      float sf2, int nsplit, float* part, cudaStream_t st);
-int gram_trace_blocks(int Np, int nsplit);
+// tr(D_d G_o) from G = [G_v; G_w] (2 Np x Np, column-major): one block per 8
+// columns, 8 partial sums per block; returns the number of blocks
+int launch_gram_trace_dense(const float* G, int Np, int N, const float* Xs, float sf2, float* part,
+                            cudaStream_t st);
+int gram_trace_dense_blocks(int Np);
 int launch_dk_alpha(const float* Xs, const float* alpha, int N, int Np, float sf2, float* ubar,
                     cudaStream_t st);
 int launch_transpose(const float* W, int Np, float* Wt, cudaStream_t st);

@@ -2,6 +2,8 @@
 // shared by the translation units that implement the ABI.
 #pragma once
 
+#include <cublas_v2.h>
+
 #include "common.cuh"
 
 constexpr uint32_t kGpMagicValue = 0x47504d31u;     // "GPM1"
@@ -48,6 +50,7 @@ struct gpmppi_ctrl_s {
     float tw[gpm::kMaxTerrains] = {};
     // adjoint-rollout scratch (allocated by the first mppi_grad call)
     void* grad_scr = nullptr;
+    cublasHandle_t blas = nullptr;      // the gradient's Gram GEMM
     size_t grad_bytes = 0;
     bool profiling = false;
     bool profiled = false;
