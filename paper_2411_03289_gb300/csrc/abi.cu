@@ -99,6 +99,7 @@ void free_gp(gpmppi_gp h) {
         cudaFree(g.mma_lo[f]);
         cudaFree(g.cl_tiles[f]);
     }
+    cudaFree(g.cl_xa);
     cudaFree(g.Wt);
     cudaFree(g.ubar);
     if (!g.shared) {
@@ -537,6 +538,7 @@ int mppi_create(const gpmppi_params* p, const float* obstacles, int32_t O, const
                 ClArgs& cl = c->cla;
                 cl.tiles = gp->g.cl_tiles[c->fmt];
                 cl.npc = gp->g.cl_npc;
+                cl.xa = gp->g.cl_xa;
                 cl.ns = cl.npc / 64;
                 cl.cs = cl.ns / 2;
                 for (int r = 0; r < 4; ++r) {

@@ -130,6 +130,9 @@ struct GpDevice {
     int cl_base[4] = {0, 0, 0, 0};
     int cl_bytes[4] = {0, 0, 0, 0};
     int cl_npc = 0;
+    // the cluster rollout's training inputs and alpha in pair layout (NpC x 4
+    // floats, then NpC x 2), copied into shared memory by one bulk copy
+    float* cl_xa = nullptr;
     // adjoint rollout, built on first use: rows of L^-1 (Np x Np) and the
     // vectors (dK/dl_d) alpha_o (8 x Np)
     float* Wt = nullptr;
@@ -306,6 +309,7 @@ struct ClArgs {
     int npc;                // padded training-set size (128, 256 or 512)
     float qscale;           // (sf2 / cB)^2
     int scene_smem;         // lane segments and obstacles staged in shared memory
+    const float* xa;        // training inputs and alpha in pair layout (npc x 6 floats)
 };
 
 struct UpdateArgs {

@@ -353,6 +353,30 @@ __global__ void k_pack_cl(const double* __restrict__ Xm, int N, int NS, int fmt,
 
 }  // namespace
 
+// training inputs and alpha of the cluster rollout in pair layout: for points
+// 2p and 2p + 1, x[2p] = (x0, x0', x1, x1'), x[2p + 1] = (x2, x2', x3, x3') and
+// a[p] = (a_v, a_v', a_w, a_w') (primes: point 2p + 1); rows j >= N get a far
+// point (exp2 underflows to exactly 0) and alpha 0
+__global__ void k_pack_xa(const float* __restrict__ Xs, const float* __restrict__ alpha, int N, int npc,
+                          float* __restrict__ out) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= npc) return;
+    float4 x = make_float4(1.0e4f, 1.0e4f, 1.0e4f, 1.0e4f);
+    float2 al = make_float2(0.0f, 0.0f);
+    if (j < N) {
+        x = reinterpret_cast<const float4*>(Xs)[j];
+        al = reinterpret_cast<const float2*>(alpha)[j];
+    }
+    float* xp = out + 8 * (j >> 1) + (j & 1);
+    xp[0] = x.x;
+    xp[2] = x.y;
+    xp[4] = x.z;
+    xp[6] = x.w;
+    float* ap = out + 4 * npc + 4 * (j >> 1) + (j & 1);
+    ap[0] = al.x;
+    ap[2] = al.y;
+}
+
 int build_cl_tiles(GpDevice& g, int fmt) {
     if (g.cl_tiles[fmt] || g.N == 0) return GPMPPI_OK;
     int rc = build_mma_tiles(g, fmt);      // sets cB (and the streaming tiles)
@@ -384,6 +408,15 @@ int build_cl_tiles(GpDevice& g, int fmt) {
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     cudaFree(dp);
     if (e != cudaSuccess) return cuda_fail(e, "build_cl_tiles");
+    if (!g.cl_xa) {
+        e = cudaMalloc(&g.cl_xa, sizeof(float) * 6 * (size_t)NpC);
+        if (e == cudaSuccess) {
+            k_pack_xa<<<(NpC + 127) / 128, 128>>>(g.Xs[0], g.alpha, g.N, NpC, g.cl_xa);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) return cuda_fail(e, "build_cl_tiles: training-set layout");
+    }
     return GPMPPI_OK;
 }
 

@@ -79,9 +79,9 @@ __host__ __device__ inline ClLayout cl_layout(int npc, int S, int O) {
     ClLayout L;
     L.b = 0;
     // a_full, empty [NSTAGE], b_res, pass_done, tmem_free, xbar[2], st_full[2], st_empty[2],
-    // nz_full[2], ar_full
+    // nz_full[2], ar_full, x_res
     L.bars = B_MAX;
-    L.tslot = L.bars + 8 * (2 * NSTAGE + 12);
+    L.tslot = L.bars + 8 * (2 * NSTAGE + 13);
     L.abort_flag = L.tslot + 4;
     // exchange buffers [2 (step parity)][8 (rank, thread half)][MT]: partial
     // |V|^2 (float) and GP mean partial (v, w) of every producer thread
@@ -272,6 +272,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_cl(const RolloutArgs a, 
     uint64_t* st_empty = st_full + 2;           // [2] ... and released by them
     uint64_t* nz_full = st_empty + 2;           // [2] noise of a step, written by the scoring warps
     uint64_t* ar_full = nz_full + 2;            // rank 0: the kernel rows copied in by the last rank
+    uint64_t* x_res = ar_full + 1;              // the training set copied in
     uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + L.tslot);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + L.abort_flag);
     float* xq = reinterpret_cast<float*>(sm + L.xq);
@@ -338,28 +339,14 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_cl(const RolloutArgs a, 
             tc::mbar_init(nz_full + i, NCOST / 32);
         }
         tc::mbar_init(ar_full, 1);
+        tc::mbar_init(x_res, 1);
         *abort_flag = 0;
         tc::fence_mbar_init();
     }
-    // training inputs and alpha in pair layout: for points 2p and 2p + 1,
-    // xs_s[2p] = (x0, x0', x1, x1'), xs_s[2p + 1] = (x2, x2', x3, x3') and
-    // al_s[p] = (a_v, a_v', a_w, a_w'), primes marking point 2p + 1
-    for (int j = tid; j < cl.npc; j += THREADS) {
-        float4 x = make_float4(1.0e4f, 1.0e4f, 1.0e4f, 1.0e4f);
-        float2 al = make_float2(0.0f, 0.0f);
-        if (j < a.N) {
-            x = __ldg(reinterpret_cast<const float4*>(a.Xs) + j);
-            al = __ldg(reinterpret_cast<const float2*>(a.alpha) + j);
-        }
-        float* xp = reinterpret_cast<float*>(xs_s + 2 * (j >> 1)) + (j & 1);
-        xp[0] = x.x;
-        xp[2] = x.y;
-        xp[4] = x.z;
-        xp[6] = x.w;
-        float* ap = reinterpret_cast<float*>(al_s + (j >> 1)) + (j & 1);
-        ap[0] = al.x;
-        ap[2] = al.y;
-    }
+    // training inputs and alpha arrive by one bulk copy (TMA engine) in pair
+    // layout: for points 2p and 2p + 1, xs_s[2p] = (x0, x0', x1, x1'),
+    // xs_s[2p + 1] = (x2, x2', x3, x3') and al_s[p] = (a_v, a_v', a_w, a_w')
+    // (primes: point 2p + 1); rows past N hold a far point and alpha 0
     const int Ssm = cl.scene_smem ? a.S : 0, Osm = cl.scene_smem ? a.O : 0;
     for (int i = tid; i < Ssm; i += THREADS) {
         seg_s[i] = __ldg(a.seg + i);
@@ -377,6 +364,9 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_cl(const RolloutArgs a, 
         // this rank's resident share of the factor, one copy for the whole horizon
         tc::mbar_expect_tx(b_res, bbytes);
         bulk_copy(bres, cl.tiles + cl.base[rank], bbytes, b_res);
+        tc::mbar_expect_tx(x_res, (uint32_t)(cl.npc * 24));
+        bulk_copy(xs_s, cl.xa, (uint32_t)(cl.npc * 16), x_res);
+        bulk_copy(al_s, cl.xa + 4 * cl.npc, (uint32_t)(cl.npc * 8), x_res);
     }
     // every CTA's barriers are initialised before any peer arrives on them
     cluster_sync_all();
@@ -502,6 +492,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_cl(const RolloutArgs a, 
             return uk;
         };
         float2 ut_next = control(0);
+        wait_or_abort(x_res, 0u, abort_flag, a.err);     // the training set in shared memory
 
         for (int k = 0; k < a.T; ++k) {
             // ---------------- query ------------------------------------------------

@@ -49,8 +49,8 @@ struct MLayout {
 
 __host__ __device__ inline MLayout mma_layout(int nstage, int NpM, int S, int O) {
     MLayout L;
-    L.bars = nstage * STAGE;                     // a_full, b_full, empty [NSTAGE] + pass_done, tmem_free
-    L.tslot = L.bars + 8 * (3 * NSTAGE + 2);
+    L.bars = nstage * STAGE;                     // a_full, b_full, empty [NSTAGE] + pass_done, tmem_free, x_res
+    L.tslot = L.bars + 8 * (3 * NSTAGE + 3);
     L.abort_flag = L.tslot + 4;
     L.qh = ((L.abort_flag + 4 + 15) / 16) * 16;  // 2 x 128 floats
     L.mh = L.qh + 2 * MT * 4;                    // 2 x 128 float2
@@ -147,6 +147,7 @@ __device__ __forceinline__ void rollout_mma_body(const RolloutArgs& a, const Mma
     uint64_t* empty = b_full + NSTAGE;
     uint64_t* pass_done = empty + NSTAGE;
     uint64_t* tmem_free = pass_done + 1;
+    uint64_t* x_res = tmem_free + 1;            // the training set copied in
     uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + L.tslot);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + L.abort_flag);
     float4* xs_s = reinterpret_cast<float4*>(sm + L.xs);
@@ -167,20 +168,23 @@ __device__ __forceinline__ void rollout_mma_body(const RolloutArgs& a, const Mma
         }
         tc::mbar_init(pass_done, 1);
         tc::mbar_init(tmem_free, NPROD / 32);
+        tc::mbar_init(x_res, 1);
         *abort_flag = 0;
         tc::fence_mbar_init();
+        // scaled training inputs and alpha (whole 16-byte lines of it) by bulk
+        // copies (TMA engine); the threads fill the rest below
+        const uint32_t xb = (uint32_t)a.N * 16u, ab = ((uint32_t)a.N * 8u) & ~15u;
+        tc::mbar_expect_tx(x_res, xb + ab);
+        if (xb) bulk_copy(xs_s, a.Xs, xb, x_res);
+        if (ab) bulk_copy(al_s, a.alpha, ab, x_res);
     }
-    // scaled training inputs and alpha in shared memory; rows j >= N get a far
-    // point (exp2 underflows to exactly 0) and alpha 0
-    for (int j = tid; j < NB * BLK; j += THREADS) {
-        if (j < a.N) {
-            xs_s[j] = __ldg(reinterpret_cast<const float4*>(a.Xs) + j);
-            al_s[j] = __ldg(reinterpret_cast<const float2*>(a.alpha) + j);
-        } else {
-            xs_s[j] = make_float4(1.0e4f, 1.0e4f, 1.0e4f, 1.0e4f);
-            al_s[j] = make_float2(0.0f, 0.0f);
-        }
+    // rows j >= N get a far point (exp2 underflows to exactly 0) and alpha 0;
+    // an odd N leaves the last alpha to a thread
+    for (int j = a.N + tid; j < NB * BLK; j += THREADS) {
+        xs_s[j] = make_float4(1.0e4f, 1.0e4f, 1.0e4f, 1.0e4f);
+        al_s[j] = make_float2(0.0f, 0.0f);
     }
+    if ((a.N & 1) && tid == 0) al_s[a.N - 1] = __ldg(reinterpret_cast<const float2*>(a.alpha) + a.N - 1);
     // lane segments and obstacles too: the cost phase reads them every step
     for (int i = tid; i < Ssm; i += THREADS) {
         seg_s[i] = __ldg(a.seg + i);
@@ -266,6 +270,7 @@ __device__ __forceinline__ void rollout_mma_body(const RolloutArgs& a, const Mma
     }
 
     // ========================== producer warps =================================
+    wait_or_abort(x_res, 0u, abort_flag, a.err);     // the training set in shared memory
     const int m = tid % MTC;           // sample within the CTA
     const int u = tid / MTC;           // which of its R threads
     const int mr = tid & (MT - 1);     // TMEM lane this thread reads at a pass end
