@@ -310,9 +310,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_cl(const RolloutArgs a, 
     const bool rows_in = CS == 4 && rank == 0;
     int me0 = 0, me1 = 0;
     if (CS == 4) {
-        const int lo[4] = {0, 24, 12, 0}, hi[4] = {0, 28, 24, 12};
-        mc0 = lo[rank];
-        mc1 = hi[rank];
+        mc0 = rank == 1 ? 24 : (rank == 2 ? 12 : 0);
+        mc1 = rank == 0 ? 0 : (rank == 1 ? 28 : (rank == 2 ? 24 : 12));
         if (rows_out) {
             me0 = 4 * NS - AR_CHUNKS;
             me1 = 4 * NS;
@@ -500,9 +499,10 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_cl(const RolloutArgs a, 
             const float z0 = mu3 * a.zscale[0], z1 = mu4 * a.zscale[1];
             const float z2 = ut.x * a.zscale[2], z3 = ut.y * a.zscale[3];
 
-            // ---------------- kernel-row tiles (8 points per thread per chunk) ----
-            // BURST chunks per burst (32 independent exp2 in flight).  The GP mean
-            // is split between the ranks: rank r sums chunks [mc0, mc1).
+            // ---------------- kernel-row tiles ---------------------------------------
+            // A burst is BURST = 4 chunks; each thread computes two whole chunks of
+            // 16 points (32 independent exp2 in flight).  The GP mean is split
+            // between the ranks: rank r sums chunks [mc0, mc1) (and [me0, me1)).
             float mv = 0.0f, mw = 0.0f, cv = 0.0f, cw = 0.0f;
             const uint64_t zz0 = f2pack(z0, z0), zz1 = f2pack(z1, z1);
             const uint64_t zz2 = f2pack(z2, z2), zz3 = f2pack(z3, z3);
@@ -602,12 +602,6 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_cl(const RolloutArgs a, 
                 __syncwarp();
                 if (lane == 0) mbar_arrive(a_full + st);
                 ++n;
-            }
-            // chunks needed for the GP mean alone, alternate between the two threads
-            for (int c = (mc0 > nch ? mc0 : nch) + u; c < mc1; c += 2) {
-                uint64_t av[8];
-                kernel_row(c, av);
-                mean_part(c, av);
             }
             // ---------------- the part of the step that needs no GP result ---------
             // (unicycle with velocity lag; the covariance recursion, which the mean
