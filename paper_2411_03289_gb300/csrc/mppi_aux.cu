@@ -92,35 +92,21 @@ __device__ __forceinline__ void update_body(const UpdateArgs& a, int cta, int n_
     // k = w, w + 8, ..., lane l the samples l, l + 32, ... (coalesced reads of
     // u~, all of a lane's loads in flight together)
     const int ns = min(a.per_cta, K - s_base);
-    // two steps per pass (k and k + 8), so that twice the loads are in flight
-    for (int k = warp; k < T; k += 2 * UPD_WARPS) {
-        const int k2 = k + UPD_WARPS;
-        const bool two = k2 < T;                 // warp-uniform
+    for (int k = warp; k < T; k += UPD_WARPS) {
         const float uv = __ldg(a.U + 2 * k), uw = __ldg(a.U + 2 * k + 1);
-        const float uv2 = two ? __ldg(a.U + 2 * k2) : 0.0f, uw2 = two ? __ldg(a.U + 2 * k2 + 1) : 0.0f;
         const float2* ut = a.u_tilde + (size_t)k * K + s_base;
-        const float2* ut2 = a.u_tilde + (size_t)(two ? k2 : k) * K + s_base;
-        float dv = 0.0f, dw = 0.0f, dv2 = 0.0f, dw2 = 0.0f;
+        float dv = 0.0f, dw = 0.0f;
 #pragma unroll 8
         for (int i = lane; i < ns; i += 32) {
             const float2 u = __ldg(ut + i);
-            const float2 u2 = two ? __ldg(ut2 + i) : make_float2(0.0f, 0.0f);
             dv = fmaf(wsh[i], u.x - uv, dv);
             dw = fmaf(wsh[i], u.y - uw, dw);
-            dv2 = fmaf(wsh[i], u2.x - uv2, dv2);
-            dw2 = fmaf(wsh[i], u2.y - uw2, dw2);
         }
         dv = warp_sum(dv);
         dw = warp_sum(dw);
-        dv2 = warp_sum(dv2);
-        dw2 = warp_sum(dw2);
         if (lane == 0) {
             a.partial[((size_t)cta * T + k) * 2] = dv;
             a.partial[((size_t)cta * T + k) * 2 + 1] = dw;
-            if (two) {
-                a.partial[((size_t)cta * T + k2) * 2] = dv2;
-                a.partial[((size_t)cta * T + k2) * 2 + 1] = dw2;
-            }
         }
     }
     // last CTA combines the partials in CTA order
@@ -132,7 +118,6 @@ __device__ __forceinline__ void update_body(const UpdateArgs& a, int cta, int n_
     __threadfence();
     for (int i = tid; i < 2 * T; i += UPD_THREADS) {
         float acc = 0.0f;
-#pragma unroll 8
         for (int c = 0; c < n_cta; ++c) acc += __ldcg(a.partial + (size_t)c * 2 * T + i);
         a.U_new[i] = __ldg(a.U + i) + acc;
     }
