@@ -1,12 +1,16 @@
 // MPPI weights and control update, Alg. 1 Step 2 (nominal tightening) and
 // the raw-noise entry points.
 //
-// Update (Alg. 1, "weights" and "weighted sum"): every CTA reduces the K
-// costs to rho = min S and Z = sum_s exp(-(S_s - rho)/lambda) in one fixed
-// order (so all CTAs agree bit for bit), writes w_s for its own samples, and
-// reduces sum_s w_s (u~_s,k - U_k) over them for every step k (one warp per
-// step, coalesced reads of u~, warp shuffles).  The per-CTA partials go to a scratch array; the CTA that
-// finishes last (atomic ticket) sums them in CTA order and writes U_new.
+// Update (Alg. 1, "weights" and "weighted sum"): CTA (b, j) of the grid
+// takes sample block b (256 samples) and step block j (16 steps).  Every
+// CTA reduces the K costs to rho = min S and Z = sum_s exp(-(S_s - rho)/lambda)
+// in one fixed order (so all CTAs agree bit for bit), forms w_s for its
+// samples (CTAs of step block 0 write them out), and reduces
+// sum_s w_s (u~_s,k - U_k) over them for its steps (two steps per warp, all
+// loads of a lane in flight together, coalesced reads of u~, warp shuffles).
+// The partials go to a scratch array [sample block][T][2]; the CTA that
+// finishes last (atomic ticket) sums them in sample-block order and writes
+// U_new.
 #include <cfloat>
 
 #include "common.cuh"
@@ -16,6 +20,8 @@ namespace {
 
 constexpr int UPD_THREADS = 256;
 constexpr int UPD_WARPS = UPD_THREADS / 32;
+constexpr int UPD_SPW = 2;                          // steps per warp
+constexpr int UPD_STEPS = UPD_WARPS * UPD_SPW;      // steps per CTA
 
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
@@ -46,8 +52,10 @@ __device__ __forceinline__ void for_costs(const float* __restrict__ costs, int K
     }
 }
 
-__device__ __forceinline__ void update_body(const UpdateArgs& a, int cta, int n_cta,
-                                            unsigned long long* it_dev) {
+// cta: sample block; [k_lo, k_hi): the CTA's steps; n_sb sample blocks and
+// n_total CTAs in all (the ticket counts every CTA)
+__device__ __forceinline__ void update_body(const UpdateArgs& a, int cta, int n_sb, int k_lo, int k_hi,
+                                            int n_total, unsigned long long* it_dev) {
     __shared__ float red[UPD_WARPS];
     __shared__ float bcast[2];
     __shared__ float wsh[UPD_THREADS];
@@ -85,40 +93,68 @@ __device__ __forceinline__ void update_body(const UpdateArgs& a, int cta, int n_
     const int s = s_base + tid;
     const bool act = (tid < a.per_cta) && (s < K);
     const float w = act ? expf((rho - __ldg(a.costs + s)) * a.inv_lambda) * inv_z : 0.0f;
-    if (act && a.weights) a.weights[s] = w;
+    if (act && a.weights && k_lo == 0) a.weights[s] = w;
     wsh[tid] = w;
     __syncthreads();
-    // sum_s w_s (u~_s,k - U_k) over the CTA's samples: warp w takes the steps
-    // k = w, w + 8, ..., lane l the samples l, l + 32, ... (coalesced reads of
-    // u~, all of a lane's loads in flight together)
+    // sum_s w_s (u~_s,k - U_k) over the CTA's samples: warp w takes steps
+    // k_lo + 2 w and k_lo + 2 w + 1 (then + 16 ...), lane l the samples l,
+    // l + 32, ... (coalesced reads of u~, all of a lane's loads in flight)
     const int ns = min(a.per_cta, K - s_base);
-    for (int k = warp; k < T; k += UPD_WARPS) {
-        const float uv = __ldg(a.U + 2 * k), uw = __ldg(a.U + 2 * k + 1);
-        const float2* ut = a.u_tilde + (size_t)k * K + s_base;
-        float dv = 0.0f, dw = 0.0f;
-#pragma unroll 8
-        for (int i = lane; i < ns; i += 32) {
-            const float2 u = __ldg(ut + i);
-            dv = fmaf(wsh[i], u.x - uv, dv);
-            dw = fmaf(wsh[i], u.y - uw, dw);
+    for (int k0 = k_lo + warp * UPD_SPW; k0 < k_hi; k0 += UPD_STEPS) {
+        float2 uu[UPD_SPW][8];
+        float uv[UPD_SPW], uw[UPD_SPW];
+#pragma unroll
+        for (int j = 0; j < UPD_SPW; ++j) {
+            const int k = k0 + j;
+            const bool kin = k < k_hi;
+            uv[j] = kin ? __ldg(a.U + 2 * k) : 0.0f;
+            uw[j] = kin ? __ldg(a.U + 2 * k + 1) : 0.0f;
+            const float2* ut = a.u_tilde + (size_t)(kin ? k : k_lo) * K + s_base;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int i = lane + 32 * q;
+                uu[j][q] = (kin && i < ns) ? __ldg(ut + i) : make_float2(0.0f, 0.0f);
+            }
         }
-        dv = warp_sum(dv);
-        dw = warp_sum(dw);
-        if (lane == 0) {
-            a.partial[((size_t)cta * T + k) * 2] = dv;
-            a.partial[((size_t)cta * T + k) * 2 + 1] = dw;
+#pragma unroll
+        for (int j = 0; j < UPD_SPW; ++j) {
+            float dv = 0.0f, dw = 0.0f;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int i = lane + 32 * q;
+                if (i < ns) {
+                    dv = fmaf(wsh[i], uu[j][q].x - uv[j], dv);
+                    dw = fmaf(wsh[i], uu[j][q].y - uw[j], dw);
+                }
+            }
+            dv = warp_sum(dv);
+            dw = warp_sum(dw);
+            const int k = k0 + j;
+            if (lane == 0 && k < k_hi) {
+                a.partial[((size_t)cta * T + k) * 2] = dv;
+                a.partial[((size_t)cta * T + k) * 2 + 1] = dw;
+            }
         }
     }
     // last CTA combines the partials in CTA order
     __threadfence();
     __syncthreads();
-    if (tid == 0) is_last = (atomicAdd(a.counter, 1u) == (unsigned int)n_cta - 1u) ? 1u : 0u;
+    if (tid == 0) is_last = (atomicAdd(a.counter, 1u) == (unsigned int)n_total - 1u) ? 1u : 0u;
     __syncthreads();
     if (!is_last) return;
     __threadfence();
     for (int i = tid; i < 2 * T; i += UPD_THREADS) {
+        // sample-block order; sixteen loads in flight at a time
         float acc = 0.0f;
-        for (int c = 0; c < n_cta; ++c) acc += __ldcg(a.partial + (size_t)c * 2 * T + i);
+        for (int c0 = 0; c0 < n_sb; c0 += 16) {
+            float p[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+                p[j] = c0 + j < n_sb ? __ldcg(a.partial + (size_t)(c0 + j) * 2 * T + i) : 0.0f;
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+                if (c0 + j < n_sb) acc += p[j];
+        }
         a.U_new[i] = __ldg(a.U + i) + acc;
     }
     if (tid == 0) {
@@ -128,7 +164,8 @@ __device__ __forceinline__ void update_body(const UpdateArgs& a, int cta, int n_
 }
 
 __global__ void __launch_bounds__(UPD_THREADS) k_update(const UpdateArgs a) {
-    update_body(a, blockIdx.x, gridDim.x, nullptr);
+    const int k_lo = blockIdx.y * UPD_STEPS;
+    update_body(a, blockIdx.x, gridDim.x, k_lo, min(a.T, k_lo + UPD_STEPS), gridDim.x * gridDim.y, nullptr);
 }
 
 // Many controllers: CTA i serves CTA items[i].y of controller items[i].x,
@@ -138,7 +175,7 @@ __global__ void __launch_bounds__(UPD_THREADS)
     k_update_batched(const UpdateArgs* __restrict__ args, const int2* __restrict__ items,
                      const int* __restrict__ ncta, unsigned long long* __restrict__ iters) {
     const int2 it = items[blockIdx.x];
-    update_body(args[it.x], it.y, ncta[it.x], iters + it.x);
+    update_body(args[it.x], it.y, ncta[it.x], 0, args[it.x].T, ncta[it.x], iters + it.x);
 }
 
 __global__ void k_philox(uint32_t key0, uint32_t key1, const uint4* __restrict__ ctr, int M,
@@ -251,7 +288,9 @@ __global__ void __launch_bounds__(NOM_THREADS) k_nominal(const RolloutArgs a, co
 }  // namespace
 
 int launch_update(const UpdateArgs& a, int n_cta, cudaStream_t st) {
-    k_update<<<n_cta, UPD_THREADS, 0, st>>>(a);
+    // (T = 0: one step block, no steps; the last CTA still writes nothing)
+    const int nstep = a.T > 0 ? (a.T + UPD_STEPS - 1) / UPD_STEPS : 1;
+    k_update<<<dim3(n_cta, nstep), UPD_THREADS, 0, st>>>(a);
     GPM_CUDA(cudaGetLastError());
     return GPMPPI_OK;
 }

@@ -17,14 +17,17 @@
 // whole shared-memory bandwidth, and streaming the factor through it every
 // step halved the MMA rate.
 //
-// Per step: every rank computes the noise, queries and kernel rows of all 128
-// samples (and its share of the GP mean), issues the MMAs of its slices, reads
-// its partial |V_m|^2 from TMEM and exchanges the partials and mean shares
-// through distributed shared memory, guarded by mbarriers that each peer
-// arrives on remotely.  All ranks then advance the same 128 states
-// identically (same inputs, same order of summation); the cost phase (lane
-// distance, obstacles, Eq. 11-16) is split between the ranks by sample, so
-// rank r scores and writes the samples m = r (mod CS).
+// Per step: every rank computes the queries and kernel rows of all 128
+// samples (and its share of the GP mean), issues the MMAs of its slices and
+// sends its mean share to every peer through distributed shared memory as
+// soon as the share is complete (asynchronous stores that complete bytes on
+// the receiver's mbarrier).  All ranks then advance the same 128 states
+// identically (same inputs, same order of summation).  The variance is off
+// that chain: a rank reads its partial |V_m|^2 from TMEM one step later,
+// while the next step's kernel rows are in flight, and sends it to the rank
+// that scores sample m.  The cost phase (lane distance, obstacles,
+// Eq. 11-16) is split between the ranks by sample, so rank r scores and
+// writes the samples m = r (mod CS).
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -57,8 +60,9 @@ static_assert(A_COL + NSTAGE * A_STAGE_COLS <= TM_COLS, "A ring exceeds the TMEM
 constexpr int B_MAX = 144 * 1024;     // largest resident share (NS = 8)
 constexpr uint64_t kWaitNs = 2000000000ull;
 // hand-off record of one scored sample and step: post-step mean (5), pre-step
-// speed, sin and cos of the pre-step heading, GP variance s
-constexpr int SST = 9;
+// speed, sin and cos of the pre-step heading (the GP variance s arrives
+// separately, as the |V_m|^2 partials of every rank)
+constexpr int SST = 8;
 // With four ranks the last rank computes the kernel rows of rank 0's last four
 // chunks and copies them into rank 0's shared memory (hi and lo, 128 rows x 16
 // points each, in the slab-major operand layout): rank 0, the rank every step
@@ -68,7 +72,7 @@ constexpr int AR_CHUNK_BYTES = 2 * MT * 16 * 2;     // 8 KiB: hi 4 KiB, then lo
 constexpr int AR_BYTES = AR_CHUNKS * AR_CHUNK_BYTES;
 
 struct ClLayout {
-    int b, bars, tslot, abort_flag, xq, xm, ar, sst, nz, xs, al, seg, il2, obs, total;
+    int b, bars, tslot, abort_flag, xq, xm, ar, sst, xs, al, seg, il2, obs, total;
 };
 
 // shared-memory layout; the resident B share is sized for the largest rank;
@@ -79,25 +83,49 @@ __host__ __device__ inline ClLayout cl_layout(int npc, int S, int O) {
     ClLayout L;
     L.b = 0;
     // a_full, empty [NSTAGE], b_res, pass_done, tmem_free, xbar[2], st_full[2], st_empty[2],
-    // nz_full[2], ar_full, x_res
+    // ar_full, x_res, qbar[4]
     L.bars = B_MAX;
-    L.tslot = L.bars + 8 * (2 * NSTAGE + 13);
+    L.tslot = L.bars + 8 * (2 * NSTAGE + 15);
     L.abort_flag = L.tslot + 4;
-    // exchange buffers [2 (step parity)][8 (rank, thread half)][MT]: partial
-    // |V|^2 (float) and GP mean partial (v, w) of every producer thread
+    // received partial |V|^2 of the samples this rank scores,
+    // [4 (step mod 4)][2 CS (sending rank, thread half)][nown] floats, and the
+    // GP mean partials (v, w) of every producer thread of every rank,
+    // [2 (step parity)][8 (rank, thread half)][MT] float2
     L.xq = ((L.abort_flag + 4 + 15) / 16) * 16;
-    L.xm = L.xq + 2 * 8 * MT * 4;
+    L.xm = L.xq + 4 * 2 * MT * 4;
     // kernel rows received by rank 0 (staged by the last rank) with four ranks
     L.ar = ((L.xm + 2 * 8 * MT * 8 + 127) / 128) * 128;
     L.sst = L.ar + (npc == 512 ? AR_BYTES : 0);  // [2][nown][SST] floats: per-step hand-off to the scoring warps
-    L.nz = L.sst + 2 * nown * SST * 4;           // [2][MT] float2: control noise, computed two steps ahead
-    L.xs = ((L.nz + 2 * MT * 8 + 127) / 128) * 128;
+    L.xs = ((L.sst + 2 * nown * SST * 4 + 127) / 128) * 128;
     L.al = L.xs + npc * 16;
     L.seg = L.al + npc * 8;                      // S float4
     L.il2 = L.seg + S * 16;                      // S floats
     L.obs = L.il2 + ((S + 3) / 4) * 16;          // O x 3 floats
     L.total = L.obs + O * 12;
     return L;
+}
+
+// Issue order of a rank's 4-chunk groups, shared by the producers and the MMA
+// warp: group 0 first (its MMAs initialise the accumulators), then the groups
+// holding the rank's GP-mean chunks [4 gm0, 4 gm1), then the rest, each part
+// ascending.  The mean share is thus complete, and on its way to the peers,
+// while the remaining groups are computed.  Returns the first chunk of the
+// i-th group.
+__device__ __forceinline__ int burst_chunk(int i, int gm0, int gm1) {
+    if (i == 0) return 0;
+    const int a0 = gm0 > 1 ? gm0 : 1;
+    const int nm = gm1 - a0 > 0 ? gm1 - a0 : 0;
+    if (i - 1 < nm) return GCH * (a0 + i - 1);
+    int g = i - nm;
+    if (g >= a0) g += nm;
+    return GCH * g;
+}
+// index of the group after which a rank's GP-mean share is complete (-1: the
+// rank sums no chunk of its own groups)
+__device__ __forceinline__ int last_mean_burst(int gm0, int gm1) {
+    if (gm1 <= gm0) return -1;
+    const int a0 = gm0 > 1 ? gm0 : 1;
+    return gm1 - a0 > 0 ? gm1 - a0 : 0;
 }
 
 __device__ __forceinline__ void bulk_copy(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
@@ -118,6 +146,11 @@ __device__ __forceinline__ uint64_t f2pack(float a, float b) {
 }
 __device__ __forceinline__ void f2unpack(uint64_t v, float& a, float& b) {
     asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ uint64_t f2add(uint64_t a, uint64_t b) {
+    uint64_t r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
 }
 __device__ __forceinline__ uint64_t f2sub(uint64_t a, uint64_t b) {
     uint64_t r;
@@ -210,6 +243,23 @@ __device__ __forceinline__ bool wait_cluster(uint64_t* bar, uint32_t parity, vol
     return true;
 }
 
+// The same, also giving up once another role of this CTA has aborted (the
+// scoring warps' wait for the variance partials).
+__device__ __forceinline__ bool wait_cluster_or_abort(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                                      unsigned int* err) {
+    if (try_wait_cluster(bar, parity)) return true;
+    const uint64_t t0 = tc::global_ns();
+    while (!try_wait_cluster(bar, parity)) {
+        if (*abort_flag) return false;
+        if (tc::global_ns() - t0 > kWaitNs) {
+            *abort_flag = 1;
+            if (err) atomicOr(err, 1u);
+            return false;
+        }
+    }
+    return true;
+}
+
 // named barrier over the 128 producer threads of one thread half (u = 0, 1)
 __device__ __forceinline__ void half_sync(int u) {
     asm volatile("bar.sync %0, 128;" ::"r"(1 + u) : "memory");
@@ -270,16 +320,15 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_cl(const RolloutArgs a, 
     uint64_t* xbar = tmem_free + 1;             // [2]
     uint64_t* st_full = xbar + 2;               // [2] post-step states handed to the scoring warps
     uint64_t* st_empty = st_full + 2;           // [2] ... and released by them
-    uint64_t* nz_full = st_empty + 2;           // [2] noise of a step, written by the scoring warps
-    uint64_t* ar_full = nz_full + 2;            // rank 0: the kernel rows copied in by the last rank
+    uint64_t* ar_full = st_empty + 2;           // rank 0: the kernel rows copied in by the last rank
     uint64_t* x_res = ar_full + 1;              // the training set copied in
+    uint64_t* qbar = x_res + 1;                 // [4] partial |V|^2 of the scored samples, by step mod 4
     uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + L.tslot);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + L.abort_flag);
     float* xq = reinterpret_cast<float*>(sm + L.xq);
     float2* xm = reinterpret_cast<float2*>(sm + L.xm);
     unsigned char* ar = sm + L.ar;
     float* sst = reinterpret_cast<float*>(sm + L.sst);
-    float2* nz = reinterpret_cast<float2*>(sm + L.nz);
     float4* xs_s = reinterpret_cast<float4*>(sm + L.xs);
     float4* al_s = reinterpret_cast<float4*>(sm + L.al);
     float4* seg_s = reinterpret_cast<float4*>(sm + L.seg);
@@ -318,6 +367,15 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_cl(const RolloutArgs a, 
         }
     }
     const int nch_p = rows_in ? nch - AR_CHUNKS : nch;   // chunks whose rows the producers write to TMEM
+    // the rank's GP-mean groups inside its own groups, and the burst that completes them
+    const int gm0 = mc0 / GCH, gm1 = (mc1 < nch_p ? mc1 : nch_p) / GCH;
+    // Rank 0 with four ranks sums no mean chunk; it sends its (empty) share
+    // after burst NSTAGE + 1 of its seven, whose wait for a free stage covers
+    // the MMAs of its second ring stage and of all stages issued before it,
+    // the stage of received rows included.  The last rank enters the next step
+    // (and overwrites its staging area and rank 0's received rows) only with
+    // every share in, so only once rank 0 has consumed those rows.
+    const int ilast = rows_in ? NSTAGE + 1 : last_mean_burst(gm0, gm1);
     const uint32_t bbytes = (uint32_t)cl.bytes[rank];
 
     if (tid == 0) {
@@ -335,10 +393,10 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_cl(const RolloutArgs a, 
         for (int i = 0; i < 2; ++i) {
             tc::mbar_init(st_full + i, 4);             // the four warps holding the writers
             tc::mbar_init(st_empty + i, NCOST / 32);
-            tc::mbar_init(nz_full + i, NCOST / 32);
         }
         tc::mbar_init(ar_full, 1);
         tc::mbar_init(x_res, 1);
+        for (int i = 0; i < 4; ++i) tc::mbar_init(qbar + i, 1);   // armed by the scoring warps
         *abort_flag = 0;
         tc::fence_mbar_init();
     }
@@ -367,7 +425,26 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_cl(const RolloutArgs a, 
         bulk_copy(xs_s, cl.xa, (uint32_t)(cl.npc * 16), x_res);
         bulk_copy(al_s, cl.xa + 4 * cl.npc, (uint32_t)(cl.npc * 8), x_res);
     }
-    // every CTA's barriers are initialised before any peer arrives on them
+    // The perturbed controls of the whole horizon (Alg. 1: nominal plus noise,
+    // clamped) do not depend on the state, so they are drawn here, while the
+    // resident share is in flight: rank r the samples m = r (mod CS) of all T
+    // steps, written to u~ in global memory, which every rank's producers then
+    // read a step ahead.  The cluster barrier below publishes them.
+    {
+        const int nown = MT / CS;
+        for (int i = tid; i < nown * a.T; i += THREADS) {
+            const int k = i / nown, m = (int)rank + CS * (i % nown);
+            const int s = tile * MT + m;
+            if (s >= a.K) continue;
+            const float2 e = control_eps((uint32_t)k, (uint32_t)s, a.it0, a.it1, a.key0, a.key1, a.sig_v, a.sig_w);
+            float2 uk;
+            uk.x = fminf(fmaxf(__ldg(a.U + 2 * k) + e.x, a.umin0), a.umax0);
+            uk.y = fminf(fmaxf(__ldg(a.U + 2 * k + 1) + e.y, a.umin1), a.umax1);
+            a.u_tilde[(size_t)k * a.K + s] = uk;
+        }
+    }
+    // every CTA's barriers are initialised before any peer arrives on them, and
+    // every rank's perturbed controls are visible to the whole cluster
     cluster_sync_all();
     const uint32_t taddr = *tslot;
 
@@ -404,11 +481,12 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_cl(const RolloutArgs a, 
                 }
                 tc::fence_after_sync();
             }
-            // stage order: the first (which initialises the accumulators), then
-            // the stage of received rows (they arrive early: the last rank computes
-            // them first), then the rest
+            // stage order: the producers' burst order (burst_chunk; its first
+            // group initialises the accumulators), with the stage of received
+            // rows second (they arrive early: the last rank computes them first)
             for (int si = 0; si < nch / GCH; ++si) {
-                const int c = !rows_in ? GCH * si : (si == 0 ? 0 : (si == 1 ? nch_p : GCH * (si - 1)));
+                const int c = !rows_in ? burst_chunk(si, gm0, gm1)
+                                       : (si == 1 ? nch_p : burst_chunk(si == 0 ? 0 : si - 1, gm0, gm1));
                 if (c >= nch_p) {
                     // the last stage from the rows the last rank copied in (upper
                     // slice alone: rank 0's last chunks are above nboth)
@@ -465,37 +543,73 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_cl(const RolloutArgs a, 
         // this warp's TMEM lanes 32 (warp % 4) .., at the A ring's first column
         const uint32_t a_lane = taddr + ((uint32_t)(32 * (warp & 3)) << 16) + A_COL;
         const int s_me = tile * MT + m;
-        const bool active = s_me < a.K;
-        const int s_q = active ? s_me : 0;
+        const int s_q = s_me < a.K ? s_me : 0;
         const int nown = MT / CS;              // samples scored by this rank
 
         float mu0 = a.x0[0], mu1 = a.x0[1], mu2 = a.x0[2], mu3 = a.x0[3], mu4 = a.x0[4];
         uint32_t n = 0;
-        // the perturbed control of step k (Alg. 1: nominal plus noise, clamped);
-        // the noise comes from the scoring warps, which compute it two steps
-        // ahead, and the control of step k + 1 is prepared while the MMAs of step
-        // k complete
-        auto control = [&](int kk) {
-            float2 e;
-            if (kk == 0) {
-                e = control_eps(0u, (uint32_t)s_q, a.it0, a.it1, a.key0, a.key1, a.sig_v, a.sig_w);
-            } else {
-                // step kk >= 1 in slot (kk - 1) & 1, its use (kk - 1) >> 1
-                wait_or_abort(nz_full + ((kk - 1) & 1), (uint32_t)((kk - 1) >> 1) & 1u, abort_flag, a.err);
-                e = nz[((kk - 1) & 1) * MT + m];
-            }
-            float2 uk;
-            uk.x = fminf(fmaxf(__ldg(a.U + 2 * kk) + e.x, a.umin0), a.umax0);
-            uk.y = fminf(fmaxf(__ldg(a.U + 2 * kk + 1) + e.y, a.umin1), a.umax1);
-            if (u == 0 && active && (m % CS) == (int)rank) a.u_tilde[(size_t)kk * a.K + s_me] = uk;
-            return uk;
-        };
-        float2 ut_next = control(0);
+        // the perturbed control of step kk, drawn before the horizon (plain
+        // loads: other ranks wrote it during this launch)
+        const float2* u_row = a.u_tilde + s_q;
+        float2 ut_next = u_row[0];
         wait_or_abort(x_res, 0u, abort_flag, a.err);     // the training set in shared memory
+
+        // This rank's partial |V_m|^2 of step kq, read once the MMAs of step kq
+        // have completed (the producers call it after the first burst of step
+        // kq + 1, and after the last step), and sent to the rank that scores
+        // sample m: slot (kq mod 4, rank, u) of its buffer, completing bytes on
+        // its barrier qbar[kq mod 4].  Freeing the accumulators lets the MMAs
+        // of step kq + 1 start.
+        auto read_q = [&](int kq) {
+            bool ok = wait_or_abort(pass_done, (uint32_t)kq & 1u, abort_flag, a.err);
+            ok = __all_sync(0xffffffffu, ok);    // tcgen05.ld is warp-collective
+            tc::fence_after_sync();
+            float qpart = 0.0f;
+            if (ok) {
+                // warp w reads TMEM lanes 32 (w % 4) ..; thread half u the 64
+                // columns of its slice: V = (hi.hi + lo.hi) + hi.lo
+                const uint32_t row = taddr + ((uint32_t)(32 * (warp & 3)) << 16);
+                const uint32_t c0 = (uint32_t)(64 * u), c1 = u ? 128u : 192u;
+                // (packed pairs of columns: four independent sums of two lanes each)
+                uint64_t p0 = 0ull, p1 = 0ull, p2 = 0ull, p3 = 0ull;
+#pragma unroll
+                for (int cc = 0; cc < 64; cc += 32) {
+                    float v[32], w[32];
+                    tc::tmem_ld32x2(row + c0 + (uint32_t)cc, row + c1 + (uint32_t)cc, v, w);
+#pragma unroll
+                    for (int i = 0; i < 32; i += 8) {
+                        const uint64_t x0 = f2add(f2pack(v[i], v[i + 1]), f2pack(w[i], w[i + 1]));
+                        const uint64_t x1 = f2add(f2pack(v[i + 2], v[i + 3]), f2pack(w[i + 2], w[i + 3]));
+                        const uint64_t x2 = f2add(f2pack(v[i + 4], v[i + 5]), f2pack(w[i + 4], w[i + 5]));
+                        const uint64_t x3 = f2add(f2pack(v[i + 6], v[i + 7]), f2pack(w[i + 6], w[i + 7]));
+                        p0 = f2fma(x0, x0, p0);
+                        p1 = f2fma(x1, x1, p1);
+                        p2 = f2fma(x2, x2, p2);
+                        p3 = f2fma(x3, x3, p3);
+                    }
+                }
+                float a0, a1, b0, b1, c0f, c1f, d0, d1;
+                f2unpack(p0, a0, a1);
+                f2unpack(p1, b0, b1);
+                f2unpack(p2, c0f, c1f);
+                f2unpack(p3, d0, d1);
+                qpart = ((a0 + a1) + (b0 + b1)) + ((c0f + c1f) + (d0 + d1));
+            }
+            tc::fence_before_sync();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(tmem_free);
+            const uint32_t owner = (uint32_t)(m % CS);
+            const int slot = ((kq & 3) * 2 * CS + 2 * (int)rank + u) * nown + m / CS;
+            st_async_f32(peer_addr(xq + slot, owner), qpart, peer_addr(qbar + (kq & 3), owner));
+        };
+
+        const int nbu = nch_p / BURST;
 
         for (int k = 0; k < a.T; ++k) {
             // ---------------- query ------------------------------------------------
             const float2 ut = ut_next;
+            // the next step's control, its load in flight during the bursts
+            if (k + 1 < a.T) ut_next = u_row[(size_t)(k + 1) * a.K];
             const float z0 = mu3 * a.zscale[0], z1 = mu4 * a.zscale[1];
             const float z2 = ut.x * a.zscale[2], z3 = ut.y * a.zscale[3];
 
@@ -565,7 +679,32 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_cl(const RolloutArgs a, 
                     bulk_copy_peer(peer_addr(ar + 2 * u * AR_CHUNK_BYTES, 0u), ar + 2 * u * AR_CHUNK_BYTES,
                                    2u * AR_CHUNK_BYTES, peer_addr(ar_full, 0u));
             }
-            for (int c = 0; c < nch_p; c += BURST) {    // nch_p is a multiple of 4 (and of BURST)
+            // the GP mean share goes to every rank (its own included) as soon as
+            // it is complete: slot (rank, u) of sample m in every rank's buffer,
+            // completing bytes on that rank's exchange barrier xbar[k & 1]
+            const int buf = k & 1;
+            if (tid == 0) tc::mbar_expect_tx(xbar + buf, (uint32_t)(CS * 2 * MT * 8));
+            auto send_mean = [&]() {
+                const int slot = (buf * 8 + 2 * (int)rank + u) * MT + m;
+                const float2 mm = make_float2(mv + cv, mw + cw);
+                for (int p = 0; p < CS; ++p)
+                    st_async_f32x2(peer_addr(xm + slot, (uint32_t)p), mm, peer_addr(xbar + buf, (uint32_t)p));
+            };
+            // the part of the step that needs no GP result (unicycle with velocity
+            // lag; the covariance recursion, which the mean never reads, runs in
+            // the scoring warps), computed during the bursts
+            float sn = 0.0f, cs = 1.0f, nX = 0.0f, nY = 0.0f, nT = 0.0f, nV0 = 0.0f, nW0 = 0.0f;
+            auto dynamics = [&]() {
+                sincosf(mu2, &sn, &cs);
+                nX = mu0 + a.dt * mu3 * cs;
+                nY = mu1 + a.dt * mu3 * sn;
+                nT = mu2 + a.dt * mu4;
+                nV0 = mu3 + a.kv * (ut.x - mu3);
+                nW0 = mu4 + a.kw * (ut.y - mu4);
+            };
+            if (ilast < 0) send_mean();
+            for (int bi = 0; bi < nbu; ++bi) {    // nch_p is a multiple of 4 (and of BURST)
+                const int c = burst_chunk(bi, gm0, gm1);
                 // the sample's two threads take alternate chunks of the burst:
                 // thread half u the chunks c + u and c + 2 + u, all 16 points each
                 uint64_t av[2][8];
@@ -602,86 +741,33 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_cl(const RolloutArgs a, 
                 __syncwarp();
                 if (lane == 0) mbar_arrive(a_full + st);
                 ++n;
+                // the previous step's variance partials, then this step's
+                // mean-free dynamics
+                if (bi == 0) {
+                    if (k > 0) read_q(k - 1);
+                    dynamics();
+                }
+                if (bi == ilast) send_mean();
             }
-            // ---------------- the part of the step that needs no GP result ---------
-            // (unicycle with velocity lag; the covariance recursion, which the mean
-            // never reads, runs in the scoring warps), while the MMAs finish
-            float sn, cs;
-            sincosf(mu2, &sn, &cs);
+            if (nch_p < BURST) {                         // (no burst in this rank's steps)
+                if (k > 0) read_q(k - 1);
+                dynamics();
+            }
             const float v_pre = mu3;
-            const float nX = mu0 + a.dt * mu3 * cs;
-            const float nY = mu1 + a.dt * mu3 * sn;
-            const float nT = mu2 + a.dt * mu4;
-            const float nV0 = mu3 + a.kv * (ut.x - mu3);
-            const float nW0 = mu4 + a.kw * (ut.y - mu4);
-            if (k + 1 < a.T) ut_next = control(k + 1);
-            // ---------------- this rank's partial |V_m|^2 -------------------------
-            bool ok = wait_or_abort(pass_done, (uint32_t)k & 1u, abort_flag, a.err);
-            ok = __all_sync(0xffffffffu, ok);    // tcgen05.ld is warp-collective
-            tc::fence_after_sync();
-            float qpart = 0.0f;
-            if (ok) {
-                // warp w reads TMEM lanes 32 (w % 4) ..; thread half u the 64
-                // columns of its slice: V = (hi.hi + lo.hi) + hi.lo
-                const uint32_t row = taddr + ((uint32_t)(32 * (warp & 3)) << 16);
-                const uint32_t c0 = (uint32_t)(64 * u), c1 = u ? 128u : 192u;
-#pragma unroll
-                for (int cc = 0; cc < 64; cc += 32) {
-                    float v[32], w[32];
-                    tc::tmem_ld32x2(row + c0 + (uint32_t)cc, row + c1 + (uint32_t)cc, v, w);
-                    float p0 = 0.0f, p1 = 0.0f, p2 = 0.0f, p3 = 0.0f;
-#pragma unroll
-                    for (int i = 0; i < 8; ++i) {
-                        const float x0 = v[i] + w[i], x1 = v[8 + i] + w[8 + i];
-                        const float x2 = v[16 + i] + w[16 + i], x3 = v[24 + i] + w[24 + i];
-                        p0 = fmaf(x0, x0, p0);
-                        p1 = fmaf(x1, x1, p1);
-                        p2 = fmaf(x2, x2, p2);
-                        p3 = fmaf(x3, x3, p3);
-                    }
-                    qpart += (p0 + p1) + (p2 + p3);
-                }
-            }
-            tc::fence_before_sync();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(tmem_free);
-            // ---------------- exchange between the ranks ---------------------------
-            // every producer thread sends (its |V_m|^2 partial, its GP mean share)
-            // to slot (rank, u) of sample m in every rank's buffer, its own
-            // included, as asynchronous stores that complete transaction bytes on
-            // the receiver's exchange barrier; no CTA barrier is needed
-            const int buf = k & 1;
-            if (tid == 0) tc::mbar_expect_tx(xbar + buf, (uint32_t)(CS * 2 * MT * 12));
-            {
-                const int slot = (buf * 8 + 2 * (int)rank + u) * MT + m;
-                const float2 mm = make_float2(mv + cv, mw + cw);
-                for (int p = 0; p < CS; ++p) {
-                    const uint32_t xb = peer_addr(xbar + buf, (uint32_t)p);
-                    st_async_f32(peer_addr(xq + slot, (uint32_t)p), qpart, xb);
-                    st_async_f32x2(peer_addr(xm + slot, (uint32_t)p), mm, xb);
-                }
-            }
+            // ---------------- the GP mean: every rank's shares -------------------------
             wait_cluster(xbar + buf, (uint32_t)(k >> 1) & 1u, abort_flag, a.err);
-            float qsum = 0.0f;
             float2 msum = make_float2(0.0f, 0.0f);
-            float pq[8];
             float2 pm[8];
 #pragma unroll
             for (int p = 0; p < 8; ++p)
-                if (p < 2 * CS) {
-                    pq[p] = xq[(buf * 8 + p) * MT + m];
-                    pm[p] = xm[(buf * 8 + p) * MT + m];
-                }
+                if (p < 2 * CS) pm[p] = xm[(buf * 8 + p) * MT + m];
 #pragma unroll
             for (int p = 0; p < 8; ++p)              // fixed order: identical on every rank
                 if (p < 2 * CS) {
-                    qsum += pq[p];
                     msum.x += pm[p].x;
                     msum.y += pm[p].y;
                 }
-            const float q = qsum * cl.qscale;
             const float mean_v = a.sf2 * msum.x, mean_w = a.sf2 * msum.y;
-            const float s = fmaxf(0.0f, a.sf2 - q);
 
             // ---------------- mean dynamics: add the GP mean -----------------------
             mu0 = nX; mu1 = nY; mu2 = nT; mu3 = nV0 + mean_v; mu4 = nW0 + mean_w;
@@ -697,38 +783,26 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_cl(const RolloutArgs a, 
                 if ((m % CS) == (int)rank) {
                     float* o = sstk + (m / CS) * SST;
                     o[0] = mu0; o[1] = mu1; o[2] = mu2; o[3] = mu3; o[4] = mu4;
-                    o[5] = v_pre; o[6] = sn; o[7] = cs; o[8] = s;
+                    o[5] = v_pre; o[6] = sn; o[7] = cs;
                 }
                 __syncwarp();
                 if (lane == 0) mbar_arrive(st_full + (k & 1));
             }
         }
+        // the variance partials of the last step
+        if (a.T > 0) read_q(a.T - 1);
     } else {
         // ======================= scoring warps (Eq. 10-16) ======================
         // One step behind the producers: the covariance recursion (Eq. 10) and
         // the chance-constrained cost of the samples this rank scores, RC lanes
         // per sample (2 with CS = 4, else 1; two passes of 64 samples with
-        // CS = 1).  Also the control noise of every sample, two steps ahead.
+        // CS = 1).  The GP variance of a step is summed here from the ranks'
+        // |V_m|^2 partials, which arrive during the producers' next step.
         const int nown = MT / CS;
         const int ct = tid - (NPROD + 32);
         const int RC = nown >= NCOST ? 1 : NCOST / nown;
         const int spp = NCOST / RC;                 // samples per pass
         const int cpart = ct % RC;
-        const uint32_t it0 = a.it0, it1 = a.it1;
-        // noise of step kk >= 1 (slot (kk - 1) & 1) for the samples ct and ct + 64
-        auto noise = [&](int kk) {
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int mm = ct + h * NCOST;
-                const int sq = tile * MT + mm < a.K ? tile * MT + mm : 0;
-                nz[((kk - 1) & 1) * MT + mm] =
-                    control_eps((uint32_t)kk, (uint32_t)sq, it0, it1, a.key0, a.key1, a.sig_v, a.sig_w);
-            }
-            __syncwarp();
-            if (lane == 0) mbar_arrive(nz_full + ((kk - 1) & 1));
-        };
-        // (the producers draw step 0's noise themselves)
-        if (a.T > 1) noise(1);
         float cost[2] = {0.0f, 0.0f};
         float Sg[2][15];                            // covariance upper triangles (sidx order)
 #pragma unroll
@@ -739,9 +813,10 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_cl(const RolloutArgs a, 
         for (int k = 0; k < a.T; ++k) {
             wait_or_abort(st_full + (k & 1), (uint32_t)(k >> 1) & 1u, abort_flag, a.err);
             __syncwarp();
-            // the slot of step k + 2 held step k's noise, which the producers read
-            // during step k - 1, before they handed step k over
-            if (k + 2 < a.T) noise(k + 2);
+            // the variance partials of step k (2 CS per scored sample) arrive on
+            // qbar[k & 3] while the next step's kernel rows are computed; one
+            // local arrival carries the expected bytes
+            if (ct == 0) tc::mbar_expect_tx(qbar + (k & 3), (uint32_t)(2 * MT * 4));
             const float* sstk = sst + (k & 1) * nown * SST;
 #pragma unroll
             for (int js = 0; js < 2; ++js) {
@@ -753,9 +828,11 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_cl(const RolloutArgs a, 
                 const float* o = sstk + ci * SST;
                 const float px = o[0], py = o[1];
                 // Eq. 10: Sigma' = A Sigma A^T + diag(0, 0, 0, s, s), A the Jacobian
-                // of the unicycle step at the pre-step state
+                // of the unicycle step at the pre-step state (s is added below, once
+                // the variance partials are in: the position block read by the
+                // constraints does not depend on it)
                 {
-                    const float vp = o[5], sn = o[6], cs = o[7], sv = o[8];
+                    const float vp = o[5], sn = o[6], cs = o[7];
                     const float a02 = -a.dt * vp * sn, a03 = a.dt * cs;
                     const float a12 = a.dt * vp * cs, a13 = a.dt * sn;
                     float* S = Sg[js];
@@ -782,9 +859,9 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_cl(const RolloutArgs a, 
                     S[9] = B22 + a.dt * B24;
                     S[10] = a.av * B23;
                     S[11] = a.aw * B24;
-                    S[12] = a.av * B33 + sv;
+                    S[12] = a.av * B33;
                     S[13] = a.aw * B34;
-                    S[14] = a.aw * B44 + sv;
+                    S[14] = a.aw * B44;
                 }
                 float sxx = Sg[js][0], sxy = Sg[js][1], syy = Sg[js][5];
                 if (a.nom_sxy) {
@@ -833,11 +910,18 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_cl(const RolloutArgs a, 
                     om = fminf(om, __shfl_xor_sync(0xffffffffu, om, o2));
                     best = fminf(best, __shfl_xor_sync(0xffffffffu, best, o2));
                 }
+                // GP variance s = sf2 - |V_m|^2, the partials summed in a fixed order
+                wait_cluster_or_abort(qbar + (k & 3), (uint32_t)(k >> 2) & 1u, abort_flag, a.err);
+                float qsum = 0.0f;
+                for (int p = 0; p < 2 * CS; ++p) qsum += xq[((k & 3) * 2 * CS + p) * nown + ci];
+                const float sv = fmaxf(0.0f, a.sf2 - qsum * cl.qscale);
+                Sg[js][12] += sv;
+                Sg[js][14] += sv;
                 if (cpart == 0) {
                     const float omargin = om, e2min = best;
                     const float e_lane = sqrtf(e2min);
                     const float rbar = a.r - a.sq_chi2 * sqrtf(lmax);
-                    const float sv = o[8], vv = o[3];
+                    const float vv = o[3];
                     float stage = a.c_var * (sv + sv) + a.c_speed * (a.v_des - vv) * (a.v_des - vv);
                     if (omargin <= 0.0f) stage += a.c_coll;
                     const float lmargin = e_lane - rbar;
