@@ -180,21 +180,18 @@ template <int FMT>
 __device__ __forceinline__ void split2(uint64_t ab, uint32_t* hi, uint32_t* lo) {
     float a, b;
     f2unpack(ab, a, b);
+    float ra, rb;
     if (FMT == 0) {
         const __half2 h = __floats2half2_rn(a, b);
-        const float2 hf = __half22float2(h);
-        float ra, rb;
-        f2unpack(f2sub(ab, f2pack(hf.x, hf.y)), ra, rb);
-        const __half2 l = __floats2half2_rn(ra, rb);
         *hi = *reinterpret_cast<const uint32_t*>(&h);
+        tc::split_resid<0>(*hi, a, b, ra, rb);
+        const __half2 l = __floats2half2_rn(ra, rb);
         *lo = *reinterpret_cast<const uint32_t*>(&l);
     } else {
         const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
-        const float2 hf = __bfloat1622float2(h);
-        float ra, rb;
-        f2unpack(f2sub(ab, f2pack(hf.x, hf.y)), ra, rb);
-        const __nv_bfloat162 l = __floats2bfloat162_rn(ra, rb);
         *hi = *reinterpret_cast<const uint32_t*>(&h);
+        tc::split_resid<1>(*hi, a, b, ra, rb);
+        const __nv_bfloat162 l = __floats2bfloat162_rn(ra, rb);
         *lo = *reinterpret_cast<const uint32_t*>(&l);
     }
 }

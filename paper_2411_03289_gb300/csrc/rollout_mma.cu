@@ -83,17 +83,18 @@ __device__ __forceinline__ void bulk_copy(void* dst, const void* src, uint32_t b
 // hi/lo split of two values into packed 16-bit pairs (element a in the low half)
 template <int FMT>
 __device__ __forceinline__ void split2(float a, float b, uint32_t* hi, uint32_t* lo) {
+    float ra, rb;
     if (FMT == 0) {
         const __half2 h = __floats2half2_rn(a, b);
-        const float2 hf = __half22float2(h);
-        const __half2 l = __floats2half2_rn(a - hf.x, b - hf.y);
         *hi = *reinterpret_cast<const uint32_t*>(&h);
+        tc::split_resid<0>(*hi, a, b, ra, rb);
+        const __half2 l = __floats2half2_rn(ra, rb);
         *lo = *reinterpret_cast<const uint32_t*>(&l);
     } else {
         const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
-        const float2 hf = __bfloat1622float2(h);
-        const __nv_bfloat162 l = __floats2bfloat162_rn(a - hf.x, b - hf.y);
         *hi = *reinterpret_cast<const uint32_t*>(&h);
+        tc::split_resid<1>(*hi, a, b, ra, rb);
+        const __nv_bfloat162 l = __floats2bfloat162_rn(ra, rb);
         *lo = *reinterpret_cast<const uint32_t*>(&l);
     }
 }

@@ -246,6 +246,24 @@ __device__ __forceinline__ void tmem_ld32x2(uint32_t taddr0, uint32_t taddr1, fl
 }
 
 // ---- mbarrier / TMA ---------------------------------------------------------
+// Residuals of a hi/lo split: (a - hi0, b - hi1) for the packed 16-bit pair
+// hb = (hi0, hi1) (FP16 for FMT 0, BF16 for FMT 1), each from one
+// mixed-precision fma hi * (-1) + a with the 16-bit operand taken as is (no
+// conversion of hi back to FP32); exact when hi is a or a's rounding.
+template <int FMT>
+__device__ __forceinline__ void split_resid(uint32_t hb, float a, float b, float& ra, float& rb) {
+    if (FMT == 0)
+        asm("{\n\t.reg .b16 h0, h1;\n\tmov.b32 {h0, h1}, %2;\n\t"
+            "fma.rn.f32.f16 %0, h0, %4, %3;\n\tfma.rn.f32.f16 %1, h1, %4, %5;\n\t}"
+            : "=f"(ra), "=f"(rb)
+            : "r"(hb), "f"(a), "h"((unsigned short)0xBC00u), "f"(b));
+    else
+        asm("{\n\t.reg .b16 h0, h1;\n\tmov.b32 {h0, h1}, %2;\n\t"
+            "fma.rn.f32.bf16 %0, h0, %4, %3;\n\tfma.rn.f32.bf16 %1, h1, %4, %5;\n\t}"
+            : "=f"(ra), "=f"(rb)
+            : "r"(hb), "f"(a), "h"((unsigned short)0xBF80u), "f"(b));
+}
+
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
 }
