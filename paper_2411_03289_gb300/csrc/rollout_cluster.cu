@@ -83,9 +83,9 @@ __host__ __device__ inline ClLayout cl_layout(int npc, int S, int O) {
     ClLayout L;
     L.b = 0;
     // a_full, empty [NSTAGE], b_res, pass_done, tmem_free, xbar[2], st_full[2], st_empty[2],
-    // ar_full, x_res, qbar[4]
+    // ar_full, x_res, qbar[4], ar_free
     L.bars = B_MAX;
-    L.tslot = L.bars + 8 * (2 * NSTAGE + 15);
+    L.tslot = L.bars + 8 * (2 * NSTAGE + 16);
     L.abort_flag = L.tslot + 4;
     // received partial |V|^2 of the samples this rank scores,
     // [4 (step mod 4)][2 CS (sending rank, thread half)][nown] floats, and the
@@ -320,6 +320,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_cl(const RolloutArgs a, 
     uint64_t* ar_full = st_empty + 2;           // rank 0: the kernel rows copied in by the last rank
     uint64_t* x_res = ar_full + 1;              // the training set copied in
     uint64_t* qbar = x_res + 1;                 // [4] partial |V|^2 of the scored samples, by step mod 4
+    uint64_t* ar_free = qbar + 4;               // last rank: rank 0's MMAs have consumed the copied rows
     uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + L.tslot);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + L.abort_flag);
     float* xq = reinterpret_cast<float*>(sm + L.xq);
@@ -366,13 +367,9 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_cl(const RolloutArgs a, 
     const int nch_p = rows_in ? nch - AR_CHUNKS : nch;   // chunks whose rows the producers write to TMEM
     // the rank's GP-mean groups inside its own groups, and the burst that completes them
     const int gm0 = mc0 / GCH, gm1 = (mc1 < nch_p ? mc1 : nch_p) / GCH;
-    // Rank 0 with four ranks sums no mean chunk; it sends its (empty) share
-    // after burst NSTAGE + 1 of its seven, whose wait for a free stage covers
-    // the MMAs of its second ring stage and of all stages issued before it,
-    // the stage of received rows included.  The last rank enters the next step
-    // (and overwrites its staging area and rank 0's received rows) only with
-    // every share in, so only once rank 0 has consumed those rows.
-    const int ilast = rows_in ? NSTAGE + 1 : last_mean_burst(gm0, gm1);
+    // (rank 0 with four ranks sums no mean chunk and sends its empty share at
+    // the start of the step)
+    const int ilast = last_mean_burst(gm0, gm1);
     const uint32_t bbytes = (uint32_t)cl.bytes[rank];
 
     if (tid == 0) {
@@ -394,6 +391,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_cl(const RolloutArgs a, 
         tc::mbar_init(ar_full, 1);
         tc::mbar_init(x_res, 1);
         for (int i = 0; i < 4; ++i) tc::mbar_init(qbar + i, 1);   // armed by the scoring warps
+        tc::mbar_init(ar_free, 1);                      // one arrival per step, from rank 0's tensor pipe
         *abort_flag = 0;
         tc::fence_mbar_init();
     }
@@ -497,6 +495,9 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_cl(const RolloutArgs a, 
                                             dAr + (uint64_t)(AR_CHUNK_BYTES >> 4),
                                             dAr + (uint64_t)((3 * AR_CHUNK_BYTES) >> 4),
                                             (uint64_t)((AR_CHUNK_BYTES / 2) >> 4), b0, 4096 >> 4, idesc128, idesc64);
+                    // tell the last rank when these MMAs have read the rows: it may
+                    // then overwrite its staging area and this buffer
+                    tc::mma_commit_mc_elect(ar_free, (uint16_t)(1u << (CS - 1)));
                     continue;
                 }
                 const int st = (int)(n % NSTAGE);
@@ -654,7 +655,9 @@ __global__ void __launch_bounds__(THREADS, 1) k_rollout_cl(const RolloutArgs a, 
             if (rows_out) {
                 // rank 0's last four chunks: rows (and their GP-mean terms) into this
                 // CTA's staging area, then one bulk copy per thread half into rank
-                // 0's shared memory (chunk positions 0, 1 for u = 0, 2, 3 for u = 1)
+                // 0's shared memory (chunk positions 0, 1 for u = 0, 2, 3 for u = 1),
+                // once rank 0's MMAs have consumed the previous step's copy
+                if (k > 0) wait_cluster_or_abort(ar_free, (uint32_t)(k - 1) & 1u, abort_flag, a.err);
 #pragma unroll
                 for (int j = 0; j < 2; ++j) {
                     const int cc = me0 + 2 * j + u;

@@ -95,6 +95,19 @@ __device__ __forceinline__ void mma_commit_elect(uint64_t* bar) {
         : "memory");
 }
 
+// The same commit arriving on the mbarrier at bar's offset in every CTA of
+// the cluster whose bit is set in cta_mask (not in this CTA unless its bit is
+// set): a peer learns that this CTA's earlier MMAs have completed.
+__device__ __forceinline__ void mma_commit_mc_elect(uint64_t* bar, uint16_t cta_mask) {
+    asm volatile(
+        "{\n\t.reg .pred e;\n\t"
+        "elect.sync _|e, 0xffffffff;\n\t"
+        "@e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;\n\t}" ::"r"(
+            smem_addr(bar)),
+        "h"(cta_mask)
+        : "memory");
+}
+
 // One ring stage of four 16-point chunks, A from tensor memory: for chunk
 // j = 0 .. 3 the products A_hi,j x B_j (instruction descriptor i_hi) and
 // A_lo,j x B_j (i_lo), all into d_tmem, then the commit that arrives on bar
