@@ -163,9 +163,12 @@ __device__ __forceinline__ void update_body(const UpdateArgs& a, int cta, int n_
     }
 }
 
+// gridDim.y step blocks of UPD_STEPS steps (one block of all T steps when
+// gridDim.y == 1)
 __global__ void __launch_bounds__(UPD_THREADS) k_update(const UpdateArgs a) {
-    const int k_lo = blockIdx.y * UPD_STEPS;
-    update_body(a, blockIdx.x, gridDim.x, k_lo, min(a.T, k_lo + UPD_STEPS), gridDim.x * gridDim.y, nullptr);
+    const int tb = gridDim.y == 1 ? a.T : UPD_STEPS;
+    const int k_lo = blockIdx.y * tb;
+    update_body(a, blockIdx.x, gridDim.x, k_lo, min(a.T, k_lo + tb), gridDim.x * gridDim.y, nullptr);
 }
 
 // Many controllers: CTA i serves CTA items[i].y of controller items[i].x,
@@ -288,8 +291,11 @@ __global__ void __launch_bounds__(NOM_THREADS) k_nominal(const RolloutArgs a, co
 }  // namespace
 
 int launch_update(const UpdateArgs& a, int n_cta, cudaStream_t st) {
-    // (T = 0: one step block, no steps; the last CTA still writes nothing)
-    const int nstep = a.T > 0 ? (a.T + UPD_STEPS - 1) / UPD_STEPS : 1;
+    // Every CTA reduces all K costs itself, so the step blocks multiply that
+    // work: they are used while there are at most 64 sample blocks (K <= 16384);
+    // beyond, one CTA per sample block covers all T steps.  (T = 0: one step
+    // block, no steps; the last CTA still writes nothing.)
+    const int nstep = (a.T > 0 && n_cta <= 64) ? (a.T + UPD_STEPS - 1) / UPD_STEPS : 1;
     k_update<<<dim3(n_cta, nstep), UPD_THREADS, 0, st>>>(a);
     GPM_CUDA(cudaGetLastError());
     return GPMPPI_OK;

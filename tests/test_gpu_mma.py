@@ -212,3 +212,23 @@ def test_cluster_kernel_scene_in_global_memory(lib):
     ro = O.rollout(sc, fits, sc.x0, sc.U0, 1)
     tr = gpu_trace(lib, ctrl, sc, sc.x0, sc.U0, it=1)
     check_trace(sc, ro, tr)
+
+
+@pytest.mark.parametrize("K", [16384, 16700])
+def test_update_sample_block_counts(lib, K):
+    """The update with 64 sample blocks (step blocks of 16 steps: 64 x 2 CTAs)
+    and with 66 (one CTA per sample block over all steps, the last block
+    ragged): weights against Alg. 1's softmax of the returned costs, U_new
+    against the weighted sum over the oracle's perturbed controls."""
+    sc = _sc("small", 2, K=K, N=100, T=20)
+    P = sc.params
+    g, ctrl = make_ctrl(lib, sc)
+    U_new, w, c = gpu_step(lib, ctrl, sc, sc.x0, sc.U0, it=3)
+    assert np.all(np.isfinite(c))
+    assert np.max(np.abs(w - O.mppi_weights(c, P.lam))) <= 1e-5
+    ut = np.empty((P.K, P.T, 2))
+    for k in range(P.T):
+        eps = O.control_noise(P.seed, k, np.arange(P.K), 3, P.sigma)
+        ut[:, k] = np.clip(sc.U0[k] + eps, P.u_min, P.u_max)
+    U_chk = sc.U0 + np.einsum("s,skc->kc", w, ut - sc.U0[None])
+    assert np.max(np.abs(U_new - U_chk)) <= TOL_U
