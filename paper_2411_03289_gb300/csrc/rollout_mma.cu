@@ -448,7 +448,7 @@ __device__ __forceinline__ void rollout_mma_body(const RolloutArgs& a, const Mma
         const float rbar = a.r - a.sq_chi2 * sqrtf(lmax);
         float om = FLT_MAX;
         for (int o = u; o < a.O; o += R) {
-            const float cx = obsp[3 * o], cy = obsp[3 * o + 1], R = obsp[3 * o + 2];
+            const float cx = obsp[3 * o], cy = obsp[3 * o + 1], rad = obsp[3 * o + 2];
             const float dx = mu0 - cx, dy = mu1 - cy;
             const float rho = sqrtf(dx * dx + dy * dy);
             float spread;
@@ -458,7 +458,7 @@ __device__ __forceinline__ void rollout_mma_body(const RolloutArgs& a, const Mma
             } else {
                 spread = sqrtf(lmax);
             }
-            om = fminf(om, (rho - R) - a.phi_inv * spread);
+            om = fminf(om, (rho - rad) - a.phi_inv * spread);
         }
         // ---------------- P5: lane distance (segments split by half) -------
         float best = FLT_MAX;
