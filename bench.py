@@ -178,7 +178,7 @@ def _cpu_child(rows, reps, workload=WORKLOAD):
     for r in range(reps):
         O.rollout(sc, fits, sc.x0, sc.U0, r, samples=samples)
     dt = time.perf_counter() - t0
-    print(json.dumps({"seconds": dt, "sample_steps": rows * sc.params.T * reps}))
+    print(json.dumps({"seconds": dt, "sample_steps": rows * sc.params.T * reps, "T": sc.params.T}))
 
 
 def cpu_baseline(rows=CPU_SAMPLE_ROWS, reps=8, workload=WORKLOAD):
@@ -196,7 +196,7 @@ def cpu_baseline(rows=CPU_SAMPLE_ROWS, reps=8, workload=WORKLOAD):
     d = json.loads(line[-1])
     return {"value": d["sample_steps"] / d["seconds"], "unit": "sample-steps/s", "cores": cores,
             "kind": "oracle",
-            "sample": f"FP64 numpy oracle, {rows} of the K samples x T={50} steps x {reps} iterations "
+            "sample": f"FP64 numpy oracle, {rows} of the K samples x T={d['T']} steps x {reps} iterations "
                       f"({d['seconds']:.1f} s), BLAS threads = {cores}"}
 
 
