@@ -86,6 +86,33 @@ def dist_env():
     return ws, rank, local
 
 
+def slowest_rank(*values):
+    """Element-wise maximum over all ranks of this rank's per-rank figures
+    (times): the replicas are independent, so the job takes as long as its
+    slowest rank.  Without a process group the values come back unchanged.
+    Under NCCL the reduction runs on the current CUDA device, under gloo on
+    the CPU."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return tuple(float(v) for v in values)
+    dev = (torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl"
+           else torch.device("cpu"))
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return tuple(float(x) for x in t.tolist())
+
+
+def replica_throughput(units_per_rank, seconds_per_rank):
+    """Whole-job throughput of independent replicas (no data-path
+    collective): the units all ranks processed over the slowest rank's time.
+    Returns (throughput, slowest time)."""
+    import torch.distributed as dist
+    ws = dist.get_world_size() if dist.is_available() and dist.is_initialized() else 1
+    (t,) = slowest_rank(seconds_per_rank)
+    return units_per_rank * ws / t, t
+
+
 # ---------------------------------------------------------------------------
 # clocks during the timed region
 # ---------------------------------------------------------------------------
@@ -346,11 +373,9 @@ def run_ours(args):
     clocks = ClockSampler(torch.cuda.current_device())
     step_ms, rollout_ms, update_ms, t_wall, clk = timed_steps(gp, ctrl, x0, U, U_new, w, c, flush, stream,
                                                              args.steps, args.warmup, barrier, clocks)
-    tot_ms = sum(step_ms)
-    if ws > 1:
-        t = torch.tensor([tot_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        tot_ms = float(t.item())
+    # whole-job throughput: every rank's sample-steps over the slowest rank's time
+    value, tot_s = replica_throughput(P.K * P.T * args.steps, sum(step_ms) / 1e3)
+    tot_ms = 1e3 * tot_s
     gp.mppi_set_profiling(ctrl, False)
 
     # ---- end to end through the ABI with host buffers -----------------------
@@ -372,15 +397,10 @@ def run_ours(args):
         out_host.copy_(U_new, non_blocking=True)
         torch.cuda.synchronize()             # the controller needs U_new[0] on the host
         e2e_s += time.perf_counter() - t0
-    if ws > 1:
-        t = torch.tensor([e2e_s], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    (e2e_s,) = slowest_rank(e2e_s)
     h2d = U_host.numel() * 4 + 5 * 4
     d2h = out_host.numel() * 4
 
-    units = P.K * P.T * args.steps * ws
-    value = units / (tot_ms / 1e3)
     S_seg = max(sc.path.shape[0] - 1, 1)
     if terrain:
         flops = sum(rollout_flops_per_sample_step(X.shape[0], sc.obstacles.shape[0], S_seg)
@@ -431,7 +451,8 @@ def run_ours(args):
         "kernel_ms": {"rollout_avg": r_avg, "update_avg": sum(update_ms) / len(update_ms)},
         "roofline": roof,
         "cpu_baseline": cpu_baseline(workload=args.workload) if (rank == 0 and ws == 1 and not args.no_cpu) else None,
-        "e2e": {"value": units / e2e_s, "unit": "sample-steps/s", "h2d_bytes_per_step": h2d,
+        "e2e": {"value": P.K * P.T * args.steps * ws / e2e_s, "unit": "sample-steps/s",
+                "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "clocks": clk,
         "fp32_path": fp32,
@@ -572,10 +593,7 @@ def run_grad(args):
         if i >= 3:
             e2e_s += time.perf_counter() - t0
     n_e2e = max(3, args.steps // 4)
-    if ws > 1:
-        t = torch.tensor([tot_ms, e2e_s], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        tot_ms, e2e_s = float(t[0].item()), float(t[1].item())
+    tot_ms, e2e_s = slowest_rank(tot_ms, e2e_s)
     if rank != 0:
         if ws > 1:
             torch.distributed.destroy_process_group()
@@ -688,10 +706,7 @@ def run_batched(args):
             stream.synchronize()
             e2e_s += time.perf_counter() - t0
     tot_ms = sum(step_ms)
-    if ws > 1:
-        t = torch.tensor([tot_ms, e2e_s], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        tot_ms, e2e_s = float(t[0].item()), float(t[1].item())
+    tot_ms, e2e_s = slowest_rank(tot_ms, e2e_s)
     units_step = sum(sc.params.K * sc.params.T for sc in scs)
     flops_step = sum(rollout_flops_per_sample_step(sc.N, sc.obstacles.shape[0], max(sc.path.shape[0] - 1, 1))
                      * sc.params.K * sc.params.T for sc in scs)
