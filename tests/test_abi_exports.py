@@ -115,3 +115,16 @@ def test_struct_layouts_match_header(tmp_path):
         cls = mirror[st]
         got = ctypes.sizeof(cls) if name == "size" else getattr(cls, name).offset
         assert got == int(val), (st, name, got, val)
+
+
+def test_binding_has_no_cpu_fallback(tmp_path, monkeypatch):
+    """The binding fails loudly instead of computing anything itself: a
+    missing library raises at load(), and host (CPU) tensors are refused
+    before any call into the library."""
+    import torch
+    monkeypatch.setattr(gp, "_lib", None)
+    monkeypatch.setattr(gp, "LIB_PATH", str(tmp_path / "libgpmppi_missing.so"))
+    with pytest.raises(RuntimeError, match="not built"):
+        gp.load()
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        gp._dptr(torch.zeros(4), name="U_nom")
