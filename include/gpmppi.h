@@ -118,7 +118,8 @@ int gp_fit(const double* X, const double* Y, int32_t N, const gpmppi_hyper hyper
 /* Release a GP handle.  A controller created from it must be destroyed first. */
 int gp_destroy(gpmppi_gp gp);
 
-/* Copy the FP64 factors of output j (0 or 1) to the host:
+/* Copy the FP64 factors of output j (0 or 1) to the host (the Cholesky
+ * quantities of Sec. III-A that the GP mean and variance are formed from):
  *   Linv  host, N x N doubles, lower triangular L_j^-1 (upper part zero); may be NULL
  *   alpha host, N doubles, K_j^-1 Y[:,j]; may be NULL
  * Blocking. */
@@ -132,7 +133,9 @@ int gp_factors(gpmppi_gp gp, int32_t j, double* Linv, double* alpha);
  * FP32 arithmetic on the FP32 factors. */
 int gp_predict(gpmppi_gp gp, const float* Z, int32_t M, float* mean, float* var, void* stream);
 
-/* Create a controller for one robot.
+/* Create a controller for one robot.  The radius tightening factors of the
+ * chance constraints (Eq. 13-16: sqrt(chi^2_2(p_x)) for the lane, Phi^-1(p_x)
+ * for obstacles) are computed here in double.
  *   p          host, parameters (validated; copied)
  *   obstacles  host, O x 3 floats (centre x, centre y, radius > 0); NULL if O = 0
  *   path       host, P x 2 floats, lane-centre polyline (P >= 1); copied
@@ -158,8 +161,10 @@ int mppi_create(const gpmppi_params* p, const float* obstacles, int32_t O, const
 int mppi_step(gpmppi_ctrl c, const float state[5], const float* U_nom, float* U_new,
               float* weights, float* costs, void* stream);
 
-/* The rollout of mppi_step for the current iteration, recording every
- * sample's trajectory (does not update U and does not advance the counter):
+/* The rollout of mppi_step for the current iteration (Alg. 1 Step 1),
+ * recording every sample's trajectory: the mean and covariance of Eq. 6 and
+ * Eq. 10 and the stage costs and margins of Eq. 11-16 (does not update U and
+ * does not advance the counter):
  *   mu      device, K x T x 5 floats: state after step k (mu(k+1)), or NULL
  *   sigma   device, K x T x 15 floats: upper triangle of Sigma(k+1), row by row
  *           (00,01,02,03,04,11,12,13,14,22,23,24,33,34,44), or NULL
@@ -275,7 +280,8 @@ int mppi_grad(gpmppi_ctrl c, const float state[5], const float* U_nom, const flo
  * start-up (cudaMalloc may synchronise the device and has no latency bound),
  * or a framework that owns all device memory and forbids plug-ins from
  * allocating.  This call runs the same softmax weights and control update as
- * mppi_step's second kernel, with its scratch (per-CTA partial sums and a
+ * mppi_step's second kernel (Alg. 1: w_s = exp(-(S_s - rho)/lambda) / Z with
+ * rho = min_s S_s, then the weighted sum of the perturbations), with its scratch (per-CTA partial sums and a
  * completion ticket) in a fixed static device array of 512 KiB that every
  * GPU loading the library holds until the process exits.  It allocates
  * nothing.
