@@ -281,10 +281,10 @@ int mppi_grad(gpmppi_ctrl c, const float state[5], const float* U_nom, const flo
  * or a framework that owns all device memory and forbids plug-ins from
  * allocating.  This call runs the same softmax weights and control update as
  * mppi_step's second kernel (Alg. 1: w_s = exp(-(S_s - rho)/lambda) / Z with
- * rho = min_s S_s, then the weighted sum of the perturbations), with its scratch (per-CTA partial sums and a
- * completion ticket) in a fixed static device array of 512 KiB that every
- * GPU loading the library holds until the process exits.  It allocates
- * nothing.
+ * rho = min_s S_s, then the weighted sum of the perturbations), with its
+ * scratch (per-CTA partial sums, per-block softmax statistics and a
+ * completion ticket) in a fixed static device array of 1 MiB that every GPU
+ * loading the library holds until the process exits.  It allocates nothing.
  *   costs    device, K floats: the samples' total costs S_s
  *   u_tilde  device, T x K x 2 floats, step-major: the clamped sampled
  *            controls u~ of sample s at step k at [(k*K + s)*2 + {0,1}]

@@ -154,10 +154,14 @@ def _dptr(t, dtype=None, numel=None, name="array"):
     """Data pointer of a contiguous CUDA tensor (None -> NULL)."""
     if t is None:
         return None
-    if not t.is_cuda or not t.is_contiguous():
-        raise ValueError(f"{name} must be a contiguous CUDA tensor")
     if dtype is not None and t.dtype != dtype:
         raise ValueError(f"{name} must have dtype {dtype}")
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous CUDA tensor")
+    import torch
+    if t.device.index is not None and t.device.index != torch.cuda.current_device():
+        raise ValueError(f"{name} lives on {t.device}, not on the current device "
+                         f"cuda:{torch.cuda.current_device()}")
     if numel is not None and t.numel() < numel:
         raise ValueError(f"{name} needs at least {numel} elements")
     return ctypes.c_void_p(t.data_ptr())
@@ -459,12 +463,20 @@ def smoothed_rollout_cost(ctrl: Ctrl, state, U, lengthscale=None, slope=20.0, we
 def mppi_update_noalloc(costs, u_tilde, U_nom, U_new, weights, K: int, T: int, lam: float,
                         stream=None):
     """Weights and control update with no device allocation (for callers that
-    cannot allocate once running); u_tilde is (T, K, 2), step-major."""
-    _check(load().mppi_update_noalloc(_dptr(costs, numel=K, name="costs"),
-                                      _dptr(u_tilde, numel=2 * K * T, name="u_tilde"),
-                                      _dptr(U_nom, numel=2 * T, name="U_nom"),
-                                      _dptr(U_new, numel=2 * T, name="U_new"),
-                                      _dptr(weights, numel=K, name="weights"), K, T, float(lam),
+    cannot allocate once running); u_tilde is (T, K, 2), step-major.  Every
+    array is float32 on the current device (anything else raises ValueError
+    before the library is called)."""
+    import torch
+    f32 = torch.float32
+    for name, t in (("costs", costs), ("u_tilde", u_tilde), ("U_nom", U_nom), ("U_new", U_new),
+                    ("weights", weights)):
+        if t is not None and t.dtype != f32:
+            raise ValueError(f"{name} must have dtype {f32}")
+    _check(load().mppi_update_noalloc(_dptr(costs, f32, K, "costs"),
+                                      _dptr(u_tilde, f32, 2 * K * T, "u_tilde"),
+                                      _dptr(U_nom, f32, 2 * T, "U_nom"),
+                                      _dptr(U_new, f32, 2 * T, "U_new"),
+                                      _dptr(weights, f32, K, "weights"), K, T, float(lam),
                                       _stream(stream)))
 
 

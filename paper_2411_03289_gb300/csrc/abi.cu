@@ -30,6 +30,27 @@ int cuda_fail(cudaError_t e, const char* what) {
     return e == cudaErrorMemoryAllocation ? GPMPPI_ERR_OOM : GPMPPI_ERR_CUDA;
 }
 
+// Device (or managed) memory of the current device?
+int check_dev_ptr(const void* p, const char* name, bool nullable) {
+    if (p == nullptr) {
+        if (nullable) return GPMPPI_OK;
+        return fail(GPMPPI_ERR_INVALID_ARG, std::string(name) + " must not be NULL");
+    }
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(GPMPPI_ERR_INVALID_ARG, std::string(name) + " is not a CUDA pointer");
+    }
+    if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)
+        return fail(GPMPPI_ERR_INVALID_ARG, std::string(name) + " must be device memory");
+    int dev = 0;
+    GPM_CUDA(cudaGetDevice(&dev));
+    if (at.type == cudaMemoryTypeDevice && at.device != dev)
+        return fail(GPMPPI_ERR_INVALID_ARG, std::string(name) + " lives on another device");
+    return GPMPPI_OK;
+}
+
 }  // namespace gpm
 
 using namespace gpm;
@@ -58,27 +79,6 @@ double normal_quantile(double p) {
         if (below) lo = mid; else hi = mid;
     }
     return 0.5 * (lo + hi);
-}
-
-// Device (or managed) memory of the current device?
-int check_dev_ptr(const void* p, const char* name, bool nullable) {
-    if (p == nullptr) {
-        if (nullable) return GPMPPI_OK;
-        return fail(GPMPPI_ERR_INVALID_ARG, std::string(name) + " must not be NULL");
-    }
-    cudaPointerAttributes at;
-    cudaError_t e = cudaPointerGetAttributes(&at, p);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        return fail(GPMPPI_ERR_INVALID_ARG, std::string(name) + " is not a CUDA pointer");
-    }
-    if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)
-        return fail(GPMPPI_ERR_INVALID_ARG, std::string(name) + " must be device memory");
-    int dev = 0;
-    GPM_CUDA(cudaGetDevice(&dev));
-    if (at.type == cudaMemoryTypeDevice && at.device != dev)
-        return fail(GPMPPI_ERR_INVALID_ARG, std::string(name) + " lives on another device");
-    return GPMPPI_OK;
 }
 
 }  // namespace

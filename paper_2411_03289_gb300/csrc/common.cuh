@@ -88,6 +88,9 @@ __device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
 void set_error(const std::string& msg);
 int fail(int code, const std::string& msg);
 int cuda_fail(cudaError_t e, const char* what);
+// INVALID_ARG unless p is device (or managed) memory of the current device
+// (NULL is accepted when nullable).
+int check_dev_ptr(const void* p, const char* name, bool nullable);
 
 #define GPM_CUDA(call)                                      \
     do {                                                    \
@@ -318,7 +321,7 @@ struct UpdateArgs {
     const float* U;         // T x 2
     float* U_new;           // T x 2
     float* weights;         // K or null
-    float* partial;         // n_cta x T x 2 scratch
+    float* partial;         // n_cta x (T + 1) x 2 scratch: partial sums, then (rho_b, Z_b) per CTA
     unsigned int* counter;  // one scratch word, zero between launches
     int K, T;
     int per_cta;            // samples per CTA

@@ -16,9 +16,10 @@
 
 namespace {
 
-// ceil(K / 256) * T * 2 partial sums at most, plus one ticket word.
+// ceil(K / 256) * T * 2 partial sums at most, then two statistics per
+// sample block (at most 2 * 65536 floats), then one ticket word.
 constexpr int kNoallocPartials = 1 << 17;     // 512 KiB of floats
-constexpr int kNoallocFloats = kNoallocPartials + 64;
+constexpr int kNoallocFloats = 2 * kNoallocPartials + 64;   // 1 MiB + 256 B in all
 constexpr int kMaxDevices = 64;
 
 // Every GPU that loads the library holds this array until the process exits.
@@ -45,24 +46,9 @@ int scratch_for_current_device(DeviceScratch* out) {
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return gpm::cuda_fail(e, "mppi_update_noalloc: cudaGetSymbolAddress");
         g_scratch[dev].partial = static_cast<float*>(p);
-        g_scratch[dev].ticket = reinterpret_cast<unsigned int*>(static_cast<float*>(p) + kNoallocPartials);
+        g_scratch[dev].ticket = reinterpret_cast<unsigned int*>(static_cast<float*>(p) + 2 * kNoallocPartials);
     }
     *out = g_scratch[dev];
-    return GPMPPI_OK;
-}
-
-int check_device_array(const void* p, const char* name, bool nullable) {
-    if (!p) {
-        if (nullable) return GPMPPI_OK;
-        return gpm::fail(GPMPPI_ERR_INVALID_ARG, std::string("mppi_update_noalloc: ") + name + " is NULL");
-    }
-    cudaPointerAttributes at;
-    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
-        cudaGetLastError();
-        return gpm::fail(GPMPPI_ERR_INVALID_ARG, std::string("mppi_update_noalloc: ") + name + " is not a CUDA pointer");
-    }
-    if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)
-        return gpm::fail(GPMPPI_ERR_INVALID_ARG, std::string("mppi_update_noalloc: ") + name + " must be device memory");
     return GPMPPI_OK;
 }
 
@@ -75,24 +61,28 @@ extern "C" int mppi_update_noalloc(const float* costs, const float* u_tilde, con
     if (K < 1 || T < 1) return fail(GPMPPI_ERR_INVALID_ARG, "mppi_update_noalloc: K and T must be >= 1");
     if (!(lambda > 0.0f) || !std::isfinite(lambda))
         return fail(GPMPPI_ERR_INVALID_ARG, "mppi_update_noalloc: lambda must be finite and > 0");
-    const long long n_cta = (K + 255) / 256;
+    const long long n_cta = ((long long)K + 255) / 256;
     if (n_cta * (long long)T * 2 > kNoallocPartials || T > GPMPPI_MAX_T)
         return fail(GPMPPI_ERR_INVALID_ARG,
                     "mppi_update_noalloc: ceil(K/256) * T must not exceed 65536 (and T <= GPMPPI_MAX_T)");
     int rc;
-    if ((rc = check_device_array(costs, "costs", false))) return rc;
-    if ((rc = check_device_array(u_tilde, "u_tilde", false))) return rc;
-    if ((rc = check_device_array(U_nom, "U_nom", false))) return rc;
-    if ((rc = check_device_array(U_new, "U_new", false))) return rc;
-    if ((rc = check_device_array(weights, "weights", true))) return rc;
+    // device (or managed) memory of the current device: a host pointer or an
+    // array on another GPU is refused here instead of faulting in the kernel
+    if ((rc = check_dev_ptr(costs, "mppi_update_noalloc: costs", false))) return rc;
+    if ((rc = check_dev_ptr(u_tilde, "mppi_update_noalloc: u_tilde", false))) return rc;
+    if ((rc = check_dev_ptr(U_nom, "mppi_update_noalloc: U_nom", false))) return rc;
+    if ((rc = check_dev_ptr(U_new, "mppi_update_noalloc: U_new", false))) return rc;
+    if ((rc = check_dev_ptr(weights, "mppi_update_noalloc: weights", true))) return rc;
     if (U_new == U_nom) return fail(GPMPPI_ERR_INVALID_ARG, "mppi_update_noalloc: U_new must not alias U_nom");
     if (reinterpret_cast<uintptr_t>(u_tilde) & 7u)
         return fail(GPMPPI_ERR_INVALID_ARG, "mppi_update_noalloc: u_tilde must be 8-byte aligned");
     DeviceScratch sc;
     if ((rc = scratch_for_current_device(&sc))) return rc;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    // the ticket must start at zero; the partial sums are fully written by
-    // their CTAs before the last one reads them
+    // the ticket must start at zero; the partial sums and block statistics
+    // (ceil(K/256) * (T + 1) * 2 floats, within the array since
+    // ceil(K/256) * T <= 65536) are fully written by their CTAs before the
+    // last one reads them
     GPM_CUDA(cudaMemsetAsync(sc.ticket, 0, sizeof(unsigned int), st));
     UpdateArgs a;
     a.costs = costs;

@@ -33,24 +33,48 @@ def _noise_controls(sc, U, it):
     return ut
 
 
-def test_cfg2_full_step(lib):
-    sc = S.scenario("cfg2")
+_CFG2_FITS = {}
+
+
+def _cfg2_oracle(sc, U, it):
+    """The oracle's full cfg2 rollout (every sample), cached across the
+    precisions: the oracle does not depend on the GPU's arithmetic."""
+    key = (sc.params.seed, it, U.tobytes())
+    if key not in _CFG2_FITS:
+        fits = O.gp_fit(sc.X, sc.Y, sc.hyper)
+        _CFG2_FITS[key] = O.rollout(sc, fits, sc.x0, U, it)
+    return _CFG2_FITS[key]
+
+
+# FP32 CUDA-core rollout (0), FP16 hi/lo split (2, the benchmarked default) and
+# BF16 hi/lo split (1) on the 4-CTA cluster tensor-core rollout
+@pytest.mark.parametrize("precision", [0, 2, 1])
+def test_cfg2_full_step(lib, precision):
+    sc = S.scenario("cfg2", precision=precision)
     g, ctrl = make_ctrl(lib, sc)
+    kind = lib.mppi_rollout_kind(ctrl)
+    assert kind == (lib.GPMPPI_KERNEL_FP32 if precision == 0 else lib.GPMPPI_KERNEL_TC_CLUSTER)
     U_new, w, c = gpu_step(lib, ctrl, sc, sc.x0, sc.U0, it=0)
-    fits = O.gp_fit(sc.X, sc.Y, sc.hyper)
-    ro = O.rollout(sc, fits, sc.x0, sc.U0, 0)
+    ro = _cfg2_oracle(sc, sc.U0, 0)
     info = check_step(sc, ro, sc.U0, U_new, w, c)
-    print("cfg2 full step", info)
+    print("cfg2 full step precision", precision, info)
     assert info["n_alt"] <= 0.01 * sc.params.K
 
 
-def test_cfg2_sampled_trajectories(lib):
-    sc = S.scenario("cfg2")
+@pytest.mark.parametrize("precision", [0, 2, 1])
+def test_cfg2_sampled_trajectories(lib, precision):
+    """Per-(sample, step) means, covariances, margins and costs at the full
+    cfg2 size: rows from every one of the cluster kernel's 32 sample tiles
+    (128 samples each; first, last and interior rows), over the whole
+    50-step horizon."""
+    sc = S.scenario("cfg2", precision=precision)
     g, ctrl = make_ctrl(lib, sc)
     U = sc.U0.copy()
     U[:, 1] = 0.4 * np.sin(np.linspace(0, 3, sc.params.T))
     tr = gpu_trace(lib, ctrl, sc, sc.x0, U, it=3)
-    rows = _rows(sc.params.K)
+    K = sc.params.K
+    rows = np.union1d(_rows(K), np.concatenate([np.arange(0, K, 128), np.arange(127, K, 128),
+                                                np.arange(61, K, 128 * 4)]))
     fits = O.gp_fit(sc.X, sc.Y, sc.hyper)
     ro = O.rollout(sc, fits, sc.x0, U, 3, samples=rows)
     info = check_trace(sc, ro, tr, rows)
@@ -83,3 +107,55 @@ def test_large_shapes_sampled_and_properties(lib, name):
     assert np.max(np.abs(U_new - U_chk)) <= TOL_U
     assert np.all(U_new[:, 0] >= P.u_min[0] - 1e-6) and np.all(U_new[:, 0] <= P.u_max[0] + 1e-6)
     del torch
+
+
+def test_cfg2_closed_loop_200_steps(lib):
+    """Alg. 1's receding-horizon loop at the full cfg2 size (K=4096, T=50,
+    N=500, 16 obstacles, figure-eight) for 200 control steps against the
+    simulated plant (nominal model plus the synthetic residual), on the
+    benchmarked FP16-split cluster rollout.
+
+    Each step the GPU and the oracle see the same state (rounded to FP32, as
+    the ABI passes it), the same nominal controls and the same Philox
+    iteration.  Checked per step: the costs of sampled rows against the
+    oracle's FP64 rollout of those rows (indicator-tie protocol), the weights
+    against the softmax of the GPU's own costs, and U_new against the
+    weighted sum of the oracle's clamped sampled controls.  The plant then
+    applies U_new[0] and U is shifted (receding horizon)."""
+    sc = S.scenario("cfg2", precision=2)
+    P = sc.params
+    g, ctrl = make_ctrl(lib, sc)
+    assert lib.mppi_rollout_kind(ctrl) == lib.GPMPPI_KERNEL_TC_CLUSTER
+    fits = O.gp_fit(sc.X, sc.Y, sc.hyper)
+    rng = np.random.default_rng(11)
+    x = sc.x0.astype(np.float32).astype(np.float64)
+    U = sc.U0.astype(np.float32).astype(np.float64)
+    n_alt, err_u, err_w = 0, 0.0, 0.0
+    lane, travelled = [], 0.0
+    for t in range(200):
+        U_new, w, c = gpu_step(lib, ctrl, sc, x, U, it=t)
+        rows = np.sort(rng.choice(P.K, 6, replace=False))
+        ro = O.rollout(sc, fits, x, U, t, samples=rows)
+        ref_c, na = reconcile_costs(sc, ro, c[rows], rows)
+        assert_close(c[rows], ref_c, TOL_COST, what=f"step {t} costs")
+        n_alt += na
+        w_ref = O.mppi_weights(c, P.lam)
+        err_w = max(err_w, float(np.max(np.abs(w - w_ref))))
+        ut = _noise_controls(sc, U, t)
+        U_chk = U + np.einsum("s,skc->kc", w_ref, ut - U[None])
+        err_u = max(err_u, float(np.max(np.abs(U_new - U_chk))))
+        assert err_w <= 1e-5, f"step {t}: weights err {err_w:.3e}"
+        assert err_u <= TOL_U, f"step {t}: U_new err {err_u:.3e}"
+        x_next = O.mppi.plant_step(sc, x, U_new[0], S.true_residual).astype(np.float32).astype(np.float64)
+        travelled += float(np.hypot(*(x_next[:2] - x[:2])))
+        x = x_next
+        U = O.mppi.shift_controls(U_new)
+        lane.append(float(O.mppi.lane_distance(x[None, :2], sc.path)[0]))
+    print(f"cfg2 closed loop: 200 steps, weights err {err_w:.2e}, U_new err {err_u:.2e}, "
+          f"{n_alt} tie-resolved costs, travelled {travelled:.2f} m, "
+          f"max lane distance {max(lane):.3f} m, final state {x}")
+    assert n_alt <= 20
+    # the loop is a working controller: the plant advances along the path
+    # (10 s at about 1.5 m/s) and stays near its centreline
+    assert travelled > 5.0
+    assert max(lane) < 2.0 * sc.params.lane_half_width
