@@ -20,6 +20,7 @@ import hashlib
 import json
 import os
 import re
+import shutil
 import statistics
 import subprocess
 import sys
@@ -46,8 +47,56 @@ def rollout_flops_per_sample_step(N, O, S):
 
 
 def fp32_peak_tflops(sm_mhz=2070.0, n_sm=152):
-    """FP32 FMA pipe: 128 lanes per SM, 2 flops per FMA."""
+    """FP32 FMA pipe from unit counts: 128 lanes per SM, 2 flops per FMA (the
+    fallback when the probe cannot run)."""
     return n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def measure_alu_peaks(gp, dev, stream):
+    """Measured throughput of the FP32 FMA pipe (scalar and packed f32x2 FMA)
+    and of the SFU's ex2 on this GPU: the library's probe kernels, timed
+    with CUDA events on the launch stream after a warm-up launch, with the
+    SM clock sampled while they run."""
+    import torch
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    blocks = 8 * n_sm
+    out = torch.empty(blocks * 256, dtype=torch.float32, device=dev)
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    res = {}
+    clocks.begin()
+    for kind, name, iters in ((0, "fma", 600_000), (1, "fma_x2", 600_000), (2, "ex2", 60_000)):
+        gp.gpmppi_alu_probe(kind, blocks, 1000, out, stream)       # warm-up
+        ms = []
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            gp.gpmppi_alu_probe(kind, blocks, iters, out, stream)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        ops = blocks * 256 * iters * 16
+        res[name] = ops / (min(ms) / 1e3)
+    clocks.end()
+    clk = clocks.stop()
+    fma = max(res["fma"], res["fma_x2"])
+    return {"fp32_tflops": 2.0 * fma / 1e12,
+            "fp32_scalar_tflops": 2.0 * res["fma"] / 1e12,
+            "fp32_packed_x2_tflops": 2.0 * res["fma_x2"] / 1e12,
+            "ex2_gops": res["ex2"] / 1e9,
+            "sm_mhz": clk["sm_mhz"] if clk else None,
+            "how": f"probe kernels ({blocks} CTAs x 256 threads x 16 independent chains), best of 3, "
+                   "CUDA events; FMA counted as 2 flops"}
+
+
+def alu_roof(achieved, peaks, kernel, traffic, note_extra=""):
+    """Roofline entry for a kernel bound by the FP32 FMA pipe."""
+    if peaks:
+        peak, note = peaks["fp32_tflops"], "measured FP32 FMA probe (faster of scalar and packed f32x2)"
+    else:
+        peak, note = fp32_peak_tflops(2070.0), "FP32 FMA pipe 152 SM x 128 lanes x 2 flops x 2070 MHz (derived)"
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "kernel": kernel, "traffic": traffic, "peak_note": note + note_extra}
 
 
 PRECISIONS = {"fp32": 0, "bf16split": 1, "fp16split": 2}
@@ -118,28 +167,60 @@ def replica_throughput(units_per_rank, seconds_per_rank):
 # ---------------------------------------------------------------------------
 
 class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples, each stamped with the host
+    time at which it was read, so that the rows of the timed region can be
+    picked out.  start() waits (bounded) until the first row arrives: the tool
+    takes a while to come up, longer than a short timed region lasts."""
     QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    PERIOD_MS = 50
 
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = None
+        self.rows = []
+        self.window = None
+        self._thread = None
 
-    def start(self):
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append((time.perf_counter(), parts))
+
+    def start(self, wait_s=5.0):
+        import threading
         try:
-            import tempfile
-            fd, self.path = tempfile.mkstemp(suffix=".csv")
-            os.close(fd)
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
-                 "--format=csv,noheader,nounits", "-lms", "50"],
-                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+                 "--format=csv,noheader,nounits", "-lms", str(self.PERIOD_MS)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True, bufsize=1)
         except Exception:
             self.proc = None
+            return
+        self._thread = threading.Thread(target=self._read, daemon=True)
+        self._thread.start()
+        t0 = time.perf_counter()
+        while not self.rows and time.perf_counter() - t0 < wait_s and self.proc.poll() is None:
+            time.sleep(0.01)
 
-    def stop(self):
+    def begin(self):
+        self.window = [time.perf_counter(), None]
+
+    def end(self):
+        if self.window is not None:
+            self.window[1] = time.perf_counter()
+
+    def in_window(self):
+        if self.window is None or self.window[1] is None:
+            return 0
+        return sum(1 for t, _ in self.rows if self.window[0] <= t <= self.window[1])
+
+    def stop(self, extra=None):
+        """Statistics of the rows inside the timed window; with fewer than 3
+        there, also those of `extra` = (t0, t1), a stretch of the same
+        untimed work run right after it.  None without nvidia-smi."""
         if self.proc is None:
             return None
         self.proc.terminate()
@@ -147,21 +228,30 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-        rows = []
-        with open(self.path) as fh:
-            for line in fh:
-                parts = [p.strip() for p in line.split(",")]
-                if len(parts) >= 9:
-                    rows.append(parts)
-        os.unlink(self.path)
+        if self._thread is not None:
+            self._thread.join(timeout=2)
+        w0, w1 = self.window if self.window else (0.0, float("inf"))
+        timed = [r for t, r in self.rows if w0 <= t <= w1]
+        rows, where = timed, "timed region"
+        if len(timed) < 3 and extra is not None:
+            rows = timed + [r for t, r in self.rows if extra[0] <= t <= extra[1]]
+            where = "timed region and the same steps run untimed right after it"
         if not rows:
             return None
-        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return None
+        sm = [x for x in (num(r[1]) for r in rows) if x is not None]
+        mx = [x for x in (num(r[2]) for r in rows) if x is not None]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
         return {"sm_mhz": statistics.median(sm) if sm else None,
-                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows),
+                "samples_in_timed_region": len(timed), "window": where,
+                "period_ms": self.PERIOD_MS}
 
 
 # ---------------------------------------------------------------------------
@@ -208,23 +298,32 @@ def _cpu_child(rows, reps, workload=WORKLOAD):
     print(json.dumps({"seconds": dt, "sample_steps": rows * sc.params.T * reps, "T": sc.params.T}))
 
 
-def cpu_baseline(rows=CPU_SAMPLE_ROWS, reps=8, workload=WORKLOAD):
-    cores = os.cpu_count() or 1
+def cpu_baseline(rows=CPU_SAMPLE_ROWS, reps=8, workload=WORKLOAD, threads=None, single_core=True):
+    """The oracle on the host cores (BLAS threads = all cores, or `threads`),
+    in a spawned process; with single_core, also a smaller sample on one
+    BLAS thread (taskset to one core where available)."""
+    cores = threads or os.cpu_count() or 1
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         env[k] = str(cores)
     env.pop("CUDA_VISIBLE_DEVICES", None)
     cmd = [sys.executable, os.path.abspath(__file__), "--cpu-child", str(rows), str(reps), workload]
+    if threads == 1 and shutil.which("taskset"):
+        cmd = ["taskset", "-c", "0"] + cmd
     out = subprocess.run(cmd, capture_output=True, text=True, env=env, cwd=ROOT, timeout=900)
     line = [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
     if out.returncode != 0 or not line:
         return {"value": None, "unit": "sample-steps/s", "cores": cores, "kind": "oracle",
                 "sample": f"failed: {out.stderr.strip()[-200:]}"}
     d = json.loads(line[-1])
-    return {"value": d["sample_steps"] / d["seconds"], "unit": "sample-steps/s", "cores": cores,
-            "kind": "oracle",
-            "sample": f"FP64 numpy oracle, {rows} of the K samples x T={d['T']} steps x {reps} iterations "
-                      f"({d['seconds']:.1f} s), BLAS threads = {cores}"}
+    res = {"value": d["sample_steps"] / d["seconds"], "unit": "sample-steps/s", "cores": cores,
+           "kind": "oracle",
+           "sample": f"FP64 numpy oracle, {rows} of the K samples x T={d['T']} steps x {reps} iterations "
+                     f"({d['seconds']:.1f} s), BLAS threads = {cores}"}
+    if single_core and threads is None:
+        one = cpu_baseline(rows=max(16, rows // 8), reps=2, workload=workload, threads=1, single_core=False)
+        res["single_core"] = {k: one[k] for k in ("value", "unit", "cores", "sample")}
+    return res
 
 
 # ---------------------------------------------------------------------------
@@ -270,38 +369,67 @@ def run_reference(args):
 
 def timed_steps(gp, ctrl, x0, U, U_new, w, c, flush, stream, steps, warmup, barrier, clocks=None):
     """W warm-up steps, then `steps` mppi_steps each bracketed by CUDA events on
-    the launch stream, with an L2 flush (untimed) between them."""
+    the launch stream, with an L2 flush (untimed) between them.  The library's
+    per-kernel profiling is off in the timed loop (its events would sit
+    between the rollout and the update, and reading them synchronises every
+    step); a second pass of min(steps, 100) steps with profiling on, after the
+    timed loop, gives the rollout and update kernel times."""
     import torch
+    gp.mppi_set_profiling(ctrl, False)
+    if clocks is not None:
+        clocks.start()
     for _ in range(warmup):
         gp.mppi_step(ctrl, x0, U, U_new, w, c)
         flush.fill_(1.0)
     torch.cuda.synchronize()
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
-    rollout_ms, update_ms = [], []
-    if clocks is not None:
-        clocks.start()
     barrier()
     torch.cuda.synchronize()
+    if clocks is not None:
+        clocks.begin()
     t_wall = time.perf_counter()
     for i in range(steps):
         starts[i].record(stream)
         gp.mppi_step(ctrl, x0, U, U_new, w, c)
         ends[i].record(stream)
-        r_ms, u_ms = gp.mppi_last_profile(ctrl)
-        rollout_ms.append(r_ms)
-        update_ms.append(u_ms)
         flush.fill_(float(i))
     torch.cuda.synchronize()
     barrier()
     t_wall = time.perf_counter() - t_wall
-    clk = clocks.stop() if clocks is not None else None
+    clk = None
+    if clocks is not None:
+        clocks.end()
+        extra = None
+        if clocks.in_window() < 3:
+            # a timed region shorter than a few sampling periods: keep the same
+            # steps running (untimed) until three more samples came in
+            t0 = time.perf_counter()
+            n0 = len(clocks.rows)
+            while len(clocks.rows) < n0 + 3 and time.perf_counter() - t0 < 3.0:
+                for _ in range(20):
+                    gp.mppi_step(ctrl, x0, U, U_new, w, c)
+                    flush.fill_(1.0)
+                torch.cuda.synchronize()
+            extra = (t0, time.perf_counter())
+        clk = clocks.stop(extra)
     gp.mppi_device_status(ctrl)
     step_ms = [s_.elapsed_time(e_) for s_, e_ in zip(starts, ends)]
+    # per-kernel times (events the library records around its launches)
+    gp.mppi_set_profiling(ctrl, True)
+    rollout_ms, update_ms = [], []
+    for i in range(min(steps, 100)):
+        gp.mppi_step(ctrl, x0, U, U_new, w, c)
+        r_ms, u_ms = gp.mppi_last_profile(ctrl)
+        rollout_ms.append(r_ms)
+        update_ms.append(u_ms)
+        flush.fill_(float(i))
+    gp.mppi_set_profiling(ctrl, False)
+    gp.mppi_device_status(ctrl)
     return step_ms, rollout_ms, update_ms, t_wall, clk
 
 
-def fp32_path(args, gp, S, dev, flush, stream, barrier):
+def fp32_path(args, gp, S, dev, flush, stream, barrier, peaks=None):
     """The plain FP32 CUDA-core path on the same workload, for comparison."""
     import numpy as np
     import torch
@@ -321,11 +449,46 @@ def fp32_path(args, gp, S, dev, flush, stream, barrier):
     flops = rollout_flops_per_sample_step(sc.N, sc.obstacles.shape[0], S_seg) * P.K * P.T
     r_avg = sum(rollout_ms) / len(rollout_ms)
     ach = flops / (r_avg / 1e3) / 1e12
+    roof = alu_roof(ach, peaks, "k_rollout_fp32", committed_traffic("rollout_fp32", args.workload))
+    if peaks:
+        # the kernel rows' exponentials: N per sample-step on the SFU
+        ex2 = sc.N * P.K * P.T / (r_avg / 1e3) / 1e9
+        roof["sfu"] = {"achieved_gops": ex2, "peak_gops": peaks["ex2_gops"], "frac": ex2 / peaks["ex2_gops"]}
     return {"value": P.K * P.T * steps / (sum(step_ms) / 1e3), "unit": "sample-steps/s",
             "p50_ms": statistics.median(step_ms), "steps": steps, "rollout_ms": r_avg,
-            "roofline": {"bound": "alu", "achieved": ach, "peak": fp32_peak_tflops(2070.0),
-                         "unit": "TFLOP/s", "frac": ach / fp32_peak_tflops(2070.0),
-                         "kernel": "k_rollout_fp32", "traffic": committed_traffic("rollout_fp32", args.workload)}}
+            "roofline": roof}
+
+
+def cfg3_leg(args, gp, S, dev, flush, stream, barrier):
+    """Secondary leg: the K=16384, T=100, N=2048, 64-obstacle workload on the
+    streaming tensor-core rollout (FP16 split), a few timed mppi_steps."""
+    import numpy as np
+    import torch
+    sc = S.scenario("cfg3", seed=1, precision=PRECISIONS["fp16split"])
+    P = sc.params
+    g = gp.gp_fit(sc.X, sc.Y, sc.hyper)
+    ctrl = gp.mppi_create(P, sc.obstacles, sc.path, g)
+    U = torch.tensor(sc.U0, dtype=torch.float32, device=dev)
+    U_new = torch.empty_like(U)
+    w = torch.empty(P.K, dtype=torch.float32, device=dev)
+    c = torch.empty_like(w)
+    gp.mppi_set_profiling(ctrl, True)
+    steps = max(5, args.steps // 40)
+    step_ms, rollout_ms, update_ms, _, _ = timed_steps(gp, ctrl, sc.x0.astype(np.float32), U, U_new, w, c,
+                                                       flush, stream, steps, 3, barrier)
+    S_seg = max(sc.path.shape[0] - 1, 1)
+    flops = rollout_flops_per_sample_step(sc.N, sc.obstacles.shape[0], S_seg) * P.K * P.T
+    r_avg = sum(rollout_ms) / len(rollout_ms)
+    ach = flops / (r_avg / 1e3) / 1e12
+    peak, note = measured_tensor_peak()
+    kind = gp.mppi_rollout_kind(ctrl)
+    return {"workload": describe(sc)["workload"], "value": P.K * P.T * steps / (sum(step_ms) / 1e3),
+            "unit": "sample-steps/s", "steps": steps, "warmup": 3, "p50_ms": statistics.median(step_ms),
+            "kernel_ms": {"rollout_avg": r_avg, "update_avg": sum(update_ms) / len(update_ms)},
+            "roofline": {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                         "frac": ach / peak, "peak_note": note,
+                         "kernel": "k_rollout_mma" if kind == gp.GPMPPI_KERNEL_TC_STREAM else str(kind),
+                         "traffic": committed_traffic("rollout_mma", "cfg3")}}
 
 
 def run_ours(args):
@@ -415,23 +578,22 @@ def run_ours(args):
                   gp.GPMPPI_KERNEL_TC_CLUSTER: ("rollout_cluster", "k_rollout_cl"),
                   gp.GPMPPI_KERNEL_ENSEMBLE: ("ensemble", "k_rollout_ens")}[kind]
     traffic = committed_traffic(src, args.workload)
+    peaks = measure_alu_peaks(gp, dev, stream) if not args.no_alu_peaks else None
     if terrain:
-        roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak_tflops(2070.0), "unit": "TFLOP/s",
-                "traffic": traffic, "kernel": "k_rollout_ens",
-                "peak_note": "FP32 FMA pipe 152 SM x 128 lanes x 2 flops x 2070 MHz (derived); "
-                             "flops summed over the three terrain GPs"}
+        roof = alu_roof(achieved, peaks, "k_rollout_ens", traffic, "; flops summed over the three terrain GPs")
     elif P.precision == 0:
-        roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak_tflops(2070.0), "unit": "TFLOP/s",
-                "traffic": traffic, "kernel": "k_rollout_fp32",
-                "peak_note": "FP32 FMA pipe 152 SM x 128 lanes x 2 flops x 2070 MHz (derived)"}
+        roof = alu_roof(achieved, peaks, "k_rollout_fp32", traffic)
     else:
         peak, note = measured_tensor_peak()
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "traffic": traffic, "kernel": kname, "peak_note": note}
-    roof["frac"] = roof["achieved"] / roof["peak"]
+        roof["frac"] = roof["achieved"] / roof["peak"]
     fp32 = None
     if P.precision != 0 and not args.no_fp32_path:
-        fp32 = fp32_path(args, gp, S, dev, flush, stream, barrier)
+        fp32 = fp32_path(args, gp, S, dev, flush, stream, barrier, peaks)
+    legs = {}
+    if args.workload == WORKLOAD and not terrain and not args.no_legs:
+        legs["cfg3"] = cfg3_leg(args, gp, S, dev, flush, stream, barrier)
     if rank != 0:
         if ws > 1:
             torch.distributed.destroy_process_group()
@@ -457,6 +619,8 @@ def run_ours(args):
         "clocks": clk,
         "fp32_path": fp32,
         "vs_plain_fp32_path": (value / (fp32["value"] * ws)) if fp32 else None,
+        "alu_peaks": peaks,
+        **legs,
         "wall_s_timed_region": t_wall,
     }
     print(json.dumps(line), flush=True)
@@ -602,7 +766,7 @@ def run_grad(args):
     flops = grad_flops_per_sample_step(sc.N, sc.obstacles.shape[0], S_seg) * P.K * P.T
     a_avg = sum(adj_ms) / len(adj_ms)
     achieved = flops / (a_avg / 1e3) / 1e12
-    peak = fp32_peak_tflops(2070.0)
+    peaks = measure_alu_peaks(gp, dev, stream) if not args.no_alu_peaks else None
     units = P.K * P.T
     line = {
         "metric": METRIC, "value": units * args.steps * ws / (tot_ms / 1e3), "unit": "sample-steps/s",
@@ -616,10 +780,8 @@ def run_grad(args):
                    "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)"},
         "gpu_launches": 3 * args.steps,
         "kernel_ms": {"adjoint_avg": a_avg, "gram_trace_and_reduce_avg": sum(rest_ms) / len(rest_ms)},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": committed_traffic("adjoint", "cfg4"),
-                     "kernel": "k_grad",
-                     "peak_note": "FP32 FMA pipe 152 SM x 128 lanes x 2 flops x 2070 MHz (derived)"},
+        "roofline": alu_roof(achieved, peaks, "k_grad", committed_traffic("adjoint", "cfg4")),
+        "alu_peaks": peaks,
         "cpu_baseline": grad_cpu_baseline() if (ws == 1 and not args.no_cpu) else None,
         "e2e": {"value": units * n_e2e * ws / e2e_s, "unit": "sample-steps/s",
                 "h2d_bytes_per_step": U_host.numel() * 4 + 20, "d2h_bytes_per_step": out_host.numel() * 4},
@@ -763,6 +925,8 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD, help="scenario name (cfg2 is the reported workload)")
     ap.add_argument("--precision", default="fp16split", choices=sorted(PRECISIONS))
     ap.add_argument("--batch", type=int, default=64, help="controllers in the cfg5 workload")
+    ap.add_argument("--no-alu-peaks", action="store_true", help="skip the FP32/SFU throughput probes")
+    ap.add_argument("--no-legs", action="store_true", help="skip the secondary workload legs (cfg3)")
     ap.add_argument("--no-fp32-path", action="store_true",
                     help="skip timing the plain FP32 CUDA-core path beside the headline path")
     args = ap.parse_args()

@@ -354,6 +354,16 @@ int gpmppi_control_noise(uint64_t seed, int32_t K, int32_t T, uint64_t it, const
 int gpmppi_mma_selftest(int32_t fmt, int32_t N, int32_t K, int32_t variant, const uint16_t* A,
                         const uint16_t* B, float* D);
 
+/* Throughput probe of one arithmetic unit (measurement tool for roofline
+ * denominators; no counterpart in the paper): blocks x 256 threads each run
+ * iters iterations of 16 independent chains of one instruction,
+ *   kind 0  fma.rn.f32 (FP32 FMA pipe), kind 1  fma.rn.f32x2 (packed pairs,
+ *           counted as two FMAs each), kind 2  ex2.approx.ftz.f32 (SFU);
+ * i.e. blocks * 256 * iters * 16 operations.  out: device, blocks * 256
+ * floats (one result per thread, so that nothing is optimised away).
+ * Asynchronous on stream; time it with events on that stream. */
+int gpmppi_alu_probe(int32_t kind, int32_t blocks, int32_t iters, float* out, void* stream);
+
 /* Thread-local message describing the last failed call ("" if none). */
 const char* gpmppi_last_error(void);
 

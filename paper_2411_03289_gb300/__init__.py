@@ -43,7 +43,7 @@ EXPORTS = ("gp_fit", "gp_destroy", "gp_factors", "gp_predict", "mppi_create", "m
            "mppi_create_ensemble", "mppi_set_terrain_weights", "terrain_weights",
            "mppi_update_noalloc", "mppi_batch_create",
            "mppi_batch_buffers", "mppi_batch_step", "mppi_batch_graph", "mppi_batch_autotune",
-           "mppi_batch_get_iteration", "mppi_batch_destroy", "gpmppi_philox", "gpmppi_control_noise", "gpmppi_mma_selftest", "gpmppi_last_error",
+           "mppi_batch_get_iteration", "mppi_batch_destroy", "gpmppi_philox", "gpmppi_control_noise", "gpmppi_mma_selftest", "gpmppi_alu_probe", "gpmppi_last_error",
            "gpmppi_version")
 
 
@@ -116,6 +116,7 @@ def load():
         "gpmppi_philox": [u64, vp, i32, vp, vp],
         "gpmppi_control_noise": [u64, i32, i32, u64, vp, vp, vp],
         "gpmppi_mma_selftest": [i32, i32, i32, i32, vp, vp, vp],
+        "gpmppi_alu_probe": [i32, i32, i32, vp, vp],
         "gpmppi_version": [],
     }
     for name, args in sig.items():
@@ -498,6 +499,13 @@ def gpmppi_mma_selftest(fmt: int, A, B, D, variant: int = 0):
     N, K = B.shape
     _check(load().gpmppi_mma_selftest(fmt, N, K, variant, _dptr(A, name="A"), _dptr(B, name="B"),
                                       _dptr(D, numel=128 * N, name="D")))
+
+
+def gpmppi_alu_probe(kind: int, blocks: int, iters: int, out, stream=None):
+    """Launch the throughput probe of one arithmetic unit (0: FP32 FMA, 1: packed
+    FP32x2 FMA, 2: SFU ex2); blocks * 256 * iters * 16 operations."""
+    _check(load().gpmppi_alu_probe(int(kind), int(blocks), int(iters),
+                                   _dptr(out, numel=256 * blocks, name="out"), _stream(stream)))
 
 
 class _DevArray:

@@ -24,7 +24,7 @@ LIB_PATH = os.path.join(LIB_DIR, "libgpmppi.so")
 SOURCES = ["abi.cu", "gp_fit.cu", "rollout_fp32.cu", "rollout_mma.cu", "mma_selftest.cu",
            "mppi_aux.cu", "update_noalloc.cu", "batch.cu", "adjoint.cu",
            "ensemble.cu", "terrain_qp.cu", "rollout_cluster.cu",
-           "lane_grid.cu"]
+           "lane_grid.cu", "peaks.cu", "gram_tc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "-I", INCLUDE, "-I", CSRC]
@@ -75,9 +75,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
     with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
     tmp = LIB_PATH + ".tmp"
-    # cuBLAS (the gradient's Gram GEMM) from the toolkit that compiles, found at run time
-    cudalib = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(nvcc))), "lib64")
-    cmd = [nvcc, *ARCH, "-shared", "-cudart=static", "-o", tmp, *objs, "-lcublas", "-Xlinker", "-rpath=" + cudalib]
+    cmd = [nvcc, *ARCH, "-shared", "-cudart=static", "-o", tmp, *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

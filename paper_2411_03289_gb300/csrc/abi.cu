@@ -59,6 +59,9 @@ namespace {
 
 constexpr uint32_t kGpMagic = kGpMagicValue;
 constexpr uint32_t kCtrlMagic = kCtrlMagicValue;
+// training sets larger than this use the separate low column set of the
+// streaming tensor-core rollout (MmaArgs::lo_set)
+constexpr int kLoSetMinN = 768;
 
 bool is_finite(double v) { return std::isfinite(v); }
 
@@ -125,7 +128,6 @@ void free_ctrl(gpmppi_ctrl c) {
     cudaFree(c->gidx);
     cudaFree(c->err);
     cudaFree(c->grad_scr);
-    if (c->blas) cublasDestroy(c->blas);
     for (cudaEvent_t e : c->ev)
         if (e) cudaEventDestroy(e);
     if (c->gp && c->gp->magic == kGpMagic) c->gp->g.n_controllers--;
@@ -446,7 +448,7 @@ int mppi_create(const gpmppi_params* p, const float* obstacles, int32_t O, const
             (rc = alloc((void**)&c->seg_il2, sizeof(float) * c->S)) ||
             (rc = alloc((void**)&c->costs, sizeof(float) * K)) ||
             (rc = alloc((void**)&c->u_tilde, sizeof(float2) * K * T)) ||
-            (rc = alloc((void**)&c->partial, sizeof(float) * 2 * T * c->n_upd)) ||
+            (rc = alloc((void**)&c->partial, sizeof(float) * 2 * (T + 1) * c->n_upd)) ||
             (rc = alloc((void**)&c->counter, sizeof(unsigned int))) ||
             (rc = alloc((void**)&c->nom_sxy, sizeof(float) * 3 * T)) ||
             (rc = alloc((void**)&c->err, sizeof(unsigned int)))) {
@@ -509,10 +511,17 @@ int mppi_create(const gpmppi_params* p, const float* obstacles, int32_t O, const
             const double r = (double)g.sf2[0] / (g.mma_cB > 0.0f ? (double)g.mma_cB : 1.0);
             c->mm.qscale = (float)(r * r);
             c->mm.scene_smem = 1;
-            c->mm.stages = rollout_mma_stages(g.NpM, c->S, O, smem_optin);
+            // The tensor core rounds its FP32 accumulator at every MMA, so the
+            // variance error grows with the MMAs per output column (3 N / 16
+            // with all split products in one column set).  Beyond 768 points
+            // the two small products get their own column set (N / 16 MMAs on
+            // the large accumulator), which keeps the variance error near
+            // 1e-5 sf2 at N = 2048 at the cost of output passes half as wide.
+            c->mm.lo_set = g.N > kLoSetMinN ? 1 : 0;
+            c->mm.stages = rollout_mma_stages(g.NpM, c->S, O, smem_optin, c->mm.lo_set);
             if (c->mm.stages < 3) {
                 // keep the pipeline deep; read the scene from global memory instead
-                const int st_noscene = rollout_mma_stages(g.NpM, 0, 0, smem_optin);
+                const int st_noscene = rollout_mma_stages(g.NpM, 0, 0, smem_optin, c->mm.lo_set);
                 if (st_noscene > c->mm.stages) {
                     c->mm.stages = st_noscene;
                     c->mm.scene_smem = 0;
@@ -594,7 +603,7 @@ int mppi_step(gpmppi_ctrl c, const float state[5], const float* U_nom, float* U_
     u.T = c->p.T;
     u.per_cta = 256;
     u.inv_lambda = 1.0f / c->p.lambda;
-    if ((rc = launch_update(u, c->n_upd, st))) return rc;
+    if ((rc = launch_update(u, c->n_upd, st, !c->profiling))) return rc;
     if (c->p.variance_mode == GPMPPI_VAR_NOMINAL) {
         RolloutArgs n = make_rollout_args(c, state, U_new);
         if ((rc = launch_nominal(n, c->nom_sxy, st))) return rc;
@@ -729,7 +738,9 @@ int mppi_grad(gpmppi_ctrl c, const float state[5], const float* U_nom, const flo
     }
     // scratch layout (bytes, each piece 256-aligned)
     const int Q = T * Kpad;
-    const int nparts = want_l ? gram_trace_dense_blocks(Np) : 0;
+    int nsm = 0;
+    GPM_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device));
+    const int nparts = want_l ? gram_tc_parts(Q, Np, nsm) : 0;
     size_t off = 0;
     auto take = [&](size_t bytes) {
         const size_t o = off;
@@ -741,11 +752,9 @@ int mppi_grad(gpmppi_ctrl c, const float state[5], const float* U_nom, const flo
     const size_t o_S = take(sizeof(float) * (size_t)K);
     const size_t o_dU = take(sizeof(float) * (size_t)2 * T * K);
     const size_t o_dl = take(sizeof(float) * (size_t)8 * K);
-    size_t o_B = 0, o_C = 0, o_G = 0, o_q = 0, o_p = 0;
+    size_t o_B = 0, o_q = 0, o_p = 0;
     if (want_l) {
         o_B = take(sizeof(float) * (size_t)Q * Np);
-        o_C = take(sizeof(float) * (size_t)Q * 2 * Np);
-        o_G = take(sizeof(float) * (size_t)2 * Np * Np);
         o_q = take(sizeof(float4) * (size_t)Q);
         o_p = take(sizeof(float) * 8 * (size_t)nparts);
     }
@@ -777,28 +786,14 @@ int mppi_grad(gpmppi_ctrl c, const float state[5], const float* U_nom, const flo
     ga.dl_out = want_l ? reinterpret_cast<float*>(base + o_dl) : nullptr;
     ga.Bq = want_l ? reinterpret_cast<float*>(base + o_B) : nullptr;
     ga.qbar = want_l ? reinterpret_cast<float4*>(base + o_q) : nullptr;
-    ga.Cq = want_l ? reinterpret_cast<float*>(base + o_C) : nullptr;
     if (c->profiling) GPM_CUDA(cudaEventRecord(c->ev[0], st));
     if ((rc = launch_grad(ga, ncta, st))) return rc;
     if (c->profiling) GPM_CUDA(cudaEventRecord(c->ev[1], st));
     if (want_l) {
-        // G = [G_v; G_w] = C B^T, C = (sbar_v b, sbar_w b) per query: a plain FP32
-        // GEMM over the T K queries (cuBLAS, BF16x9 emulation of FP32 where it is
-        // faster), then the traces against dK/dl_d
-        if (!c->blas) {
-            if (cublasCreate(&c->blas) != CUBLAS_STATUS_SUCCESS) {
-                c->blas = nullptr;
-                return fail(GPMPPI_ERR_CUDA, "mppi_grad: cublasCreate failed");
-            }
-        }
-        float* G = reinterpret_cast<float*>(base + o_G);
-        const float one = 1.0f, zero = 0.0f;
-        if (cublasSetStream(c->blas, st) != CUBLAS_STATUS_SUCCESS ||
-            cublasGemmEx(c->blas, CUBLAS_OP_N, CUBLAS_OP_T, 2 * Np, Np, Q, &one, ga.Cq, CUDA_R_32F, 2 * Np, ga.Bq,
-                         CUDA_R_32F, Np, &zero, G, CUDA_R_32F, 2 * Np, CUBLAS_COMPUTE_32F_EMULATED_16BFX9,
-                         CUBLAS_GEMM_DEFAULT) != CUBLAS_STATUS_SUCCESS)
-            return fail(GPMPPI_ERR_CUDA, "mppi_grad: Gram GEMM failed");
-        if ((rc = launch_gram_trace_dense(G, Np, N, g.Xs[0], g.sf2[0], reinterpret_cast<float*>(base + o_p), st)))
+        // tr(dK/dl_d G_o), G_o = sum_q sbar_o,q b_q b_q^T over the T K queries:
+        // the Gram contraction on the tensor cores, traced tile by tile
+        if ((rc = launch_gram_tc(ga.Bq, ga.qbar, Q, Np, N, g.Xs[0], g.sf2[0], reinterpret_cast<float*>(base + o_p),
+                                 nparts, c->err, nsm, st)))
             return rc;
     }
     GradReduceArgs rr;

@@ -468,20 +468,12 @@ __global__ void __launch_bounds__(GT, 2) k_grad(const GradArgs g) {
             __syncthreads();
             const float sbv2 = save[20], sbw2 = save[21], mbv2 = save[22], mbw2 = save[23];
             if (g.Bq) {
-                // b_q and (sbar_v b_q, sbar_w b_q): the two operands of G = C B^T
+                // b_q for the Gram contraction G_o = sum_q sbar_o,q b_q b_q^T (the
+                // adjoints sbar go with it in qbar; a padding sample's are zero)
                 const size_t q0 = (size_t)k * g.Kpad + (size_t)blockIdx.x * GMT;
                 for (int ws = 0; ws < GMT; ++ws) {
-                    const bool live = blockIdx.x * GMT + ws < g.r.K;
-                    const float sv = live ? saves[ws * SAVE + 20] : 0.0f;
-                    const float sw = live ? saves[ws * SAVE + 21] : 0.0f;
                     float* dst = g.Bq + (q0 + ws) * Np;
-                    float* dc = g.Cq + (q0 + ws) * 2 * Np;
-                    for (int j = tid; j < Np; j += GT) {
-                        const float b = bufB[j * GMT + ws];
-                        dst[j] = b;
-                        dc[j] = sv * b;
-                        dc[Np + j] = sw * b;
-                    }
+                    for (int j = tid; j < Np; j += GT) dst[j] = bufB[j * GMT + ws];
                 }
                 if (lane == 0)
                     g.qbar[q0 + w] = act ? make_float4(mbv2, mbw2, sbv2, sbw2) : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -560,43 +552,6 @@ __global__ void __launch_bounds__(GT, 2) k_grad(const GradArgs g) {
 // (xs_id - xs_jd)^2 (dK/dl_d up to the factor 2 ln2 / l_d) and G = [G_v; G_w]
 // (2 Np x Np, column-major, symmetric blocks): warp w of block b takes column
 // j = 8 b + w, lanes the rows i (coalesced); 8 partial sums per block.
-__global__ void __launch_bounds__(256) k_gram_trace_dense(const float* __restrict__ G, int Np, int N,
-                                                          const float* __restrict__ Xs, float sf2,
-                                                          float* __restrict__ part) {
-    __shared__ float red[8][8];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int j = blockIdx.x * 8 + warp;
-    float tr[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    if (j < N) {
-        const float4 xj = ldg4(Xs + 4 * j);
-        const float* gv = G + (size_t)j * 2 * Np;
-        const float* gw = gv + Np;
-        for (int i = lane; i < N; i += 32) {
-            const float4 xi = ldg4(Xs + 4 * i);
-            const float d0 = xi.x - xj.x, d1 = xi.y - xj.y, d2 = xi.z - xj.z, d3 = xi.w - xj.w;
-            const float dd[4] = {d0 * d0, d1 * d1, d2 * d2, d3 * d3};
-            const float kf = sf2 * exp2f(-(dd[0] + dd[1] + dd[2] + dd[3]));
-            const float a = __ldg(gv + i), b = __ldg(gw + i);
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                tr[e] = fmaf(kf * dd[e], a, tr[e]);
-                tr[4 + e] = fmaf(kf * dd[e], b, tr[4 + e]);
-            }
-        }
-    }
-#pragma unroll
-    for (int e = 0; e < 8; ++e) {
-        const float v = wsum(tr[e]);
-        if (lane == 0) red[warp][e] = v;
-    }
-    __syncthreads();
-    if (threadIdx.x < 8) {
-        float v = 0.0f;
-        for (int w = 0; w < 8; ++w) v += red[w][threadIdx.x];
-        part[(size_t)blockIdx.x * 8 + threadIdx.x] = v;
-    }
-}
-
 // ubar[(o*4+d)][i] = sum_j Kf_ij (xs_id - xs_jd)^2 alpha_o[j]: (dK/dl_d) alpha_o
 // up to the factor 2 ln2 / l_d; one warp per row i.
 __global__ void k_dk_alpha(const float* __restrict__ Xs, const float* __restrict__ alpha, int N, int Np,
@@ -684,15 +639,6 @@ int launch_grad(const GradArgs& g, int ncta, cudaStream_t st) {
     const int smem = grad_smem_bytes(g.r.Np, g.C);
     GPM_CUDA(cudaFuncSetAttribute(k_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     k_grad<<<ncta, GT, smem, st>>>(g);
-    GPM_CUDA(cudaGetLastError());
-    return 0;
-}
-
-int gram_trace_dense_blocks(int Np) { return (Np + 7) / 8; }
-
-int launch_gram_trace_dense(const float* G, int Np, int N, const float* Xs, float sf2, float* part,
-                            cudaStream_t st) {
-    k_gram_trace_dense<<<gram_trace_dense_blocks(Np), 256, 0, st>>>(G, Np, N, Xs, sf2, part);
     GPM_CUDA(cudaGetLastError());
     return 0;
 }

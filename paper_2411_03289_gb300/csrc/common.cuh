@@ -202,9 +202,11 @@ struct MmaArgs {
     int nblocks;            // NpM / 128
     int nchunks;            // NpM / 16
     float qscale;           // (sf2 / cB)^2: |L^-1 k*|^2 = qscale * |V'|^2
-    int stages;             // shared-memory pipeline depth (2..4)
+    int stages;             // shared-memory pipeline depth (2..6)
     int rps;                // producer threads per sample (2, 4, 8): 128, 64, 32 samples per CTA
     int scene_smem;         // lane segments and obstacles staged in shared memory
+    int lo_set;             // 1: the small split products in their own TMEM column set
+                            // (passes of 2 output blocks), 0: all three in one (passes of 4)
 };
 
 // The lane segments to scan for the point (px, py): (offset into gidx, count),
@@ -283,7 +285,6 @@ struct GradArgs {
     float* dl_out;          // 8 x K per-sample lengthscale terms, or null
     float* Bq;              // (T Kpad) x Np: b = K^-1 k* per query, or null
     float4* qbar;           // T Kpad: (mbar_v, mbar_w, sbar_v, sbar_w) per query
-    float* Cq;              // (T Kpad) x 2 Np: (sbar_v b, sbar_w b) per query, or null
 };
 
 struct GradReduceArgs {
@@ -335,7 +336,9 @@ int launch_rollout_fp32(const RolloutArgs& a, const CUtensorMap* tmap_w, bool tr
 int make_w_tensor_map(CUtensorMap* out, const float* W, int Np);
 // pipeline depth that fits shared memory (0 if none fits)
 int rollout_fp32_stages(int Np, int smem_optin);
-int launch_update(const UpdateArgs& a, int n_cta, cudaStream_t st);
+// after_rollout: the previous operation on st is the rollout kernel, and the
+// update's launch may overlap its tail (programmatic dependent launch)
+int launch_update(const UpdateArgs& a, int n_cta, cudaStream_t st, bool after_rollout);
 int launch_update_batched(const UpdateArgs* args, const int2* items, const int* ncta,
                           unsigned long long* iters, int nitems, int maxT, cudaStream_t st);
 int launch_rollout_mma_batched(const RolloutArgs* args, const MmaArgs* mms, const int2* items, int nitems,
@@ -350,7 +353,7 @@ int launch_noise(uint64_t seed, int K, int T, uint64_t it, float sv, float sw, f
 int launch_nominal(const RolloutArgs& a, float* sxy_out, cudaStream_t st);
 int rollout_fp32_smem_bytes(int Np, int mtp, int stages);
 int launch_rollout_mma(const RolloutArgs& a, const MmaArgs& mm, int fmt, bool trace, cudaStream_t st);
-int rollout_mma_stages(int NpM, int S, int O, int smem_optin);
+int rollout_mma_stages(int NpM, int S, int O, int smem_optin, int lo_set);
 int build_mma_tiles(GpDevice& g, int fmt);
 int build_cl_tiles(GpDevice& g, int fmt);
 int cl_smem_bytes(const ClArgs& cl, int S, int O);
@@ -364,9 +367,11 @@ int grad_samples_per_cta();
 int launch_grad(const GradArgs& g, int ncta, cudaStream_t st);
 // tr(D_d G_o) from G = [G_v; G_w] (2 Np x Np, column-major): one block per 8
 // columns, 8 partial sums per block; returns the number of blocks
-int launch_gram_trace_dense(const float* G, int Np, int N, const float* Xs, float sf2, float* part,
-                            cudaStream_t st);
-int gram_trace_dense_blocks(int Np);
+// the lengthscale Gram traces on the tensor cores (gram_tc.cu): nparts x 8
+// partial traces, nparts = gram_tc_parts(Q, Np, nsm)
+int gram_tc_parts(int Q, int Np, int nsm);
+int launch_gram_tc(const float* Bq, const float4* qbar, int Q, int Np, int N, const float* Xs, float sf2,
+                   float* part, int nparts, unsigned int* err, int nsm, cudaStream_t st);
 int launch_dk_alpha(const float* Xs, const float* alpha, int N, int Np, float sf2, float* ubar,
                     cudaStream_t st);
 int launch_transpose(const float* W, int Np, float* Wt, cudaStream_t st);

@@ -2,7 +2,6 @@
 // shared by the translation units that implement the ABI.
 #pragma once
 
-#include <cublas_v2.h>
 
 #include "common.cuh"
 
@@ -28,7 +27,7 @@ struct gpmppi_ctrl_s {
     float* seg_il2 = nullptr;
     float* costs = nullptr;       // K, used when the caller passes no costs array
     float2* u_tilde = nullptr;    // T x K
-    float* partial = nullptr;     // n_upd x T x 2
+    float* partial = nullptr;     // n_upd x T x 2 update partials, then n_upd x 2 block statistics
     unsigned int* counter = nullptr;
     float* nom_sxy = nullptr;     // T x 3
     int2* gcell = nullptr;        // lane-distance grid (null: scan every segment)
@@ -50,7 +49,6 @@ struct gpmppi_ctrl_s {
     float tw[gpm::kMaxTerrains] = {};
     // adjoint-rollout scratch (allocated by the first mppi_grad call)
     void* grad_scr = nullptr;
-    cublasHandle_t blas = nullptr;      // the gradient's Gram GEMM
     size_t grad_bytes = 0;
     bool profiling = false;
     bool profiled = false;

@@ -2,15 +2,14 @@
 // the raw-noise entry points.
 //
 // Update (Alg. 1, "weights" and "weighted sum"): CTA (b, j) of the grid
-// takes sample block b (256 samples) and step block j (16 steps).  Every
-// CTA reduces the K costs to rho = min S and Z = sum_s exp(-(S_s - rho)/lambda)
-// in one fixed order (so all CTAs agree bit for bit), forms w_s for its
-// samples (CTAs of step block 0 write them out), and reduces
-// sum_s w_s (u~_s,k - U_k) over them for its steps (two steps per warp, all
-// loads of a lane in flight together, coalesced reads of u~, warp shuffles).
-// The partials go to a scratch array [sample block][T][2]; the CTA that
-// finishes last (atomic ticket) sums them in sample-block order and writes
-// U_new.
+// takes sample block b (256 samples) and step block j (16 steps).  It
+// reduces its own samples to the log-sum-exp tuple (rho_b = min S,
+// Z_b = sum exp(-(S - rho_b)/lambda), V_b = sum exp(-(S - rho_b)/lambda)
+// (u~ - U) for its steps; two steps per warp, all loads of a lane in flight
+// together, coalesced reads of u~, warp shuffles).  The tuples go to a
+// scratch array; the CTA that finishes last (atomic ticket) rescales them to
+// the global minimum and combines them in sample-block order into U_new and
+// the weights.
 #include <cfloat>
 
 #include "common.cuh"
@@ -35,68 +34,56 @@ __device__ __forceinline__ float warp_min(float v) {
     return v;
 }
 
-// loads of the K costs in groups of eight per thread, all in flight together
-template <typename F>
-__device__ __forceinline__ void for_costs(const float* __restrict__ costs, int K, F&& f) {
-    const int tid = threadIdx.x;
-    for (int s0 = tid; s0 < K; s0 += 8 * UPD_THREADS) {
-        float c[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const int s = s0 + j * UPD_THREADS;
-            c[j] = s < K ? __ldg(costs + s) : FLT_MAX;
-        }
-#pragma unroll
-        for (int j = 0; j < 8; ++j)
-            if (s0 + j * UPD_THREADS < K) f(c[j]);
-    }
+__device__ __forceinline__ float block_reduce(float v, float* red, bool is_min) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    v = is_min ? warp_min(v) : warp_sum(v);
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    float r = red[0];
+    for (int w = 1; w < UPD_WARPS; ++w) r = is_min ? fminf(r, red[w]) : r + red[w];
+    return r;
 }
 
 // cta: sample block; [k_lo, k_hi): the CTA's steps; n_sb sample blocks and
-// n_total CTAs in all (the ticket counts every CTA)
+// n_total CTAs in all (the ticket counts every CTA).
+//
+// Each CTA reduces only its own samples: rho_b = min S over the block,
+// e_s = exp(-(S_s - rho_b)/lambda), Z_b = sum e_s and, for its steps,
+// V_b,k = sum_s e_s (u~_s,k - U_k).  (rho_b, Z_b, V_b) is the associative
+// log-sum-exp tuple: with rho = min_b rho_b and c_b = exp(-(rho_b - rho)/lambda),
+// Z = sum_b c_b Z_b and U_new = U + sum_b c_b V_b / Z.  The last CTA forms
+// that combination in sample-block order and writes the weights
+// w_s = exp(-(S_s - rho)/lambda) / Z.  No CTA reads all K costs but the last.
+//
+// Scratch layout (a.partial): V at [(b T + k) 2 + {0,1}], then the block
+// statistics (rho_b, Z_b) at [n_sb T 2 + 2 b + {0,1}].
 __device__ __forceinline__ void update_body(const UpdateArgs& a, int cta, int n_sb, int k_lo, int k_hi,
                                             int n_total, unsigned long long* it_dev) {
+    // launched as a programmatic dependent of the rollout (its launch overlaps
+    // the rollout's tail): wait until the rollout grid has completed and its
+    // costs and u~ are visible (a no-op for an ordinary launch)
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     __shared__ float red[UPD_WARPS];
-    __shared__ float bcast[2];
     __shared__ float wsh[UPD_THREADS];
     __shared__ unsigned int is_last;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int K = a.K, T = a.T;
-    // rho = min_s S_s
-    float mn = FLT_MAX;
-    for_costs(a.costs, K, [&](float c) { mn = fminf(mn, c); });
-    mn = warp_min(mn);
-    if (lane == 0) red[warp] = mn;
-    __syncthreads();
-    if (tid == 0) {
-        float r = red[0];
-        for (int w = 1; w < UPD_WARPS; ++w) r = fminf(r, red[w]);
-        bcast[0] = r;
-    }
-    __syncthreads();
-    const float rho = bcast[0];
-    // Z = sum_s exp(-(S_s - rho)/lambda), fixed summation order
-    float z = 0.0f;
-    for_costs(a.costs, K, [&](float c) { z += expf((rho - c) * a.inv_lambda); });
-    z = warp_sum(z);
-    if (lane == 0) red[warp] = z;
-    __syncthreads();
-    if (tid == 0) {
-        float r = 0.0f;
-        for (int w = 0; w < UPD_WARPS; ++w) r += red[w];
-        bcast[1] = r;
-    }
-    __syncthreads();
-    const float inv_z = 1.0f / bcast[1];
-    // own samples' weights
     const int s_base = cta * a.per_cta;
     const int s = s_base + tid;
     const bool act = (tid < a.per_cta) && (s < K);
-    const float w = act ? expf((rho - __ldg(a.costs + s)) * a.inv_lambda) * inv_z : 0.0f;
-    if (act && a.weights && k_lo == 0) a.weights[s] = w;
-    wsh[tid] = w;
+    const float cs = act ? __ldg(a.costs + s) : FLT_MAX;
+    const float rho_b = block_reduce(cs, red, true);
+    const float e = act ? expf((rho_b - cs) * a.inv_lambda) : 0.0f;
+    const float z_b = block_reduce(e, red, false);
+    float* stats = a.partial + (size_t)n_sb * T * 2;
+    if (k_lo == 0 && tid == 0) {
+        stats[2 * cta] = rho_b;
+        stats[2 * cta + 1] = z_b;
+    }
+    wsh[tid] = e;
     __syncthreads();
-    // sum_s w_s (u~_s,k - U_k) over the CTA's samples: warp w takes steps
+    // sum_s e_s (u~_s,k - U_k) over the CTA's samples: warp w takes steps
     // k_lo + 2 w and k_lo + 2 w + 1 (then + 16 ...), lane l the samples l,
     // l + 32, ... (coalesced reads of u~, all of a lane's loads in flight)
     const int ns = min(a.per_cta, K - s_base);
@@ -136,26 +123,56 @@ __device__ __forceinline__ void update_body(const UpdateArgs& a, int cta, int n_
             }
         }
     }
-    // last CTA combines the partials in CTA order
+    // the last CTA combines the blocks' tuples in sample-block order
     __threadfence();
     __syncthreads();
     if (tid == 0) is_last = (atomicAdd(a.counter, 1u) == (unsigned int)n_total - 1u) ? 1u : 0u;
     __syncthreads();
     if (!is_last) return;
     __threadfence();
+    float mn = FLT_MAX;
+    for (int b = tid; b < n_sb; b += UPD_THREADS) mn = fminf(mn, __ldcg(stats + 2 * b));
+    const float rho = block_reduce(mn, red, true);
+    // c_b replaces rho_b in the scratch; Z = sum_b c_b Z_b
+    float zp = 0.0f;
+    for (int b = tid; b < n_sb; b += UPD_THREADS) {
+        const float cb = expf((rho - __ldcg(stats + 2 * b)) * a.inv_lambda);
+        zp = fmaf(cb, __ldcg(stats + 2 * b + 1), zp);
+        __stcg(stats + 2 * b, cb);
+    }
+    const float inv_z = 1.0f / block_reduce(zp, red, false);   // its barriers publish the c_b
     for (int i = tid; i < 2 * T; i += UPD_THREADS) {
         // sample-block order; sixteen loads in flight at a time
         float acc = 0.0f;
         for (int c0 = 0; c0 < n_sb; c0 += 16) {
-            float p[16];
+            float p[16], cb[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const bool in = c0 + j < n_sb;
+                p[j] = in ? __ldcg(a.partial + (size_t)(c0 + j) * 2 * T + i) : 0.0f;
+                cb[j] = in ? __ldcg(stats + 2 * (c0 + j)) : 0.0f;
+            }
 #pragma unroll
             for (int j = 0; j < 16; ++j)
-                p[j] = c0 + j < n_sb ? __ldcg(a.partial + (size_t)(c0 + j) * 2 * T + i) : 0.0f;
-#pragma unroll
-            for (int j = 0; j < 16; ++j)
-                if (c0 + j < n_sb) acc += p[j];
+                if (c0 + j < n_sb) acc = fmaf(cb[j], p[j], acc);
         }
-        a.U_new[i] = __ldg(a.U + i) + acc;
+        a.U_new[i] = fmaf(acc, inv_z, __ldg(a.U + i));
+    }
+    if (a.weights) {
+        // w_s = exp(-(S_s - rho)/lambda) / Z, eight loads in flight per thread
+        for (int s0 = tid; s0 < K; s0 += 8 * UPD_THREADS) {
+            float c[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int q = s0 + j * UPD_THREADS;
+                c[j] = q < K ? __ldg(a.costs + q) : 0.0f;
+            }
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int q = s0 + j * UPD_THREADS;
+                if (q < K) a.weights[q] = expf((rho - c[j]) * a.inv_lambda) * inv_z;
+            }
+        }
     }
     if (tid == 0) {
         *a.counter = 0u;
@@ -290,14 +307,25 @@ __global__ void __launch_bounds__(NOM_THREADS) k_nominal(const RolloutArgs a, co
 
 }  // namespace
 
-int launch_update(const UpdateArgs& a, int n_cta, cudaStream_t st) {
-    // Every CTA reduces all K costs itself, so the step blocks multiply that
-    // work: they are used while there are at most 64 sample blocks (K <= 16384);
-    // beyond, one CTA per sample block covers all T steps.  (T = 0: one step
-    // block, no steps; the last CTA still writes nothing.)
-    const int nstep = (a.T > 0 && n_cta <= 64) ? (a.T + UPD_STEPS - 1) / UPD_STEPS : 1;
-    k_update<<<dim3(n_cta, nstep), UPD_THREADS, 0, st>>>(a);
-    GPM_CUDA(cudaGetLastError());
+int launch_update(const UpdateArgs& a, int n_cta, cudaStream_t st, bool after_rollout) {
+    // sample blocks x step blocks of UPD_STEPS steps (a CTA reads only its own
+    // samples' costs, so the step blocks add no reduction work)
+    const int nstep = a.T > 0 ? (a.T + UPD_STEPS - 1) / UPD_STEPS : 1;
+    // after_rollout: programmatic stream serialisation, so that the launch may
+    // begin while the previous kernel on the stream (the rollout) finishes;
+    // the kernel's griddepcontrol.wait holds every CTA until that kernel has
+    // completed.  Otherwise (say a memset precedes it) an ordinary launch.
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)n_cta, (unsigned)nstep);
+    cfg.blockDim = dim3(UPD_THREADS);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = after_rollout ? 1 : 0;
+    GPM_CUDA(cudaLaunchKernelEx(&cfg, k_update, a));
     return GPMPPI_OK;
 }
 

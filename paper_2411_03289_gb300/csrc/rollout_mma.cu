@@ -5,20 +5,28 @@
 // variance, Eq. 10 mean/covariance, Eq. 11-16 costs); only the dense part
 // of the variance, V = K* L^-T with |V_m|^2 = |L^-1 k*_m|^2, moves to the
 // tensor cores.  Operands are split into a high and a low 16-bit part
-// (x = hi + lo, both FP16 or both BF16) and three products hi*hi + hi*lo +
-// lo*hi are accumulated in FP32, which keeps the variance close to FP32
-// accuracy; the queries are scaled to a_j = k*_j / sf2 in [0, 1] and L^-T by a
-// power of two cB so that both fit the 16-bit range.
+// (x = hi + lo, both FP16 or both BF16) and the three products hi*hi, hi*lo,
+// lo*hi are accumulated in FP32; the queries are scaled to a_j = k*_j / sf2
+// in [0, 1] and L^-T by a power of two cB so that both fit the 16-bit range.
+// The tensor core's FP32 accumulation rounds at every MMA relative to the
+// accumulator's magnitude, so its error grows with the number of MMAs that
+// add into one accumulator.  For large training sets (mm.lo_set) hi*hi goes
+// to one TMEM column set and the two small products to a second one, added
+// only at the pass end: the large accumulator then sees one addition per
+// chunk instead of three, which keeps the variance near FP32 accuracy at
+// N = 2048, at the price of output passes half as wide.
 //
 // CTA = 128 samples (the MMA M), 256 threads: thread t serves sample t % 128
 // and half h = t / 128 of every shared loop.  The output columns of V are
-// processed in passes of up to 512 (one TMEM allocation), 64 columns per MMA
-// block; the reduction dimension in chunks of 32 training points through two
+// processed in passes of up to 512 columns (one TMEM allocation), or of 256
+// with the low column set in the other half, 128 columns per MMA block; the
+// reduction dimension in chunks of 16 training points through a ring of
 // shared-memory stages.  Per chunk the threads compute the kernel-row tile
 // (exp2 on the SFU), one thread fetches the pre-arranged L^-T tiles with bulk
-// copies and issues 3 x 2 MMAs per active block (blocks entirely above the
+// copies and issues 3 MMAs per active block (blocks entirely above the
 // triangle are skipped) and commits them to the stage's mbarrier.  At the end
-// of a pass each thread reads its sample's TMEM row and sums the squares.
+// of a pass each thread reads its sample's TMEM row (both column sets, added,
+// with mm.lo_set) and sums the squares.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -35,11 +43,13 @@ constexpr int NPROD = 256;            // producer threads (warps 0-7): two per s
 constexpr int THREADS = NPROD + 64;   // + warp 8 (MMA issuer) + warp 9 (tile loader)
 constexpr int KC = 16;                // training points per chunk (one MMA K-step)
 constexpr int BLK = 128;              // output columns per MMA block (MMA N)
-constexpr int BLOCKS_PER_PASS = 4;    // 512 TMEM columns
-constexpr int NSTAGE = 4;             // maximum pipeline depth (3 when the training set is large)
+constexpr int BLOCKS_PER_PASS = 4;    // 512 TMEM columns (2 blocks per column set with mm.lo_set)
+constexpr int LO_COL = 256;           // first TMEM column of the low set
+constexpr int NSTAGE = 6;             // maximum pipeline depth (fewer when the training set is large)
 constexpr int A_PART = MT * KC * 2;                         // 4 KiB
 constexpr int B_PART = BLK * KC * 2;                        // 4 KiB
-constexpr int STAGE = 2 * A_PART + BLOCKS_PER_PASS * 2 * B_PART;   // 40 KiB
+// a stage: the A tile (hi, lo), then up to bpp B pieces hi, then bpp lo
+__host__ __device__ constexpr int stage_bytes(int bpp) { return 2 * A_PART + bpp * 2 * B_PART; }
 constexpr uint64_t kWaitNs = 2000000000ull;
 
 // Shared-memory layout for a given pipeline depth and padded training-set size.
@@ -47,9 +57,9 @@ struct MLayout {
     int bars, tslot, abort_flag, qh, mh, ep, om, xs, al, seg, il2, obs, total;
 };
 
-__host__ __device__ inline MLayout mma_layout(int nstage, int NpM, int S, int O) {
+__host__ __device__ inline MLayout mma_layout(int nstage, int NpM, int S, int O, int bpp) {
     MLayout L;
-    L.bars = nstage * STAGE;                     // a_full, b_full, empty [NSTAGE] + pass_done, tmem_free, x_res
+    L.bars = nstage * stage_bytes(bpp);                     // a_full, b_full, empty [NSTAGE] + pass_done, tmem_free, x_res
     L.tslot = L.bars + 8 * (3 * NSTAGE + 3);
     L.abort_flag = L.tslot + 4;
     L.qh = ((L.abort_flag + 4 + 15) / 16) * 16;  // 2 x 128 floats
@@ -66,9 +76,9 @@ __host__ __device__ inline MLayout mma_layout(int nstage, int NpM, int S, int O)
 }
 
 // deepest pipeline that fits (0 if none)
-inline int mma_stages(int NpM, int S, int O, int optin) {
+inline int mma_stages(int NpM, int S, int O, int optin, int bpp) {
     for (int s = NSTAGE; s >= 2; --s)
-        if (mma_layout(s, NpM, S, O).total <= optin) return s;
+        if (mma_layout(s, NpM, S, O, bpp).total <= optin) return s;
     return 0;
 }
 
@@ -142,7 +152,9 @@ __device__ __forceinline__ void rollout_mma_body(const RolloutArgs& a, const Mma
     constexpr int KPT = KC / R;
     const int nstage = mm.stages;
     const int Ssm = mm.scene_smem ? a.S : 0, Osm = mm.scene_smem ? a.O : 0;
-    const MLayout L = mma_layout(nstage, mm.nblocks * BLK, Ssm, Osm);
+    const int bpp = mm.lo_set ? BLOCKS_PER_PASS / 2 : BLOCKS_PER_PASS;   // output blocks per pass
+    const int STAGE = stage_bytes(bpp);
+    const MLayout L = mma_layout(nstage, mm.nblocks * BLK, Ssm, Osm, bpp);
     uint64_t* a_full = reinterpret_cast<uint64_t*>(sm + L.bars);
     uint64_t* b_full = a_full + NSTAGE;
     uint64_t* empty = b_full + NSTAGE;
@@ -159,7 +171,7 @@ __device__ __forceinline__ void rollout_mma_body(const RolloutArgs& a, const Mma
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int NB = mm.nblocks;                 // 64-column blocks of L^-T
-    const int npass = (NB + BLOCKS_PER_PASS - 1) / BLOCKS_PER_PASS;
+    const int npass = (NB + bpp - 1) / bpp;
 
     if (tid == 0) {
         for (int i = 0; i < nstage; ++i) {
@@ -217,8 +229,8 @@ __device__ __forceinline__ void rollout_mma_body(const RolloutArgs& a, const Mma
         uint32_t n = 0, pc = 0;
         for (int k = 0; k < a.T; ++k) {
             for (int g = 0; g < npass; ++g, ++pc) {
-                const int b0 = g * BLOCKS_PER_PASS;
-                const int b1 = min(NB, b0 + BLOCKS_PER_PASS);
+                const int b0 = g * bpp;
+                const int b1 = min(NB, b0 + bpp);
                 const int nchunk = 8 * b1;               // block b needs chunks 0 .. 8b+7
                 if (issuer && pc > 0) {
                     wait_or_abort(tmem_free, (pc - 1) & 1u, abort_flag, a.err);
@@ -243,7 +255,7 @@ __device__ __forceinline__ void rollout_mma_body(const RolloutArgs& a, const Mma
                         const size_t off = ((size_t)c * NB + ba) * (B_PART / 2);
                         unsigned char* dst = stage + 2 * A_PART + (ba - b0) * B_PART;
                         bulk_copy(dst, mm.Bhi + off, bytes, b_full + st);
-                        bulk_copy(dst + BLOCKS_PER_PASS * B_PART, mm.Blo + off, bytes, b_full + st);
+                        bulk_copy(dst + bpp * B_PART, mm.Blo + off, bytes, b_full + st);
                     } else {
                         bool ok = wait_or_abort(a_full + st, use & 1u, abort_flag, a.err);
                         ok = ok && wait_or_abort(b_full + st, use & 1u, abort_flag, a.err);
@@ -257,9 +269,13 @@ __device__ __forceinline__ void rollout_mma_body(const RolloutArgs& a, const Mma
                         while (ba < b1 && c >= 8 * ba + 8) ++ba;
                         for (int b = ba; b < b1; ++b) {
                             const uint64_t dBh = dB0 + (uint64_t)((st * STAGE + 2 * A_PART + (b - b0) * B_PART) >> 4);
-                            const uint64_t dBl = dBh + (uint64_t)((BLOCKS_PER_PASS * B_PART) >> 4);
+                            const uint64_t dBl = dBh + (uint64_t)((bpp * B_PART) >> 4);
                             const uint32_t d = taddr + (uint32_t)((b - b0) * BLK);
-                            tc::mma3_split_elect(d, dAh, dAl, dBh, dBl, idesc, c > 0 ? 1u : 0u);
+                            if (mm.lo_set)
+                                tc::mma3_split2_elect(d, d + (uint32_t)LO_COL, dAh, dAl, dBh, dBl, idesc,
+                                                      c > 0 ? 1u : 0u);
+                            else
+                                tc::mma3_split_elect(d, dAh, dAl, dBh, dBl, idesc, c > 0 ? 1u : 0u);
                         }
                         tc::mma_commit_elect(empty + st);
                         if (c == nchunk - 1) tc::mma_commit_elect(pass_done);
@@ -314,8 +330,8 @@ __device__ __forceinline__ void rollout_mma_body(const RolloutArgs& a, const Mma
         // ---------------- P2/P3: kernel-row tiles for the tensor cores ------
         float qpart = 0.0f, mv = 0.0f, mw = 0.0f, cv = 0.0f, cw = 0.0f;
         for (int g = 0; g < npass; ++g, ++pc) {
-            const int b1 = min(NB, (g + 1) * BLOCKS_PER_PASS);
-            const int b0 = g * BLOCKS_PER_PASS;
+            const int b1 = min(NB, (g + 1) * bpp);
+            const int b0 = g * bpp;
             const int nchunk = 8 * b1;
             const bool last_pass = (g == npass - 1);
             for (int c = 0; c < nchunk; ++c, ++n) {
@@ -371,16 +387,34 @@ __device__ __forceinline__ void rollout_mma_body(const RolloutArgs& a, const Mma
             if (ok && 32 * (warp & 3) < MTC) {
                 const int half_cols = (b1 - b0) * BLK / 2;
                 const uint32_t row = taddr + ((uint32_t)(32 * (warp & 3)) << 16);
-                for (int cc = 0; cc < half_cols; cc += 32) {
-                    float v[32];
-                    tc::tmem_ld32(row + (uint32_t)(hr * half_cols + cc), v);
+                // with the low set: V = main + low column sets (32 columns per
+                // load pair); without: 64 columns of V per load pair
+                const int step = mm.lo_set ? 32 : 64;
+                const uint32_t second = mm.lo_set ? (uint32_t)LO_COL : 32u;
+#pragma unroll 1
+                for (int cc = 0; cc < half_cols; cc += step) {
+                    float v[32], w[32];
+                    const uint32_t col = row + (uint32_t)(hr * half_cols + cc);
+                    tc::tmem_ld32x2(col, col + second, v, w);
                     float p0 = 0.0f, p1 = 0.0f, p2 = 0.0f, p3 = 0.0f;
+                    if (mm.lo_set) {
 #pragma unroll
-                    for (int i = 0; i < 8; ++i) {
-                        p0 = fmaf(v[i], v[i], p0);
-                        p1 = fmaf(v[8 + i], v[8 + i], p1);
-                        p2 = fmaf(v[16 + i], v[16 + i], p2);
-                        p3 = fmaf(v[24 + i], v[24 + i], p3);
+                        for (int i = 0; i < 8; ++i) {
+                            const float x0 = v[i] + w[i], x1 = v[8 + i] + w[8 + i];
+                            const float x2 = v[16 + i] + w[16 + i], x3 = v[24 + i] + w[24 + i];
+                            p0 = fmaf(x0, x0, p0);
+                            p1 = fmaf(x1, x1, p1);
+                            p2 = fmaf(x2, x2, p2);
+                            p3 = fmaf(x3, x3, p3);
+                        }
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) {
+                            p0 = fmaf(v[i], v[i], p0);
+                            p1 = fmaf(v[16 + i], v[16 + i], p1);
+                            p2 = fmaf(w[i], w[i], p2);
+                            p3 = fmaf(w[16 + i], w[16 + i], p3);
+                        }
                     }
                     qpart += (p0 + p1) + (p2 + p3);
                 }
@@ -546,13 +580,16 @@ __global__ void __launch_bounds__(THREADS, 1)
 
 }  // namespace
 
-int rollout_mma_stages(int NpM, int S, int O, int smem_optin) { return mma_stages(NpM, S, O, smem_optin); }
+int rollout_mma_stages(int NpM, int S, int O, int smem_optin, int lo_set) {
+    return mma_stages(NpM, S, O, smem_optin, lo_set ? BLOCKS_PER_PASS / 2 : BLOCKS_PER_PASS);
+}
 
 int launch_rollout_mma(const RolloutArgs& a, const MmaArgs& mm, int fmt, bool trace, cudaStream_t st) {
     const int nstage = mm.stages;
     if (nstage < 2 || nstage > NSTAGE) return fail(GPMPPI_ERR_INVALID_ARG, "rollout: bad MMA pipeline depth");
     if (mm.rps != 2 && mm.rps != 4 && mm.rps != 8) return fail(GPMPPI_ERR_INVALID_ARG, "rollout: bad threads per sample");
-    const int smem = mma_layout(nstage, mm.nblocks * BLK, mm.scene_smem ? a.S : 0, mm.scene_smem ? a.O : 0).total;
+    const int smem = mma_layout(nstage, mm.nblocks * BLK, mm.scene_smem ? a.S : 0, mm.scene_smem ? a.O : 0,
+                                mm.lo_set ? BLOCKS_PER_PASS / 2 : BLOCKS_PER_PASS).total;
     const int mtc = NPROD / mm.rps;
     const int grid = (a.K + mtc - 1) / mtc;
 #define GPM_LAUNCH_MMA(F, RR, TR)                                                                 \
@@ -583,7 +620,8 @@ int launch_rollout_mma(const RolloutArgs& a, const MmaArgs& mm, int fmt, bool tr
 namespace gpm {
 
 int rollout_mma_smem(const MmaArgs& mm, int S, int O) {
-    return mma_layout(mm.stages, mm.nblocks * BLK, mm.scene_smem ? S : 0, mm.scene_smem ? O : 0).total;
+    return mma_layout(mm.stages, mm.nblocks * BLK, mm.scene_smem ? S : 0, mm.scene_smem ? O : 0,
+                      mm.lo_set ? BLOCKS_PER_PASS / 2 : BLOCKS_PER_PASS).total;
 }
 
 int launch_rollout_mma_batched(const RolloutArgs* args, const MmaArgs* mms, const int2* items, int nitems,

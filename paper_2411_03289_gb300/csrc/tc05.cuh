@@ -84,6 +84,26 @@ __device__ __forceinline__ void mma3_split_elect(uint32_t d_tmem, uint64_t a_hi,
         : "memory");
 }
 
+// The same three products with the two small ones kept apart from the main
+// one: A_hi B_hi into d_main (accumulating only if acc0 != 0), A_hi B_lo and
+// A_lo B_hi into d_lo (the first of them accumulating only if acc0 != 0).
+// The FP32 accumulator of the large product then sees one addition per
+// chunk instead of three; the small products' rounding is 2^-11 (FP16) of
+// the main one's.
+__device__ __forceinline__ void mma3_split2_elect(uint32_t d_main, uint32_t d_lo, uint64_t a_hi, uint64_t a_lo,
+                                                  uint64_t b_hi, uint64_t b_lo, uint32_t idesc, uint32_t acc0) {
+    asm volatile(
+        "{\n\t.reg .pred e, p0, p1;\n\t"
+        "elect.sync _|e, 0xffffffff;\n\t"
+        "setp.ne.b32 p0, %7, 0;\n\t"
+        "setp.ne.b32 p1, 1, 0;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %2, %4, %6, p0;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%1], %2, %5, %6, p0;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%1], %3, %4, %6, p1;\n\t}" ::"r"(d_main), "r"(d_lo),
+        "l"(a_hi), "l"(a_lo), "l"(b_hi), "l"(b_lo), "r"(idesc), "r"(acc0)
+        : "memory");
+}
+
 // Warp-collective commit: the whole (converged) warp executes it and one lane,
 // chosen by elect.sync, issues it.
 __device__ __forceinline__ void mma_commit_elect(uint64_t* bar) {
@@ -212,20 +232,23 @@ __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
 }
 
 // 32 consecutive FP32 columns of this thread's TMEM lane (warp w reads lanes
-// 32 (w % 4) .. 32 (w % 4) + 31; the lane offset is encoded in taddr).
+// 32 (w % 4) .. 32 (w % 4) + 31; the lane offset is encoded in taddr).  The
+// wait is part of the same asm statement, so that no use of the registers
+// can be scheduled before it.
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
     uint32_t r[32];
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
         "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
           "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
           "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
           "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
           "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        : "r"(taddr)
+        : "memory");
 #pragma unroll
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }

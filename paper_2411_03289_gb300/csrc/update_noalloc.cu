@@ -96,5 +96,5 @@ extern "C" int mppi_update_noalloc(const float* costs, const float* u_tilde, con
     a.T = T;
     a.per_cta = 256;
     a.inv_lambda = 1.0f / lambda;
-    return launch_update(a, (int)n_cta, st);
+    return launch_update(a, (int)n_cta, st, false);
 }

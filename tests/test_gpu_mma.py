@@ -214,11 +214,11 @@ def test_cluster_kernel_scene_in_global_memory(lib):
     check_trace(sc, ro, tr)
 
 
-@pytest.mark.parametrize("K", [16384, 16700])
+@pytest.mark.parametrize("K", [16384, 16700, 65800])
 def test_update_sample_block_counts(lib, K):
-    """The update with 64 sample blocks (step blocks of 16 steps: 64 x 2 CTAs)
-    and with 66 (one CTA per sample block over all steps, the last block
-    ragged): weights against Alg. 1's softmax of the returned costs, U_new
+    """The update over 64, 66 (last block ragged) and 258 sample blocks (more
+    blocks than the combining CTA has threads), each with two step blocks of
+    16 steps: weights against Alg. 1's softmax of the returned costs, U_new
     against the weighted sum over the oracle's perturbed controls."""
     sc = _sc("small", 2, K=K, N=100, T=20)
     P = sc.params
