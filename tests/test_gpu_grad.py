@@ -24,6 +24,12 @@ def grad_err(g, ref):
     return float(np.max(np.abs(g - ref) / np.maximum(np.abs(ref), floor)))
 
 
+def grad_err_unfloored(g, ref):
+    """Per-component relative errors |g - ref| / |ref| (reported, not asserted)."""
+    g, ref = np.asarray(g, dtype=np.float64).ravel(), np.asarray(ref, dtype=np.float64).ravel()
+    return np.abs(g - ref) / np.maximum(np.abs(ref), 1e-30)
+
+
 def f32(x):
     return np.asarray(x, dtype=np.float32).astype(np.float64)
 
@@ -126,7 +132,8 @@ def test_grad_cfg4_sampled(lib):
     for h, vals in ref.items():
         vals = np.array(vals)
         err = np.max(np.abs(gpu_u - vals) / np.maximum(np.abs(vals), floor))
-        print("cfg4 dU", h, err)
+        print("cfg4 dU", h, err, "unfloored max", float(np.max(grad_err_unfloored(gpu_u, vals))),
+              "min |ref| / max |ref|", float(np.min(np.abs(vals)) / np.max(np.abs(vals))))
         assert err <= TOL_GRAD
     for h in (1e-3, 1e-6):
         gL = np.zeros((2, 4))
@@ -135,7 +142,8 @@ def test_grad_cfg4_sampled(lib):
                 jp, _ = O.objective(sc, O.with_lengthscale(sc.hyper, o, d, h), x0, U64, 0, sub, SLOPE)
                 jm, _ = O.objective(sc, O.with_lengthscale(sc.hyper, o, d, -h), x0, U64, 0, sub, SLOPE)
                 gL[o, d] = (jp - jm) / (2 * h)
-        print("cfg4 dl", h, grad_err(dl, gL), dl.ravel(), gL.ravel())
+        print("cfg4 dl", h, grad_err(dl, gL), "unfloored", grad_err_unfloored(dl, gL).tolist(),
+              dl.ravel(), gL.ravel())
         assert grad_err(dl, gL) <= TOL_GRAD
 
 
