@@ -491,6 +491,61 @@ def cfg3_leg(args, gp, S, dev, flush, stream, barrier):
                          "traffic": committed_traffic("rollout_mma", "cfg3")}}
 
 
+def cfg5_leg(args, gp, S, dev):
+    """Secondary leg: 64 independent controllers (K 1024..16384, T 20..100,
+    N 200..4096, FP16 split) advanced by one CUDA-graph replay of the batched
+    step (one persistent rollout launch over the work queue, one update
+    launch), after the per-shape autotuner; a few timed replays."""
+    import torch
+    scs = S.batched_scenarios(64)
+    for sc in scs:
+        sc.params.precision = PRECISIONS["fp16split"]
+    t_fit = time.perf_counter()
+    gps = [gp.gp_fit(sc.X, sc.Y, sc.hyper) for sc in scs]
+    ctrls = [gp.mppi_create(sc.params, sc.obstacles, sc.path, g) for sc, g in zip(scs, gps)]
+    batch = gp.mppi_batch_create(ctrls)
+    for i, sc in enumerate(scs):
+        batch.state[i].copy_(torch.tensor(sc.x0, dtype=torch.float32))
+        batch.U_nom[i].copy_(torch.tensor(sc.U0, dtype=torch.float32))
+    torch.cuda.synchronize()
+    t_fit = time.perf_counter() - t_fit
+    stream = torch.cuda.Stream()
+    t_tune = time.perf_counter()
+    gp.mppi_batch_autotune(batch, stream)
+    t_tune = time.perf_counter() - t_tune
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    steps = 3
+    with torch.cuda.stream(stream):
+        for _ in range(2):
+            gp.mppi_batch_graph(batch, stream)
+        stream.synchronize()
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        for i in range(steps):
+            starts[i].record(stream)
+            gp.mppi_batch_graph(batch, stream)
+            ends[i].record(stream)
+            flush.fill_(float(i))
+        stream.synchronize()
+    step_ms = [a.elapsed_time(b_) for a, b_ in zip(starts, ends)]
+    units = sum(sc.params.K * sc.params.T for sc in scs)
+    flops = sum(rollout_flops_per_sample_step(sc.N, sc.obstacles.shape[0], max(sc.path.shape[0] - 1, 1))
+                * sc.params.K * sc.params.T for sc in scs)
+    peak, note = measured_tensor_peak()
+    ach = flops / (statistics.median(step_ms) / 1e3) / 1e12
+    layouts = [gp.mppi_batch_layout(batch, i)[0] for i in range(len(scs))]
+    return {"workload": f"cfg5: 64 controllers, K {min(s.params.K for s in scs)}..{max(s.params.K for s in scs)}, "
+                        f"T {min(s.params.T for s in scs)}..{max(s.params.T for s in scs)}, "
+                        f"N {min(s.N for s in scs)}..{max(s.N for s in scs)}, fp16split, one graph replay per step",
+            "value": units * steps / (sum(step_ms) / 1e3), "unit": "sample-steps/s", "steps": steps, "warmup": 2,
+            "p50_ms": statistics.median(step_ms), "sample_steps_per_step": units,
+            "threads_per_sample_chosen": {str(r): layouts.count(r) for r in sorted(set(layouts))},
+            "fit_and_create_s": t_fit, "autotune_s": t_tune,
+            "roofline": {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                         "kernel": "k_rollout_persistent", "traffic": None,
+                         "peak_note": note + "; algorithmic flops of all controllers over the whole step"}}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -516,7 +571,8 @@ def run_ours(args):
         gps = [gp.gp_fit(X, Y, h) for X, Y, h in sc.terrains]
         ctrl = gp.mppi_create_ensemble(P, sc.obstacles, sc.path, gps, sc.terrain_w)
     else:
-        sc = S.scenario(args.workload, seed=1 + rank, precision=PRECISIONS[args.precision])
+        kw = {"T": args.horizon} if args.horizon else {}
+        sc = S.scenario(args.workload, seed=1 + rank, precision=PRECISIONS[args.precision], **kw)
         P = sc.params
         g = gp.gp_fit(sc.X, sc.Y, sc.hyper)
         ctrl = gp.mppi_create(P, sc.obstacles, sc.path, g)
@@ -594,6 +650,7 @@ def run_ours(args):
     legs = {}
     if args.workload == WORKLOAD and not terrain and not args.no_legs:
         legs["cfg3"] = cfg3_leg(args, gp, S, dev, flush, stream, barrier)
+        legs["cfg5"] = cfg5_leg(args, gp, S, dev)
     if rank != 0:
         if ws > 1:
             torch.distributed.destroy_process_group()
@@ -889,12 +946,12 @@ def run_batched(args):
                                f"T {min(s.params.T for s in scs)}..{max(s.params.T for s in scs)}, "
                                f"N {min(s.N for s in scs)}..{max(s.N for s in scs)}, one CUDA-graph replay per step",
                    "controllers": len(scs), "sample_steps_per_step": units_step,
-                   "tile_layout_threads_per_sample": chosen, "precision": args.precision,
+                   "autotune_layouts_changed": chosen, "precision": args.precision,
                    "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)",
                    "fit_and_create_s": t_fit},
-        "gpu_launches": args.steps * (2 + sum(1 for sc in scs if sc.params.precision == 0)),
+        "gpu_launches": 2 * args.steps,
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None, "kernel": "k_rollout_mma_batched",
+                     "frac": achieved / peak, "traffic": None, "kernel": "k_rollout_persistent",
                      "peak_note": note + "; whole batched step timed"},
         "cpu_baseline": None,
         "e2e": {"value": units_step * args.steps * ws / e2e_s, "unit": "sample-steps/s",
@@ -925,8 +982,10 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD, help="scenario name (cfg2 is the reported workload)")
     ap.add_argument("--precision", default="fp16split", choices=sorted(PRECISIONS))
     ap.add_argument("--batch", type=int, default=64, help="controllers in the cfg5 workload")
+    ap.add_argument("--horizon", type=int, default=None,
+                    help="override the workload's horizon T (short cases for profiler captures)")
     ap.add_argument("--no-alu-peaks", action="store_true", help="skip the FP32/SFU throughput probes")
-    ap.add_argument("--no-legs", action="store_true", help="skip the secondary workload legs (cfg3)")
+    ap.add_argument("--no-legs", action="store_true", help="skip the secondary workload legs (cfg3, cfg5)")
     ap.add_argument("--no-fp32-path", action="store_true",
                     help="skip timing the plain FP32 CUDA-core path beside the headline path")
     args = ap.parse_args()

@@ -314,9 +314,11 @@ int mppi_update_noalloc(const float* costs, const float* u_tilde, const float* U
  * device memory while batched: it starts from the controller's counter at
  * creation, advances by one per batched step, and is read back with
  * mppi_batch_get_iteration (the controller's own counter is not updated).
- * A step = all tensor-core controllers in one launch per 16-bit format (CTAs
- * over (controller, sample-tile) items, largest work first), the FP32
- * controllers one after the other, then one update launch for all. */
+ * A step = ONE persistent rollout launch (one CTA per SM) whose CTAs take
+ * (controller, sample tile) items from an atomic work queue - FP32 tiles and
+ * FP16- or BF16-split tensor-core tiles alike, longest first - then one update
+ * launch for all controllers.  Controllers whose own mppi_step would use the
+ * cluster rollout (N <= 512) run the streaming tensor-core body here. */
 int mppi_batch_create(const gpmppi_ctrl* ctrls, int32_t B, gpmppi_batch* out);
 int mppi_batch_buffers(gpmppi_batch b, int32_t i, float** state, float** U_nom, float** U_new,
                        float** weights, float** costs);
@@ -325,10 +327,21 @@ int mppi_batch_step(gpmppi_batch b, void* stream);
 /* The same iteration through a CUDA graph: captured on first use (stream
  * must be a created stream, not NULL) and replayed by every later call. */
 int mppi_batch_graph(gpmppi_batch b, void* stream);
-/* Autotuner: times the tensor-core tile layouts (2, 4 or 8 producer threads
- * per sample, i.e. 128, 64 or 32 samples per CTA) on this batch, keeps the
- * fastest and returns it in *chosen.  Blocking; restores the counters. */
+/* Autotuner, per controller shape (precision, K, T, N, lane segments,
+ * obstacles): times one wave of the controller's tiles for each tensor-core
+ * tile layout (2, 4 or 8 producer threads per sample, i.e. 128, 64 or 32
+ * samples per tile; FP32 controllers have one layout), keeps the layout with
+ * the least SM time (tiles x time per tile) and orders the work queue by the
+ * measured time per tile.  Results are kept for the process and reused for
+ * the same shape.  Runs rollouts only (their outputs are scratch; iteration
+ * counters do not move).  Blocking.  *chosen = number of controllers whose
+ * layout changed. */
 int mppi_batch_autotune(gpmppi_batch b, void* stream, int32_t* chosen);
+/* The tile layout of controller i in the batch: producer threads per sample of
+ * its tensor-core tiles (0 for an FP32 controller) and the time per tile that
+ * orders the work queue (microseconds: measured by the autotuner, else an
+ * estimate). */
+int mppi_batch_layout(gpmppi_batch b, int32_t i, int32_t* threads_per_sample, float* tile_us);
 int mppi_batch_get_iteration(gpmppi_batch b, int32_t i, uint64_t* it);
 int mppi_batch_destroy(gpmppi_batch b);
 

@@ -42,7 +42,7 @@ EXPORTS = ("gp_fit", "gp_destroy", "gp_factors", "gp_predict", "mppi_create", "m
            "mppi_destroy", "mppi_rollout_kind", "mppi_set_profiling", "mppi_last_profile", "mppi_device_status", "mppi_grad",
            "mppi_create_ensemble", "mppi_set_terrain_weights", "terrain_weights",
            "mppi_update_noalloc", "mppi_batch_create",
-           "mppi_batch_buffers", "mppi_batch_step", "mppi_batch_graph", "mppi_batch_autotune",
+           "mppi_batch_buffers", "mppi_batch_step", "mppi_batch_graph", "mppi_batch_autotune", "mppi_batch_layout",
            "mppi_batch_get_iteration", "mppi_batch_destroy", "gpmppi_philox", "gpmppi_control_noise", "gpmppi_mma_selftest", "gpmppi_alu_probe", "gpmppi_last_error",
            "gpmppi_version")
 
@@ -110,6 +110,7 @@ def load():
         "mppi_batch_step": [vp, vp],
         "mppi_batch_graph": [vp, vp],
         "mppi_batch_autotune": [vp, vp, vp],
+        "mppi_batch_layout": [vp, i32, vp, vp],
         "mppi_batch_get_iteration": [vp, i32, ctypes.POINTER(u64)],
         "mppi_batch_destroy": [vp],
         "mppi_update_noalloc": [vp, vp, vp, vp, vp, i32, i32, ctypes.c_float, vp],
@@ -560,9 +561,19 @@ def mppi_batch_graph(batch: Batch, stream=None):
 
 
 def mppi_batch_autotune(batch: Batch, stream=None) -> int:
+    """Per-shape tile layouts and queue order from measured tile times;
+    returns the number of controllers whose layout changed."""
     v = ctypes.c_int32()
     _check(load().mppi_batch_autotune(batch.handle, _stream(stream), ctypes.byref(v)))
     return v.value
+
+
+def mppi_batch_layout(batch: Batch, i: int):
+    """(producer threads per sample of controller i's tensor-core tiles (0 for
+    FP32), time per tile in microseconds)."""
+    r, t = ctypes.c_int32(), ctypes.c_float()
+    _check(load().mppi_batch_layout(batch.handle, int(i), ctypes.byref(r), ctypes.byref(t)))
+    return r.value, t.value
 
 
 def mppi_batch_get_iteration(batch: Batch, i: int) -> int:

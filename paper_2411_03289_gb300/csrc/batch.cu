@@ -1,17 +1,23 @@
 // Batched MPPI iterations over many independent controllers.
 //
-// One iteration of every controller in the batch runs as (at most) two
-// tensor-core rollout launches (one per 16-bit format) whose CTAs each take a
-// (controller, sample tile) item, plus one launch of the weights/update for all
-// controllers; controllers on the FP32 CUDA-core path are launched one after
-// the other in between.  States, nominal controls, outputs and the Philox
-// iteration counters live in device buffers owned by the batch, so the whole
-// iteration can be captured once in a CUDA graph and replayed.
+// One iteration of every controller in the batch is ONE persistent rollout
+// launch (one CTA per SM) whose CTAs take (controller, sample tile) items
+// from an atomic work queue - FP32 CUDA-core tiles and FP16- or BF16-split
+// tensor-core tiles alike, longest first - followed by one launch of the
+// weights/update for all controllers.  The autotuner picks, per controller
+// shape, the producer threads per sample of its tensor-core tiles (128, 64 or
+// 32 samples per tile) from measured tile times, and orders the queue by
+// them.  States, nominal controls, outputs and the Philox iteration counters
+// live in device buffers owned by the batch, so the whole iteration (queue
+// reset, rollout, update) can be captured once in a CUDA graph and replayed.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <numeric>
+#include <tuple>
 #include <vector>
 
 #include "common.cuh"
@@ -50,15 +56,18 @@ struct gpmppi_batch_s {
     MmaArgs* d_mm = nullptr;
     UpdateArgs* d_uargs = nullptr;
     int* d_ncta = nullptr;
-    int2* d_items[2] = {nullptr, nullptr};
-    int nitems[2] = {0, 0};
+    CUtensorMap* d_tmaps = nullptr;     // per controller: TMA map over L^-T (FP32 controllers)
+    int4* d_items = nullptr;            // (controller, tile, kind, threads per sample)
+    int nitems = 0;
+    unsigned int* d_head = nullptr;     // the work queue's next item
     int2* d_uitems = nullptr;
     int nuitems = 0;
     std::vector<RolloutArgs> h_args;
     std::vector<MmaArgs> h_mm;
-    std::vector<int> fp32_ids;
-    int rps = 2;
-    int smem[2] = {0, 0};
+    std::vector<int> rps;               // per controller: producer threads per sample (tensor cores)
+    std::vector<double> tile_us;        // per controller: estimated (or measured) time of one tile
+    int smem = 0;                       // dynamic shared memory of the persistent launch
+    int grid = 1;
     int maxT = 1;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
@@ -81,8 +90,9 @@ void free_batch(gpmppi_batch b) {
     cudaFree(b->d_mm);
     cudaFree(b->d_uargs);
     cudaFree(b->d_ncta);
-    cudaFree(b->d_items[0]);
-    cudaFree(b->d_items[1]);
+    cudaFree(b->d_tmaps);
+    cudaFree(b->d_items);
+    cudaFree(b->d_head);
     cudaFree(b->d_uitems);
     b->magic = 0;
     delete b;
@@ -95,47 +105,112 @@ void drop_graph(gpmppi_batch b) {
     b->graph = nullptr;
 }
 
-// (controller, tile) items of the tensor-core controllers of one format,
-// largest work first so that the long tiles start in the first wave
-int build_items(gpmppi_batch b, int rps) {
-    const int mtc = 256 / rps;
-    for (int f = 0; f < 2; ++f) {
-        std::vector<int> ids;
-        for (int i = 0; i < b->B; ++i)
-            if (b->ctrls[i]->fmt == f) ids.push_back(i);
-        std::stable_sort(ids.begin(), ids.end(), [&](int x, int y) {
-            const double wx = (double)b->h_args[x].T * b->h_mm[x].nblocks * (b->h_mm[x].nblocks + 1);
-            const double wy = (double)b->h_args[y].T * b->h_mm[y].nblocks * (b->h_mm[y].nblocks + 1);
-            return wx > wy;
-        });
-        std::vector<int2> items;
-        for (int i : ids) {
-            const int tiles = (b->h_args[i].K + mtc - 1) / mtc;
-            for (int t = 0; t < tiles; ++t) items.push_back(make_int2(i, t));
-        }
-        cudaFree(b->d_items[f]);
-        b->d_items[f] = nullptr;
-        b->nitems[f] = (int)items.size();
-        if (!items.empty()) {
-            GPM_CUDA(cudaMalloc(&b->d_items[f], items.size() * sizeof(int2)));
-            GPM_CUDA(cudaMemcpy(b->d_items[f], items.data(), items.size() * sizeof(int2),
-                                cudaMemcpyHostToDevice));
+int kind_of(gpmppi_ctrl c) { return c->fmt < 0 ? 0 : 1 + c->fmt; }
+
+// samples per tile of controller i
+int tile_samples(gpmppi_batch b, int i) {
+    gpmppi_ctrl c = b->ctrls[i];
+    return c->fmt < 0 ? c->mt : 256 / b->rps[i];
+}
+
+int tile_count(gpmppi_batch b, int i) {
+    const int ms = tile_samples(b, i);
+    return (b->ctrls[i]->p.K + ms - 1) / ms;
+}
+
+// time of one tile before anything was measured: proportional to the
+// tensor-core MMAs of its horizon (the FP32 path taken ~8x slower per sample)
+double tile_estimate(gpmppi_batch b, int i) {
+    gpmppi_ctrl c = b->ctrls[i];
+    const double T = c->p.T, np = c->gp->g.Np > 0 ? c->gp->g.Np : 1;
+    if (c->fmt < 0) return T * np * np * c->mt / 128.0 * 8.0e-6;
+    return T * np * np * (c->mm.lo_set ? 1.5 : 1.0) * 1.0e-6;
+}
+
+// the work queue: every controller's tiles, longest tile first
+int build_items(gpmppi_batch b) {
+    std::vector<int> ids(b->B);
+    std::iota(ids.begin(), ids.end(), 0);
+    std::stable_sort(ids.begin(), ids.end(), [&](int x, int y) { return b->tile_us[x] > b->tile_us[y]; });
+    std::vector<int4> items;
+    int smem = 0;
+    for (int i : ids) {
+        gpmppi_ctrl c = b->ctrls[i];
+        const int n = tile_count(b, i);
+        for (int t = 0; t < n; ++t) items.push_back(make_int4(i, t, kind_of(c), c->fmt < 0 ? 0 : b->rps[i]));
+        if (c->fmt < 0) {
+            smem = std::max(smem, rollout_fp32_smem_bytes(c->gp->g.Np, rollout_fp32_mtp(c->gp->g.Np), c->stages));
+        } else {
+            MmaArgs mm = c->mm;
+            mm.rps = b->rps[i];
+            smem = std::max(smem, rollout_mma_smem(mm, c->S, c->O));
         }
     }
-    b->rps = rps;
+    // each controller's tensor-core layout (threads per sample) as chosen
+    for (int i = 0; i < b->B; ++i) b->h_mm[i].rps = b->rps[i];
+    GPM_CUDA(cudaMemcpy(b->d_mm, b->h_mm.data(), sizeof(MmaArgs) * b->B, cudaMemcpyHostToDevice));
+    cudaFree(b->d_items);
+    b->d_items = nullptr;
+    b->nitems = (int)items.size();
+    if (!items.empty()) {
+        GPM_CUDA(cudaMalloc(&b->d_items, items.size() * sizeof(int4)));
+        GPM_CUDA(cudaMemcpy(b->d_items, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    }
+    int nsm = 0;
+    GPM_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, b->device));
+    b->grid = std::max(1, std::min(nsm, b->nitems));
+    b->smem = smem;
     drop_graph(b);
     return GPMPPI_OK;
 }
 
 int enqueue_step(gpmppi_batch b, cudaStream_t st) {
     int rc;
-    for (int f = 0; f < 2; ++f)
-        if ((rc = launch_rollout_mma_batched(b->d_args, b->d_mm, b->d_items[f], b->nitems[f], f, b->rps,
-                                             b->smem[f], st)))
-            return rc;
-    for (int i : b->fp32_ids)
-        if ((rc = launch_rollout_fp32(b->h_args[i], &b->ctrls[i]->tmW, false, st))) return rc;
+    GPM_CUDA(cudaMemsetAsync(b->d_head, 0, sizeof(unsigned int), st));
+    if ((rc = launch_rollout_persistent(b->d_args, b->d_mm, b->d_tmaps, b->d_items, b->nitems, b->d_head, b->grid,
+                                        b->smem, st)))
+        return rc;
     return launch_update_batched(b->d_uargs, b->d_uitems, b->d_ncta, b->iters, b->nuitems, b->maxT, st);
+}
+
+// Measured tile times per controller shape, kept for the process: a shape is
+// (precision, K, T, Np, lane segments, obstacles) and the value (threads per
+// sample, microseconds per tile).
+using ShapeKey = std::tuple<int, int, int, int, int, int>;
+std::map<ShapeKey, std::pair<int, double>> g_tuned;
+std::mutex g_tuned_mu;
+
+ShapeKey shape_of(gpmppi_ctrl c) {
+    return ShapeKey(c->fmt, c->p.K, c->p.T, c->gp->g.Np, c->S, c->O);
+}
+
+// time of one wave of tiles of controller i (at most one tile per SM) with
+// rps producer threads per sample (tensor cores) or its FP32 tiles
+int time_wave(gpmppi_batch b, int i, int rps, int nsm, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1,
+              double* us, int* tiles_out) {
+    gpmppi_ctrl c = b->ctrls[i];
+    RolloutArgs a = b->h_args[i];
+    const int ms = c->fmt < 0 ? c->mt : 256 / rps;
+    const int tiles = (c->p.K + ms - 1) / ms;
+    a.K = std::min(c->p.K, nsm * ms);           // one wave; u~ is laid out for this K (scratch)
+    MmaArgs mm = c->mm;
+    mm.rps = rps;
+    int rc = GPMPPI_OK;
+    float best = 1e30f;
+    for (int rep = 0; rep < 3 && !rc; ++rep) {
+        cudaEventRecord(e0, st);
+        rc = c->fmt < 0 ? launch_rollout_fp32(a, &c->tmW, false, st) : launch_rollout_mma(a, mm, c->fmt, false, st);
+        cudaEventRecord(e1, st);
+        if (rc) break;
+        if (cudaEventSynchronize(e1) != cudaSuccess) return cuda_fail(cudaGetLastError(), "mppi_batch_autotune");
+        float ms_ = 0.0f;
+        cudaEventElapsedTime(&ms_, e0, e1);
+        if (rep > 0) best = std::min(best, ms_);      // the first launch warms up
+    }
+    if (rc) return rc;
+    *us = 1e3 * best;
+    *tiles_out = tiles;
+    return GPMPPI_OK;
 }
 
 }  // namespace
@@ -189,7 +264,9 @@ int mppi_batch_create(const gpmppi_ctrl* ctrls, int32_t B, gpmppi_batch* out) {
             (rc = alloc((void**)&b->d_args, sizeof(RolloutArgs) * B)) ||
             (rc = alloc((void**)&b->d_mm, sizeof(MmaArgs) * B)) ||
             (rc = alloc((void**)&b->d_uargs, sizeof(UpdateArgs) * B)) ||
-            (rc = alloc((void**)&b->d_ncta, sizeof(int) * B)))
+            (rc = alloc((void**)&b->d_ncta, sizeof(int) * B)) ||
+            (rc = alloc((void**)&b->d_tmaps, sizeof(CUtensorMap) * B)) ||
+            (rc = alloc((void**)&b->d_head, sizeof(unsigned int))))
             return fail_free(rc);
         std::vector<unsigned long long> its(B);
         std::vector<UpdateArgs> uargs(B);
@@ -197,6 +274,9 @@ int mppi_batch_create(const gpmppi_ctrl* ctrls, int32_t B, gpmppi_batch* out) {
         std::vector<int2> uitems;
         b->h_args.resize(B);
         b->h_mm.resize(B);
+        b->rps.assign(B, 2);
+        b->tile_us.assign(B, 0.0);
+        std::vector<CUtensorMap> tmaps(B);
         const float zero_state[5] = {0, 0, 0, 0, 0};
         for (int i = 0; i < B; ++i) {
             gpmppi_ctrl c = ctrls[i];
@@ -207,10 +287,16 @@ int mppi_batch_create(const gpmppi_ctrl* ctrls, int32_t B, gpmppi_batch* out) {
             a.costs = c->costs;
             b->h_args[i] = a;
             b->h_mm[i] = c->mm;
-            if (c->fmt < 0) {
-                b->fp32_ids.push_back(i);
-            } else {
-                b->smem[c->fmt] = std::max(b->smem[c->fmt], rollout_mma_smem(c->mm, c->S, c->O));
+            tmaps[i] = c->tmW;
+            if (c->fmt >= 0) b->rps[i] = c->mm.rps;
+            b->tile_us[i] = tile_estimate(b, i);
+            {
+                std::lock_guard<std::mutex> lock(g_tuned_mu);
+                auto hit = g_tuned.find(shape_of(c));
+                if (hit != g_tuned.end()) {
+                    if (c->fmt >= 0) b->rps[i] = hit->second.first;
+                    b->tile_us[i] = hit->second.second;
+                }
             }
             UpdateArgs& u = uargs[i];
             u.costs = c->costs;
@@ -232,6 +318,8 @@ int mppi_batch_create(const gpmppi_ctrl* ctrls, int32_t B, gpmppi_batch* out) {
         if (e == cudaSuccess) e = cudaMemcpy(b->d_mm, b->h_mm.data(), sizeof(MmaArgs) * B, cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemcpy(b->d_uargs, uargs.data(), sizeof(UpdateArgs) * B, cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemcpy(b->d_ncta, ncta.data(), sizeof(int) * B, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(b->d_tmaps, tmaps.data(), sizeof(CUtensorMap) * B, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemset(b->d_head, 0, sizeof(unsigned int));
         if (e == cudaSuccess) e = cudaMemset(b->states, 0, sizeof(float) * 5 * B);
         if (e == cudaSuccess) e = cudaMemset(b->U_nom, 0, sizeof(float) * b->utotal);
         if (e == cudaSuccess) e = cudaMemset(b->U_new, 0, sizeof(float) * b->utotal);
@@ -241,7 +329,7 @@ int mppi_batch_create(const gpmppi_ctrl* ctrls, int32_t B, gpmppi_batch* out) {
             e = cudaMemcpy(b->d_uitems, uitems.data(), uitems.size() * sizeof(int2), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) return fail_free(cuda_fail(e, "mppi_batch_create: upload"));
         b->nuitems = (int)uitems.size();
-        if ((rc = build_items(b, 2))) return fail_free(rc);
+        if ((rc = build_items(b))) return fail_free(rc);
         *out = b;
         return GPMPPI_OK;
     } catch (...) {
@@ -293,43 +381,66 @@ int mppi_batch_graph(gpmppi_batch b, void* stream) {
 int mppi_batch_autotune(gpmppi_batch b, void* stream, int32_t* chosen) {
     if (!valid_batch(b)) return fail(GPMPPI_ERR_INVALID_ARG, "mppi_batch_autotune: invalid handle");
     cudaStream_t st = (cudaStream_t)stream;
-    if (b->nitems[0] + b->nitems[1] == 0) {
-        if (chosen) *chosen = b->rps;
-        return GPMPPI_OK;
-    }
-    // trial steps advance the iteration counters: keep and restore them
-    std::vector<unsigned long long> saved(b->B);
-    GPM_CUDA(cudaMemcpy(saved.data(), b->iters, sizeof(unsigned long long) * b->B, cudaMemcpyDeviceToHost));
+    int nsm = 0;
+    GPM_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, b->device));
     cudaEvent_t e0, e1;
     GPM_CUDA(cudaEventCreate(&e0));
     GPM_CUDA(cudaEventCreate(&e1));
-    const int cand[3] = {2, 4, 8};
-    float best_ms = 1e30f;
-    int best = 2, rc = GPMPPI_OK;
-    for (int r : cand) {
-        if ((rc = build_items(b, r))) break;
-        if ((rc = enqueue_step(b, st))) break;             // warm-up
-        cudaEventRecord(e0, st);
-        for (int rep = 0; rep < 2 && !rc; ++rep) rc = enqueue_step(b, st);
-        cudaEventRecord(e1, st);
+    // Per controller shape: one wave of its tiles timed for each tile layout
+    // (tensor cores: 2, 4 or 8 producer threads per sample, i.e. 128, 64 or
+    // 32 samples per tile; FP32: its one layout); the layout with the least
+    // SM time (tiles x time per tile) is kept, and the time per tile orders
+    // the work queue.  Only rollouts run (scratch outputs); no update, so the
+    // iteration counters do not move.
+    int rc = GPMPPI_OK, changed = 0;
+    for (int i = 0; i < b->B && !rc; ++i) {
+        gpmppi_ctrl c = b->ctrls[i];
+        const ShapeKey key = shape_of(c);
+        {
+            std::lock_guard<std::mutex> lock(g_tuned_mu);
+            auto hit = g_tuned.find(key);
+            if (hit != g_tuned.end()) {
+                if (c->fmt >= 0 && b->rps[i] != hit->second.first) ++changed;
+                if (c->fmt >= 0) b->rps[i] = hit->second.first;
+                b->tile_us[i] = hit->second.second;
+                continue;
+            }
+        }
+        int best_r = c->fmt < 0 ? 0 : b->rps[i];
+        double best_cost = 1e300, best_us = b->tile_us[i];
+        const int cand[3] = {2, 4, 8};
+        for (int r : cand) {
+            if (c->fmt < 0 && r != 2) break;            // FP32 tiles have one layout
+            double us = 0.0;
+            int tiles = 0;
+            if ((rc = time_wave(b, i, r, nsm, st, e0, e1, &us, &tiles))) break;
+            const double cost = us * tiles;              // SM-microseconds of the controller's tiles
+            if (cost < best_cost) {
+                best_cost = cost;
+                best_us = us;
+                best_r = c->fmt < 0 ? 0 : r;
+            }
+        }
         if (rc) break;
-        if (cudaEventSynchronize(e1) != cudaSuccess) {
-            rc = cuda_fail(cudaGetLastError(), "mppi_batch_autotune");
-            break;
-        }
-        float ms = 0.0f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (ms < best_ms) {
-            best_ms = ms;
-            best = r;
-        }
+        if (c->fmt >= 0 && b->rps[i] != best_r) ++changed;
+        if (c->fmt >= 0) b->rps[i] = best_r;
+        b->tile_us[i] = best_us;
+        std::lock_guard<std::mutex> lock(g_tuned_mu);
+        g_tuned[key] = std::make_pair(best_r, best_us);
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc) return rc;
-    GPM_CUDA(cudaMemcpy(b->iters, saved.data(), sizeof(unsigned long long) * b->B, cudaMemcpyHostToDevice));
-    if ((rc = build_items(b, best))) return rc;
-    if (chosen) *chosen = best;
+    if ((rc = build_items(b))) return rc;
+    if (chosen) *chosen = changed;
+    return GPMPPI_OK;
+}
+
+int mppi_batch_layout(gpmppi_batch b, int32_t i, int32_t* threads_per_sample, float* tile_us) {
+    if (!valid_batch(b)) return fail(GPMPPI_ERR_INVALID_ARG, "mppi_batch_layout: invalid handle");
+    if (i < 0 || i >= b->B) return fail(GPMPPI_ERR_INVALID_ARG, "mppi_batch_layout: index out of range");
+    if (threads_per_sample) *threads_per_sample = b->ctrls[i]->fmt < 0 ? 0 : b->rps[i];
+    if (tile_us) *tile_us = (float)b->tile_us[i];
     return GPMPPI_OK;
 }
 

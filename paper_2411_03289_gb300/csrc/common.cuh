@@ -341,9 +341,13 @@ int rollout_fp32_stages(int Np, int smem_optin);
 int launch_update(const UpdateArgs& a, int n_cta, cudaStream_t st, bool after_rollout);
 int launch_update_batched(const UpdateArgs* args, const int2* items, const int* ncta,
                           unsigned long long* iters, int nitems, int maxT, cudaStream_t st);
-int launch_rollout_mma_batched(const RolloutArgs* args, const MmaArgs* mms, const int2* items, int nitems,
-                               int fmt, int rps, int smem, cudaStream_t st);
 int rollout_mma_smem(const MmaArgs& mm, int S, int O);
+// Batched persistent rollout: `grid` CTAs (one per SM) take items (controller,
+// tile, kind: 0 FP32 / 1 FP16 split / 2 BF16 split, producer threads per
+// sample) from the queue, advancing *head (zero before the launch).
+int launch_rollout_persistent(const RolloutArgs* args, const MmaArgs* mms, const CUtensorMap* tmaps,
+                              const int4* items, int nitems, unsigned int* head, int grid, int smem,
+                              cudaStream_t st);
 int launch_gp_predict(const GpDevice& g, const float* Z, int M, float* mean, float* var,
                       cudaStream_t st);
 int gp_fit_device(GpDevice& g, const double* X, const double* Y, int N, cudaStream_t st);

@@ -33,6 +33,7 @@
 #include <cfloat>
 
 #include "common.cuh"
+#include "rollout_fp32_body.cuh"
 #include "tc05.cuh"
 
 namespace gpm {
@@ -145,9 +146,14 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 // R producer threads per sample: a CTA owns MTC = 256 / R samples (rows
 // m >= MTC of the 128-row MMA tile are never written; their TMEM lanes are
 // not read) and each thread makes KPT = 16 / R points of every chunk.
+// tmem_given: kTmemAlloc to allocate the 512 TMEM columns here (and free them
+// at the end), else the base of columns the caller holds (the persistent
+// batched kernel allocates once per CTA).
+constexpr uint32_t kTmemAlloc = 0xFFFFFFFFu;
+
 template <int FMT, int R, bool TRACE>
 __device__ __forceinline__ void rollout_mma_body(const RolloutArgs& a, const MmaArgs& mm, int tile,
-                                                 unsigned char* sm) {
+                                                 unsigned char* sm, uint32_t tmem_given) {
     constexpr int MTC = NPROD / R;
     constexpr int KPT = KC / R;
     const int nstage = mm.stages;
@@ -208,7 +214,11 @@ __device__ __forceinline__ void rollout_mma_body(const RolloutArgs& a, const Mma
     const float4* segp = mm.scene_smem ? seg_s : a.seg;
     const float* il2p = mm.scene_smem ? il2_s : a.seg_il2;
     const float* obsp = mm.scene_smem ? obs_s : a.obst;
-    if (warp == 0 && NB > 0) tc::tmem_alloc(tslot, 512);
+    if (tmem_given == kTmemAlloc) {
+        if (warp == 0 && NB > 0) tc::tmem_alloc(tslot, 512);
+    } else if (tid == 0) {
+        *tslot = tmem_given;
+    }
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
@@ -557,28 +567,125 @@ __device__ __forceinline__ void rollout_mma_body(const RolloutArgs& a, const Mma
     }
     tc::fence_before_sync();
     producers_sync();
-    if (warp == 0 && NB > 0) tc::tmem_dealloc(taddr, 512);
+    if (tmem_given == kTmemAlloc && warp == 0 && NB > 0) tc::tmem_dealloc(taddr, 512);
 }
 
 template <int FMT, int R, bool TRACE>
 __global__ void __launch_bounds__(THREADS, 1) k_rollout_mma(const RolloutArgs a, const MmaArgs mm) {
     extern __shared__ __align__(1024) unsigned char sm[];
-    rollout_mma_body<FMT, R, TRACE>(a, mm, blockIdx.x, sm);
+    rollout_mma_body<FMT, R, TRACE>(a, mm, blockIdx.x, sm, kTmemAlloc);
 }
 
-// Many controllers in one launch: CTA i runs tile items[i].y of controller
-// items[i].x (items ordered by decreasing work), with that controller's
-// arguments, state and Philox iteration read from device memory.
-template <int FMT, int R>
+// ---------------------------------------------------------------------------
+// Batched step of many controllers as ONE persistent launch: one CTA per SM
+// takes items from an atomic work queue until it is empty.  An item is
+// (controller, sample tile, kind, producer threads per sample); kind 0 runs the
+// FP32 CUDA-core rollout body on warps 0-7 (warps 8-9 wait), kinds 1 and 2 the
+// tensor-core body with FP16 or BF16 split operands.  The queue holds the
+// items in decreasing order of their estimated time (longest first).  The CTA
+// holds its 512 TMEM columns for the whole launch; between items every role of
+// the CTA meets at a barrier and the previous item's mbarriers are
+// invalidated before their shared memory is reused.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void mbar_inval(uint64_t* bar) {
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(tc::smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ int fp32_mtp(int Np) { return Np <= 1024 ? 32 : (Np <= 2048 ? 16 : 8); }
+
+// invalidate the mbarriers an item initialised (thread 0, after every role is done)
+__device__ void inval_item_barriers(const RolloutArgs& a, const MmaArgs& mm, int kind, unsigned char* sm) {
+    if (kind == 0) {
+        const int mtp = fp32_mtp(a.Np);
+        const int off = mtp == 32 ? f32r::Smem<32>::bars(a.Np, a.stages)
+                                  : (mtp == 16 ? f32r::Smem<16>::bars(a.Np, a.stages) : f32r::Smem<8>::bars(a.Np, a.stages));
+        uint64_t* bars = reinterpret_cast<uint64_t*>(sm + off);
+        for (int i = 0; i < f32r::WARPS * a.stages; ++i) mbar_inval(bars + i);
+        return;
+    }
+    const int bpp = mm.lo_set ? BLOCKS_PER_PASS / 2 : BLOCKS_PER_PASS;
+    const MLayout L = mma_layout(mm.stages, mm.nblocks * BLK, mm.scene_smem ? a.S : 0, mm.scene_smem ? a.O : 0, bpp);
+    uint64_t* a_full = reinterpret_cast<uint64_t*>(sm + L.bars);
+    for (int i = 0; i < mm.stages; ++i) {
+        mbar_inval(a_full + i);
+        mbar_inval(a_full + NSTAGE + i);
+        mbar_inval(a_full + 2 * NSTAGE + i);
+    }
+    for (int i = 0; i < 3; ++i) mbar_inval(a_full + 3 * NSTAGE + i);
+}
+
 __global__ void __launch_bounds__(THREADS, 1)
-    k_rollout_mma_batched(const RolloutArgs* __restrict__ args, const MmaArgs* __restrict__ mms,
-                          const int2* __restrict__ items) {
+    k_rollout_persistent(const RolloutArgs* __restrict__ args, const MmaArgs* __restrict__ mms,
+                         const CUtensorMap* __restrict__ tmaps, const int4* __restrict__ items, int nitems,
+                         unsigned int* __restrict__ head) {
     extern __shared__ __align__(1024) unsigned char sm[];
-    const int2 it = items[blockIdx.x];
-    rollout_mma_body<FMT, R, false>(args[it.x], mms[it.x], it.y, sm);
+    __shared__ uint32_t tbase;
+    __shared__ int cur, prev;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    if (warp == 0) {
+        // held for the whole launch (one CTA per SM), so the permit is not relinquished
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
+                         tc::smem_addr(&tbase))
+                     : "memory");
+    }
+    if (tid == 0) prev = -1;
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t taddr = tbase;
+    for (;;) {
+        if (tid == 0) {
+            if (prev >= 0) {
+                const int4 pi = items[prev];
+                inval_item_barriers(args[pi.x], mms[pi.x], pi.z, sm);
+            }
+            cur = (int)atomicAdd(head, 1u);
+        }
+        __syncthreads();
+        const int item = cur;
+        if (item >= nitems) break;
+        const int4 it = items[item];
+        const RolloutArgs& a = args[it.x];
+        if (it.z == 0) {
+            if (warp < f32r::WARPS) {
+                const int mtp = fp32_mtp(a.Np);
+                if (mtp == 32) f32r::rollout_fp32_body<32, false>(a, tmaps + it.x, it.y, sm);
+                else if (mtp == 16) f32r::rollout_fp32_body<16, false>(a, tmaps + it.x, it.y, sm);
+                else f32r::rollout_fp32_body<8, false>(a, tmaps + it.x, it.y, sm);
+            }
+        } else {
+            const MmaArgs& mm = mms[it.x];
+            if (it.z == 1) {
+                if (it.w == 2) rollout_mma_body<0, 2, false>(a, mm, it.y, sm, taddr);
+                else if (it.w == 4) rollout_mma_body<0, 4, false>(a, mm, it.y, sm, taddr);
+                else rollout_mma_body<0, 8, false>(a, mm, it.y, sm, taddr);
+            } else {
+                if (it.w == 2) rollout_mma_body<1, 2, false>(a, mm, it.y, sm, taddr);
+                else if (it.w == 4) rollout_mma_body<1, 4, false>(a, mm, it.y, sm, taddr);
+                else rollout_mma_body<1, 8, false>(a, mm, it.y, sm, taddr);
+            }
+        }
+        // every role of this CTA is done with the item (TMEM reads included)
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        if (tid == 0) prev = item;
+    }
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(taddr, 512);
 }
 
 }  // namespace
+
+int launch_rollout_persistent(const RolloutArgs* args, const MmaArgs* mms, const CUtensorMap* tmaps,
+                              const int4* items, int nitems, unsigned int* head, int grid, int smem,
+                              cudaStream_t st) {
+    if (nitems == 0) return GPMPPI_OK;
+    GPM_CUDA(cudaFuncSetAttribute(k_rollout_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    k_rollout_persistent<<<grid, THREADS, smem, st>>>(args, mms, tmaps, items, nitems, head);
+    GPM_CUDA(cudaGetLastError());
+    return GPMPPI_OK;
+}
 
 int rollout_mma_stages(int NpM, int S, int O, int smem_optin, int lo_set) {
     return mma_stages(NpM, S, O, smem_optin, lo_set ? BLOCKS_PER_PASS / 2 : BLOCKS_PER_PASS);
@@ -622,25 +729,6 @@ namespace gpm {
 int rollout_mma_smem(const MmaArgs& mm, int S, int O) {
     return mma_layout(mm.stages, mm.nblocks * BLK, mm.scene_smem ? S : 0, mm.scene_smem ? O : 0,
                       mm.lo_set ? BLOCKS_PER_PASS / 2 : BLOCKS_PER_PASS).total;
-}
-
-int launch_rollout_mma_batched(const RolloutArgs* args, const MmaArgs* mms, const int2* items, int nitems,
-                               int fmt, int rps, int smem, cudaStream_t st) {
-    if (nitems == 0) return GPMPPI_OK;
-#define GPM_LAUNCH_MMA_B(F, RR)                                                                   \
-    do {                                                                                          \
-        auto kern = k_rollout_mma_batched<F, RR>;                                                 \
-        GPM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));  \
-        kern<<<nitems, THREADS, smem, st>>>(args, mms, items);                                    \
-    } while (0)
-    if (fmt == 0) {
-        if (rps == 2) GPM_LAUNCH_MMA_B(0, 2); else if (rps == 4) GPM_LAUNCH_MMA_B(0, 4); else GPM_LAUNCH_MMA_B(0, 8);
-    } else {
-        if (rps == 2) GPM_LAUNCH_MMA_B(1, 2); else if (rps == 4) GPM_LAUNCH_MMA_B(1, 4); else GPM_LAUNCH_MMA_B(1, 8);
-    }
-#undef GPM_LAUNCH_MMA_B
-    GPM_CUDA(cudaGetLastError());
-    return GPMPPI_OK;
 }
 
 }  // namespace gpm

@@ -86,8 +86,12 @@ def test_batch_graph_replay_equals_steps(lib):
 def test_batch_autotune_keeps_parity(lib):
     import torch
     b, ctrls, items = _batch(lib)
-    chosen = lib.mppi_batch_autotune(b)
-    assert chosen in (2, 4, 8)
+    changed = lib.mppi_batch_autotune(b)
+    assert 0 <= changed <= len(SPECS)
+    for i, spec in enumerate(SPECS):
+        rps, tile_us = lib.mppi_batch_layout(b, i)
+        assert rps == (0 if spec[5] == 0 else rps) and (rps == 0 or rps in (2, 4, 8))
+        assert tile_us > 0.0
     assert all(lib.mppi_batch_get_iteration(b, i) == 0 for i in range(len(SPECS)))
     lib.mppi_batch_step(b)
     torch.cuda.synchronize()
@@ -108,3 +112,57 @@ def test_batch_rejects_bad_groups(lib):
     with pytest.raises(lib.GpmppiError) as ei:
         lib.mppi_batch_create([c, c2])
     assert ei.value.code == lib.GPMPPI_ERR_UNSUPPORTED
+
+
+def _cfg5_scenarios(B=64):
+    """cfg5: 64 controllers, K 1024..16384, T 20..100, N 200..4096, 4..64
+    obstacles, sinusoid / figure-eight paths; arithmetic cycling FP16 split,
+    FP16 split, BF16 split, FP32."""
+    scs = S.batched_scenarios(B)
+    for i, sc in enumerate(scs):
+        sc.params.precision = (2, 2, 1, 0)[i % 4]
+    return scs
+
+
+def test_batch_cfg5_shapes_sampled_rows_and_properties(lib):
+    """The batched persistent launch at the cfg5 shapes, after autotuning:
+    for every controller, the costs of sampled rows against the oracle's FP64
+    rollout of those rows (indicator-tie protocol), the weights against the
+    softmax of the controller's costs, and U_new against the weighted sum of
+    the oracle's clamped sampled controls."""
+    import torch
+    from parity import TOL_COST, assert_close, reconcile_costs
+    scs = _cfg5_scenarios()
+    gps = [lib.gp_fit(sc.X, sc.Y, sc.hyper) for sc in scs]
+    ctrls = [lib.mppi_create(sc.params, sc.obstacles, sc.path, g) for sc, g in zip(scs, gps)]
+    b = lib.mppi_batch_create(ctrls)
+    for i, sc in enumerate(scs):
+        b.state[i].copy_(torch.tensor(sc.x0, dtype=torch.float32))
+        b.U_nom[i].copy_(torch.tensor(sc.U0, dtype=torch.float32))
+    lib.mppi_batch_autotune(b)
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        lib.mppi_batch_graph(b, st)
+    st.synchronize()
+    rng = np.random.default_rng(5)
+    layouts = []
+    for i, sc in enumerate(scs):
+        P = sc.params
+        assert lib.mppi_batch_get_iteration(b, i) == 1
+        c = to_np(b.costs[i])
+        w = to_np(b.weights[i])
+        U_new = to_np(b.U_new[i])
+        rows = np.unique(np.concatenate([[0, P.K - 1], rng.integers(0, P.K, 2)]))
+        fits = O.gp_fit(sc.X, sc.Y, sc.hyper)
+        ro = O.rollout(sc, fits, sc.x0.astype(np.float32).astype(np.float64), sc.U0, 0, samples=rows)
+        ref_c, _ = reconcile_costs(sc, ro, c[rows], rows)
+        assert_close(c[rows], ref_c, TOL_COST, what=f"controller {i} costs")
+        assert np.max(np.abs(w - O.mppi_weights(c, P.lam))) <= 1e-5
+        ut = np.empty((P.K, P.T, 2))
+        for k in range(P.T):
+            eps = O.control_noise(P.seed, k, np.arange(P.K), 0, P.sigma)
+            ut[:, k] = np.clip(sc.U0[k] + eps, P.u_min, P.u_max)
+        U_chk = sc.U0 + np.einsum("s,skc->kc", w, ut - sc.U0[None])
+        assert np.max(np.abs(U_new - U_chk)) <= TOL_U, f"controller {i}"
+        layouts.append(lib.mppi_batch_layout(b, i))
+    print("cfg5 layouts (threads per sample, us per tile):", layouts)
