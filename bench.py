@@ -572,6 +572,8 @@ def run_ours(args):
         ctrl = gp.mppi_create_ensemble(P, sc.obstacles, sc.path, gps, sc.terrain_w)
     else:
         kw = {"T": args.horizon} if args.horizon else {}
+        if args.samples:
+            kw["K"] = args.samples
         sc = S.scenario(args.workload, seed=1 + rank, precision=PRECISIONS[args.precision], **kw)
         P = sc.params
         g = gp.gp_fit(sc.X, sc.Y, sc.hyper)
@@ -750,7 +752,10 @@ def run_grad(args):
         torch.cuda.set_device(0)
     B.build()
     dev = torch.device("cuda", torch.cuda.current_device())
-    sc = S.scenario("cfg4", seed=1 + rank)
+    kw = {"T": args.horizon} if args.horizon else {}
+    if args.samples:
+        kw["K"] = args.samples
+    sc = S.scenario("cfg4", seed=1 + rank, **kw)
     P = sc.params
     g = gp.gp_fit(sc.X, sc.Y, sc.hyper)
     ctrl = gp.mppi_create(P, sc.obstacles, sc.path, g)
@@ -984,6 +989,8 @@ def main():
     ap.add_argument("--batch", type=int, default=64, help="controllers in the cfg5 workload")
     ap.add_argument("--horizon", type=int, default=None,
                     help="override the workload's horizon T (short cases for profiler captures)")
+    ap.add_argument("--samples", type=int, default=None,
+                    help="override the workload's sample count K (small cases for profiler captures)")
     ap.add_argument("--no-alu-peaks", action="store_true", help="skip the FP32/SFU throughput probes")
     ap.add_argument("--no-legs", action="store_true", help="skip the secondary workload legs (cfg3, cfg5)")
     ap.add_argument("--no-fp32-path", action="store_true",

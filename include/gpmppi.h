@@ -377,6 +377,21 @@ int gpmppi_mma_selftest(int32_t fmt, int32_t N, int32_t K, int32_t variant, cons
  * Asynchronous on stream; time it with events on that stream. */
 int gpmppi_alu_probe(int32_t kind, int32_t blocks, int32_t iters, float* out, void* stream);
 
+/* Failure-detection hook (no counterpart in the paper) for the FP32
+ * CUDA-core rollout of this controller:
+ *   ns            time limit of each bounded wait for a tile copy of L^-T, in
+ *                 nanoseconds (default 2e9)
+ *   expire_first  non-zero: before any copy, one warp of every CTA waits,
+ *                 bounded by ns, on an mbarrier that nothing arrives on, so
+ *                 that the wait runs out
+ * A wait that runs out records GPMPPI_ERR_TIMEOUT in the controller's status
+ * word (mppi_device_status reports and clears it) and stops that warp's copies;
+ * the copies in flight land (bounded) before the CTA exits and the kernel ends
+ * normally, so the context stays usable; that step's outputs are unspecified.
+ * A host-side setting of this controller only (not applied in batches); no GPU
+ * setting is changed. */
+int mppi_set_wait_limit(gpmppi_ctrl c, uint64_t ns, int32_t expire_first);
+
 /* Thread-local message describing the last failed call ("" if none). */
 const char* gpmppi_last_error(void);
 

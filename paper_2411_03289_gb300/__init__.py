@@ -39,7 +39,7 @@ GPMPPI_KERNEL_ENSEMBLE = 3
 # names every build of the library exports (checked by the CPU test suite)
 EXPORTS = ("gp_fit", "gp_destroy", "gp_factors", "gp_predict", "mppi_create", "mppi_step",
            "mppi_rollout_trace", "mppi_set_iteration", "mppi_get_iteration", "mppi_nominal_sxy",
-           "mppi_destroy", "mppi_rollout_kind", "mppi_set_profiling", "mppi_last_profile", "mppi_device_status", "mppi_grad",
+           "mppi_destroy", "mppi_rollout_kind", "mppi_set_wait_limit", "mppi_set_profiling", "mppi_last_profile", "mppi_device_status", "mppi_grad",
            "mppi_create_ensemble", "mppi_set_terrain_weights", "terrain_weights",
            "mppi_update_noalloc", "mppi_batch_create",
            "mppi_batch_buffers", "mppi_batch_step", "mppi_batch_graph", "mppi_batch_autotune", "mppi_batch_layout",
@@ -98,6 +98,7 @@ def load():
         "mppi_nominal_sxy": [vp, vp, vp],
         "mppi_destroy": [vp],
         "mppi_rollout_kind": [vp, vp],
+        "mppi_set_wait_limit": [vp, u64, i32],
         "mppi_set_profiling": [vp, i32],
         "mppi_last_profile": [vp, vp, vp],
         "mppi_device_status": [vp],
@@ -361,6 +362,12 @@ def mppi_rollout_kind(ctrl: Ctrl) -> int:
     v = ctypes.c_int32()
     _check(load().mppi_rollout_kind(ctrl.handle, ctypes.byref(v)))
     return v.value
+
+
+def mppi_set_wait_limit(ctrl: Ctrl, ns: int, expire_first: bool = False):
+    """Failure-detection hook of the FP32 rollout: limit (ns) of each bounded
+    tile-copy wait and, with expire_first, a first wait that nothing completes."""
+    _check(load().mppi_set_wait_limit(ctrl.handle, int(ns), 1 if expire_first else 0))
 
 
 def mppi_set_profiling(ctrl: Ctrl, on: bool):

@@ -103,6 +103,7 @@ void free_gp(gpmppi_gp h) {
         cudaFree(g.cl_tiles[f]);
     }
     cudaFree(g.cl_xa);
+    cudaFree(g.mma_xa);
     cudaFree(g.Wt);
     cudaFree(g.ubar);
     if (!g.shared) {
@@ -205,6 +206,8 @@ RolloutArgs gpm::make_rollout_args(gpmppi_ctrl c, const float* state, const floa
     a.mt = c->mt;
     a.stages = c->stages;
     a.err = c->err;
+    a.wait_ns = c->wait_ns;
+    a.expire_first = c->expire_first;
     a.sf2 = g.sf2[0];
     for (int i = 0; i < 5; ++i) a.x0[i] = state[i];
     for (int d = 0; d < 4; ++d) a.zscale[d] = g.zscale[0][d];
@@ -402,7 +405,10 @@ int mppi_create(const gpmppi_params* p, const float* obstacles, int32_t O, const
         int nsm = 0, smem_optin = 0;
         GPM_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
         GPM_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-        const int stages = rollout_fp32_stages(gp->g.Np, smem_optin);
+        // the rollout layouts leave 64 bytes for the batched persistent kernel's
+        // own words past the largest layout
+        const int layout_limit = smem_optin - 64;
+        const int stages = rollout_fp32_stages(gp->g.Np, layout_limit);
         if (stages == 0) return fail(GPMPPI_ERR_UNSUPPORTED, "mppi_create: GP too large for shared memory");
 
         gpmppi_ctrl c = new (std::nothrow) gpmppi_ctrl_s;
@@ -506,6 +512,7 @@ int mppi_create(const gpmppi_params* p, const float* obstacles, int32_t O, const
             const GpDevice& g = gp->g;
             c->mm.Bhi = g.mma_hi[c->fmt];
             c->mm.Blo = g.mma_lo[c->fmt];
+            c->mm.xa = g.mma_xa;
             c->mm.nblocks = g.NpM / 128;
             c->mm.nchunks = g.NpM / 16;
             const double r = (double)g.sf2[0] / (g.mma_cB > 0.0f ? (double)g.mma_cB : 1.0);
@@ -518,10 +525,10 @@ int mppi_create(const gpmppi_params* p, const float* obstacles, int32_t O, const
             // the large accumulator), which keeps the variance error near
             // 1e-5 sf2 at N = 2048 at the cost of output passes half as wide.
             c->mm.lo_set = g.N > kLoSetMinN ? 1 : 0;
-            c->mm.stages = rollout_mma_stages(g.NpM, c->S, O, smem_optin, c->mm.lo_set);
+            c->mm.stages = rollout_mma_stages(g.NpM, c->S, O, layout_limit, c->mm.lo_set);
             if (c->mm.stages < 3) {
                 // keep the pipeline deep; read the scene from global memory instead
-                const int st_noscene = rollout_mma_stages(g.NpM, 0, 0, smem_optin, c->mm.lo_set);
+                const int st_noscene = rollout_mma_stages(g.NpM, 0, 0, layout_limit, c->mm.lo_set);
                 if (st_noscene > c->mm.stages) {
                     c->mm.stages = st_noscene;
                     c->mm.scene_smem = 0;
@@ -838,6 +845,13 @@ int mppi_nominal_sxy(gpmppi_ctrl c, float* sxy, void* stream) {
     if ((rc = check_dev_ptr(sxy, "mppi_nominal_sxy: sxy", false))) return rc;
     GPM_CUDA(cudaMemcpyAsync(sxy, c->nom_sxy, sizeof(float) * 3 * c->p.T, cudaMemcpyDeviceToDevice,
                              (cudaStream_t)stream));
+    return GPMPPI_OK;
+}
+
+int mppi_set_wait_limit(gpmppi_ctrl c, uint64_t ns, int32_t expire_first) {
+    if (!valid_ctrl(c)) return fail(GPMPPI_ERR_INVALID_ARG, "mppi_set_wait_limit: invalid handle");
+    c->wait_ns = ns;
+    c->expire_first = expire_first ? 1 : 0;
     return GPMPPI_OK;
 }
 

@@ -283,6 +283,7 @@ int mppi_batch_create(const gpmppi_ctrl* ctrls, int32_t B, gpmppi_batch* out) {
             its[i] = c->it;
             RolloutArgs a = make_rollout_args(c, zero_state, b->U_nom + b->uoff[i]);
             a.x0_dev = b->states + 5 * i;
+            a.expire_first = 0;                 // the failure-detection hook is not batched
             a.it_dev = b->iters + i;
             a.costs = c->costs;
             b->h_args[i] = a;

@@ -123,6 +123,9 @@ struct GpDevice {
     uint16_t* mma_lo[2] = {nullptr, nullptr};
     float mma_cB = 0.0f;
     int NpM = 0;
+    // the streaming rollout's training inputs and alpha in pair layout (NpM x 4
+    // floats, then NpM x 2; see k_pack_xa), copied into shared memory in bulk
+    float* mma_xa = nullptr;
     // resident tiles of the cluster rollout (N <= 512): per 16-bit format, rank
     // r's pieces at element offset cl_base[r], cl_bytes[r] bytes; NpC = 128,
     // 256 or 512 output columns.  A piece holds one 16-point chunk of the
@@ -165,6 +168,8 @@ struct RolloutArgs {
     int mt;                 // samples per CTA
     int stages;             // per-warp TMA pipeline depth for the L^-T tiles
     unsigned int* err;      // device status word (bit 0: a bounded wait gave up)
+    unsigned long long wait_ns;   // FP32 rollout: limit of each tile-copy wait (mppi_set_wait_limit)
+    int expire_first;             // FP32 rollout: first wait on a barrier nothing completes (test hook)
     float sf2;
     float x0[5];
     float zscale[4];
@@ -199,6 +204,7 @@ struct RolloutArgs {
 struct MmaArgs {
     const uint16_t* Bhi;
     const uint16_t* Blo;
+    const float* xa;        // training inputs and alpha in pair layout (GpDevice::mma_xa)
     int nblocks;            // NpM / 128
     int nchunks;            // NpM / 16
     float qscale;           // (sf2 / cB)^2: |L^-1 k*|^2 = qscale * |V'|^2

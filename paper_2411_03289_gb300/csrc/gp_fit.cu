@@ -447,6 +447,12 @@ int build_mma_tiles(GpDevice& g, int fmt) {
     k_pack_mma<<<(unsigned)((n + 255) / 256), 256>>>(g.Linv64[0], N, g.NpM, fmt, (double)g.mma_cB,
                                                       g.mma_hi[fmt], g.mma_lo[fmt]);
     GPM_CUDA(cudaGetLastError());
+    if (!g.mma_xa) {
+        // the streaming rollout's training inputs and alpha in pair layout
+        GPM_CUDA(cudaMalloc(&g.mma_xa, sizeof(float) * 6 * (size_t)g.NpM));
+        k_pack_xa<<<(g.NpM + 127) / 128, 128>>>(g.Xs[0], g.alpha, g.N, g.NpM, g.mma_xa);
+        GPM_CUDA(cudaGetLastError());
+    }
     GPM_CUDA(cudaDeviceSynchronize());
     return GPMPPI_OK;
 }

@@ -21,6 +21,8 @@ struct gpmppi_ctrl_s {
     int O = 0, P = 0, S = 0;
     int mt = 1, n_upd = 1;
     uint64_t it = 0;
+    uint64_t wait_ns = 2000000000ull;   // FP32 rollout: limit of each tile-copy wait
+    int expire_first = 0;               // FP32 rollout: failure-detection hook
     double sq_chi2 = 0.0, phi_inv = 0.0;
     float* obst = nullptr;
     float4* seg = nullptr;

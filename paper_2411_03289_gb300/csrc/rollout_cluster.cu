@@ -39,6 +39,13 @@
 namespace gpm {
 namespace {
 
+using tc::f2add;
+using tc::f2fma;
+using tc::f2mul;
+using tc::f2pack;
+using tc::f2sub;
+using tc::f2unpack;
+
 constexpr int MT = 128;               // samples per cluster (the MMA M)
 constexpr int NPROD = 256;            // producer threads: two per sample
 constexpr int NCOST = 64;             // scoring threads (two warps)
@@ -136,37 +143,6 @@ __device__ __forceinline__ void bulk_copy(void* dst, const void* src, uint32_t b
         : "memory");
 }
 
-// Packed FP32 pairs (f32x2: two lanes per 64-bit register, element 0 in the
-// low half).  The kernel rows are computed two training points at a time, so
-// one packed instruction does the work of two scalar ones.
-__device__ __forceinline__ uint64_t f2pack(float a, float b) {
-    uint64_t r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
-    return r;
-}
-__device__ __forceinline__ void f2unpack(uint64_t v, float& a, float& b) {
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
-}
-__device__ __forceinline__ uint64_t f2add(uint64_t a, uint64_t b) {
-    uint64_t r;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-__device__ __forceinline__ uint64_t f2sub(uint64_t a, uint64_t b) {
-    uint64_t r;
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-__device__ __forceinline__ uint64_t f2mul(uint64_t a, uint64_t b) {
-    uint64_t r;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-__device__ __forceinline__ uint64_t f2fma(uint64_t a, uint64_t b, uint64_t c) {
-    uint64_t r;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
-    return r;
-}
 // 2^x (the hardware approximation; results below the normal range flush to 0,
 // far below what a 16-bit split operand can carry)
 __device__ __forceinline__ float ex2_ftz(float x) {

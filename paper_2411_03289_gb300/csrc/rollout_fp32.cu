@@ -27,7 +27,9 @@ using namespace f32r;
 template <int MTP, bool TRACE>
 __global__ void __launch_bounds__(THREADS, 1)
     k_rollout_fp32(const RolloutArgs a, const __grid_constant__ CUtensorMap tmW) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    // no static shared memory in this kernel: the dynamic region starts at the
+    // base of the CTA's shared memory, aligned as the tensor copies need
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
     rollout_fp32_body<MTP, TRACE>(a, &tmW, blockIdx.x, smem_raw);
 }
 

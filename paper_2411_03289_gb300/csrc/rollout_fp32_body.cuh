@@ -52,10 +52,29 @@ __device__ __forceinline__ uint64_t global_ns() {
     return t;
 }
 
+// non-blocking probe of a phase
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
 // Wait for a phase with a time limit; on expiry record the error and report
-// failure (the caller then stops waiting for further copies).
+// failure (the caller then stops waiting for further copies).  A limit of 0
+// gives up at once unless the phase is already complete.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint64_t limit_ns,
                                                   unsigned int* err) {
+    if (mbar_test_wait(bar, parity)) return true;
+    if (limit_ns == 0) {
+        atomicOr(err, 1u);
+        return false;
+    }
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = global_ns();
     while (!mbar_try_wait(bar, parity)) {
@@ -84,7 +103,6 @@ __device__ __forceinline__ void fence_mbar_init() {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
-constexpr uint64_t kWaitLimitNs = 2000000000ull;   // 2 s per copy: only a broken copy waits this long
 
 // Geometry of the L^-T tiles: a warp owns 32 consecutive (sample-group, pair)
 // items, i.e. PPW = 32 / NMG pairs; its A tile covers columns [8 p0, 8 p0 + 8 PPW)
@@ -112,7 +130,9 @@ struct Smem {
     static __host__ __device__ int bars(int Np, int stages) {
         return tiles(Np) + WARPS * stages * 2 * Tile<MTP>::BYTES;
     }
-    static __host__ __device__ int total(int Np, int stages) { return bars(Np, stages) + WARPS * stages * 8; }
+    // one more mbarrier for the failure-detection hook (nothing arrives on it)
+    static __host__ __device__ int never(int Np, int stages) { return bars(Np, stages) + WARPS * stages * 8; }
+    static __host__ __device__ int total(int Np, int stages) { return never(Np, stages) + 8; }
 };
 
 // Named barrier over the 256 threads of the rollout (the whole CTA of the
@@ -175,6 +195,23 @@ __device__ __forceinline__ void rollout_fp32_body(const RolloutArgs& a, const CU
     uint32_t nrun = 0;          // tile stages consumed by this warp so far
     uint32_t nissued = 0;       // tile stages requested by this warp (lane 0)
     bool tma_ok = true;         // warp-uniform; false once a copy failed to arrive in time
+    // Failure-detection hook (a.expire_first): before any copy, warp 0 waits,
+    // bounded by a.wait_ns, on an mbarrier that nothing arrives on.  The wait
+    // runs out, records the timeout and turns the warp's copies off, exactly as
+    // a copy that never lands would; the rest of the rollout runs on (its
+    // results are then unspecified) and the kernel ends normally.
+    if (a.expire_first && warp == 0) {
+        // (in the dynamic layout: a static shared variable would move the
+        // dynamic region off the alignment the tensor copies need)
+        uint64_t* never_bar = reinterpret_cast<uint64_t*>(smem_raw + Smem<MTP>::never(Np, S));
+        int ok = 1;
+        if (lane == 0) {
+            mbar_init(never_bar, 1);
+            ok = mbar_wait_bounded(never_bar, 0u, a.wait_ns, a.err) ? 1 : 0;
+            asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(never_bar)) : "memory");
+        }
+        tma_ok = __shfl_sync(0xffffffffu, ok, 0) != 0;
+    }
 
     for (int k = 0; k < a.T; ++k) {
         // ---------------- P1: noise, clamp, query --------------------------
@@ -250,7 +287,7 @@ __device__ __forceinline__ void rollout_fp32_body(const RolloutArgs& a, const CU
                 const uint32_t n = nrun + (uint32_t)c;
                 const int st = (int)(n % (uint32_t)S);
                 bool ok = tma_ok;
-                if (ok) ok = mbar_wait_bounded(wbar + st, (n / (uint32_t)S) & 1u, kWaitLimitNs, a.err);
+                if (ok) ok = mbar_wait_bounded(wbar + st, (n / (uint32_t)S) & 1u, a.wait_ns, a.err);
                 tma_ok = __all_sync(0xffffffffu, ok);
                 const float* tA = reinterpret_cast<const float*>(wtile + (size_t)st * 2 * TL::BYTES);
                 const float* tB = tA + TL::TW * TL::R;

@@ -67,8 +67,8 @@ __host__ __device__ inline MLayout mma_layout(int nstage, int NpM, int S, int O,
     L.mh = L.qh + 2 * MT * 4;                    // 2 x 128 float2
     L.ep = L.mh + 2 * MT * 8;                    // 2 x 128 floats
     L.om = L.ep + 2 * MT * 4;                    // 2 x 128 floats
-    L.xs = ((L.om + 2 * MT * 4 + 127) / 128) * 128;   // NpM float4: scaled training inputs
-    L.al = L.xs + NpM * 16;                      // NpM float2: alpha
+    L.xs = ((L.om + 2 * MT * 4 + 127) / 128) * 128;   // NpM x 4 floats: scaled inputs, pair layout
+    L.al = L.xs + NpM * 16;                      // NpM x 2 floats: alpha, pair layout
     L.seg = L.al + NpM * 8;                      // S float4: lane segments
     L.il2 = L.seg + S * 16;                      // S floats
     L.obs = L.il2 + ((S + 3) / 4) * 16;          // O x 3 floats: obstacles
@@ -190,20 +190,16 @@ __device__ __forceinline__ void rollout_mma_body(const RolloutArgs& a, const Mma
         tc::mbar_init(x_res, 1);
         *abort_flag = 0;
         tc::fence_mbar_init();
-        // scaled training inputs and alpha (whole 16-byte lines of it) by bulk
-        // copies (TMA engine); the threads fill the rest below
-        const uint32_t xb = (uint32_t)a.N * 16u, ab = ((uint32_t)a.N * 8u) & ~15u;
+        // scaled training inputs and alpha in pair layout (two points per
+        // 16-byte line; rows past N hold a far point and alpha 0) by two bulk
+        // copies (TMA engine)
+        const uint32_t xb = (uint32_t)(NB * BLK) * 16u, ab = (uint32_t)(NB * BLK) * 8u;
         tc::mbar_expect_tx(x_res, xb + ab);
-        if (xb) bulk_copy(xs_s, a.Xs, xb, x_res);
-        if (ab) bulk_copy(al_s, a.alpha, ab, x_res);
+        if (xb) {
+            bulk_copy(xs_s, mm.xa, xb, x_res);
+            bulk_copy(al_s, mm.xa + 4 * NB * BLK, ab, x_res);
+        }
     }
-    // rows j >= N get a far point (exp2 underflows to exactly 0) and alpha 0;
-    // an odd N leaves the last alpha to a thread
-    for (int j = a.N + tid; j < NB * BLK; j += THREADS) {
-        xs_s[j] = make_float4(1.0e4f, 1.0e4f, 1.0e4f, 1.0e4f);
-        al_s[j] = make_float2(0.0f, 0.0f);
-    }
-    if ((a.N & 1) && tid == 0) al_s[a.N - 1] = __ldg(reinterpret_cast<const float2*>(a.alpha) + a.N - 1);
     // lane segments and obstacles too: the cost phase reads them every step
     for (int i = tid; i < Ssm; i += THREADS) {
         seg_s[i] = __ldg(a.seg + i);
@@ -306,6 +302,8 @@ __device__ __forceinline__ void rollout_mma_body(const RolloutArgs& a, const Mma
     const int mvalid = min(MTC, a.K - s0);
     const bool active = m < mvalid;
     const int s_me = s0 + (active ? m : 0);
+    const ulonglong2* xs2 = reinterpret_cast<const ulonglong2*>(xs_s);   // pair layout
+    const ulonglong2* al2 = reinterpret_cast<const ulonglong2*>(al_s);
     float* qh = reinterpret_cast<float*>(sm + L.qh);
     float2* mh = reinterpret_cast<float2*>(sm + L.mh);
     float* ep = reinterpret_cast<float*>(sm + L.ep);
@@ -336,6 +334,8 @@ __device__ __forceinline__ void rollout_mma_body(const RolloutArgs& a, const Mma
         if (u == 0 && active) a.u_tilde[(size_t)k * a.K + s_me] = ut;
         const float z0 = mu3 * a.zscale[0], z1 = mu4 * a.zscale[1];
         const float z2 = ut.x * a.zscale[2], z3 = ut.y * a.zscale[3];
+        const uint64_t zz0 = tc::f2pack(z0, z0), zz1 = tc::f2pack(z1, z1);
+        const uint64_t zz2 = tc::f2pack(z2, z2), zz3 = tc::f2pack(z3, z3);
 
         // ---------------- P2/P3: kernel-row tiles for the tensor cores ------
         float qpart = 0.0f, mv = 0.0f, mw = 0.0f, cv = 0.0f, cw = 0.0f;
@@ -348,22 +348,40 @@ __device__ __forceinline__ void rollout_mma_body(const RolloutArgs& a, const Mma
                 const int st = (int)(n % (uint32_t)nstage);
                 const uint32_t use = n / (uint32_t)nstage;
                 unsigned char* stage = sm + st * STAGE;
-                // this thread's KPT training points of the chunk
-                const int jb = c * KC + u * KPT;
+                // this thread's KPT training points of the chunk, two at a time
+                // (packed f32x2 arithmetic on the pair layout)
+                const int pb = (c * KC + u * KPT) / 2;
                 float av[KPT];
 #pragma unroll
-                for (int e = 0; e < KPT; ++e) {
-                    const float4 x = xs_s[jb + e];
-                    const float d0 = z0 - x.x, d1 = z1 - x.y, d2 = z2 - x.z, d3 = z3 - x.w;
-                    av[e] = ex2_ftz(-(d0 * d0 + d1 * d1 + d2 * d2 + d3 * d3));
+                for (int q = 0; q < KPT / 2; ++q) {
+                    const ulonglong2 xa = xs2[2 * (pb + q)], xb = xs2[2 * (pb + q) + 1];
+                    const uint64_t d0 = tc::f2sub(zz0, xa.x), d1 = tc::f2sub(zz1, xa.y);
+                    const uint64_t d2 = tc::f2sub(zz2, xb.x), d3 = tc::f2sub(zz3, xb.y);
+                    uint64_t t = tc::f2mul(d0, d0);
+                    t = tc::f2fma(d1, d1, t);
+                    t = tc::f2fma(d2, d2, t);
+                    t = tc::f2fma(d3, d3, t);
+                    float t0, t1;
+                    tc::f2unpack(t, t0, t1);
+                    av[2 * q] = ex2_ftz(-t0);
+                    av[2 * q + 1] = ex2_ftz(-t1);
                 }
                 if (last_pass) {
+                    // the chunk's mean terms as packed partial sums, then one
+                    // compensated addition per output
+                    uint64_t pv = 0ull, pw = 0ull;
 #pragma unroll
-                    for (int e = 0; e < KPT; ++e) {
-                        const float2 al = al_s[jb + e];
-                        kahan_add(mv, cv, av[e] * al.x);
-                        kahan_add(mw, cw, av[e] * al.y);
+                    for (int q = 0; q < KPT / 2; ++q) {
+                        const ulonglong2 al = al2[pb + q];
+                        const uint64_t k2 = tc::f2pack(av[2 * q], av[2 * q + 1]);
+                        pv = tc::f2fma(k2, al.x, pv);
+                        pw = tc::f2fma(k2, al.y, pw);
                     }
+                    float pv0, pv1, pw0, pw1;
+                    tc::f2unpack(pv, pv0, pv1);
+                    tc::f2unpack(pw, pw0, pw1);
+                    kahan_add(mv, cv, pv0 + pv1);
+                    kahan_add(mw, cw, pw0 + pw1);
                 }
                 uint32_t hw[KPT / 2], lw[KPT / 2];
 #pragma unroll
@@ -614,13 +632,31 @@ __device__ void inval_item_barriers(const RolloutArgs& a, const MmaArgs& mm, int
     for (int i = 0; i < 3; ++i) mbar_inval(a_full + 3 * NSTAGE + i);
 }
 
+// The item bodies as separate (not inlined) functions: the persistent kernel's
+// register budget (168 per thread at 320 threads: ten warps on four schedulers)
+// is then met by each body on its own instead of by their union.
+template <int FMT, int R>
+__device__ __noinline__ void persistent_mma_item(const RolloutArgs& a, const MmaArgs& mm, int tile,
+                                                 unsigned char* sm, uint32_t taddr) {
+    rollout_mma_body<FMT, R, false>(a, mm, tile, sm, taddr);
+}
+template <int MTP>
+__device__ __noinline__ void persistent_fp32_item(const RolloutArgs& a, const CUtensorMap* tm, int tile,
+                                                  unsigned char* sm) {
+    f32r::rollout_fp32_body<MTP, false>(a, tm, tile, sm);
+}
+
 __global__ void __launch_bounds__(THREADS, 1)
     k_rollout_persistent(const RolloutArgs* __restrict__ args, const MmaArgs* __restrict__ mms,
                          const CUtensorMap* __restrict__ tmaps, const int4* __restrict__ items, int nitems,
-                         unsigned int* __restrict__ head) {
+                         unsigned int* __restrict__ head, int ctl_off) {
+    // no static shared memory (it would move the dynamic region off the
+    // alignment the bulk and tensor copies need): the CTA's own words (TMEM
+    // base, current and previous item) sit past the largest item layout
     extern __shared__ __align__(1024) unsigned char sm[];
-    __shared__ uint32_t tbase;
-    __shared__ int cur, prev;
+    uint32_t& tbase = *reinterpret_cast<uint32_t*>(sm + ctl_off);
+    int& cur = *reinterpret_cast<int*>(sm + ctl_off + 4);
+    int& prev = *reinterpret_cast<int*>(sm + ctl_off + 8);
     const int tid = threadIdx.x, warp = tid >> 5;
     if (warp == 0) {
         // held for the whole launch (one CTA per SM), so the permit is not relinquished
@@ -649,20 +685,20 @@ __global__ void __launch_bounds__(THREADS, 1)
         if (it.z == 0) {
             if (warp < f32r::WARPS) {
                 const int mtp = fp32_mtp(a.Np);
-                if (mtp == 32) f32r::rollout_fp32_body<32, false>(a, tmaps + it.x, it.y, sm);
-                else if (mtp == 16) f32r::rollout_fp32_body<16, false>(a, tmaps + it.x, it.y, sm);
-                else f32r::rollout_fp32_body<8, false>(a, tmaps + it.x, it.y, sm);
+                if (mtp == 32) persistent_fp32_item<32>(a, tmaps + it.x, it.y, sm);
+                else if (mtp == 16) persistent_fp32_item<16>(a, tmaps + it.x, it.y, sm);
+                else persistent_fp32_item<8>(a, tmaps + it.x, it.y, sm);
             }
         } else {
             const MmaArgs& mm = mms[it.x];
             if (it.z == 1) {
-                if (it.w == 2) rollout_mma_body<0, 2, false>(a, mm, it.y, sm, taddr);
-                else if (it.w == 4) rollout_mma_body<0, 4, false>(a, mm, it.y, sm, taddr);
-                else rollout_mma_body<0, 8, false>(a, mm, it.y, sm, taddr);
+                if (it.w == 2) persistent_mma_item<0, 2>(a, mm, it.y, sm, taddr);
+                else if (it.w == 4) persistent_mma_item<0, 4>(a, mm, it.y, sm, taddr);
+                else persistent_mma_item<0, 8>(a, mm, it.y, sm, taddr);
             } else {
-                if (it.w == 2) rollout_mma_body<1, 2, false>(a, mm, it.y, sm, taddr);
-                else if (it.w == 4) rollout_mma_body<1, 4, false>(a, mm, it.y, sm, taddr);
-                else rollout_mma_body<1, 8, false>(a, mm, it.y, sm, taddr);
+                if (it.w == 2) persistent_mma_item<1, 2>(a, mm, it.y, sm, taddr);
+                else if (it.w == 4) persistent_mma_item<1, 4>(a, mm, it.y, sm, taddr);
+                else persistent_mma_item<1, 8>(a, mm, it.y, sm, taddr);
             }
         }
         // every role of this CTA is done with the item (TMEM reads included)
@@ -681,8 +717,10 @@ int launch_rollout_persistent(const RolloutArgs* args, const MmaArgs* mms, const
                               const int4* items, int nitems, unsigned int* head, int grid, int smem,
                               cudaStream_t st) {
     if (nitems == 0) return GPMPPI_OK;
-    GPM_CUDA(cudaFuncSetAttribute(k_rollout_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    k_rollout_persistent<<<grid, THREADS, smem, st>>>(args, mms, tmaps, items, nitems, head);
+    const int ctl_off = ((smem + 15) / 16) * 16;
+    const int total = ctl_off + 16;
+    GPM_CUDA(cudaFuncSetAttribute(k_rollout_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, total));
+    k_rollout_persistent<<<grid, THREADS, total, st>>>(args, mms, tmaps, items, nitems, head, ctl_off);
     GPM_CUDA(cudaGetLastError());
     return GPMPPI_OK;
 }

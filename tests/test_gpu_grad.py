@@ -13,14 +13,17 @@ from parity import make_ctrl, to_np
 pytestmark = pytest.mark.gpu
 
 SLOPE = 20.0
-TOL_GRAD = 1e-3        # relative, per component, floored at 5% of the largest component
+TOL_GRAD = 1e-3        # relative, per component, floored at 0.1% of the largest component
 TOL_J = 1e-4
 
 
 def grad_err(g, ref):
-    """Largest |g - ref| / max(|ref|, 0.05 max |ref|)."""
+    """Largest |g - ref| / max(|ref|, 1e-3 max |ref|): every component of at
+    least 0.1% of the largest is held to the relative tolerance; smaller ones
+    to an absolute error of TOL_GRAD * 1e-3 * max |ref| (their FP32 sums are
+    rounded at the scale of the largest terms)."""
     g, ref = np.asarray(g, dtype=np.float64).ravel(), np.asarray(ref, dtype=np.float64).ravel()
-    floor = 0.05 * np.max(np.abs(ref))
+    floor = 1e-3 * np.max(np.abs(ref))
     return float(np.max(np.abs(g - ref) / np.maximum(np.abs(ref), floor)))
 
 
@@ -127,8 +130,8 @@ def test_grad_cfg4_sampled(lib):
             jm, _ = O.objective(sc, sc.hyper, x0, Um, 0, sub, SLOPE, fits)
             ref[h].append((jp - jm) / (2 * h))
     gpu_u = dU.reshape(-1)[comps]
-    # floor for the sampled components: 5% of the largest |dJ/dU| on the GPU
-    floor = 0.05 * np.max(np.abs(dU))
+    # floor for the sampled components: 0.1% of the largest |dJ/dU| on the GPU
+    floor = 1e-3 * np.max(np.abs(dU))
     for h, vals in ref.items():
         vals = np.array(vals)
         err = np.max(np.abs(gpu_u - vals) / np.maximum(np.abs(vals), floor))

@@ -176,3 +176,30 @@ def test_closed_loop_teacher_forced(lib):
         x = O.mppi.plant_step(sc, x, U_ref[0], S.true_residual)
         U = O.mppi.shift_controls(U_ref)
     assert n_alt <= 5
+
+
+def test_wait_expiry_reports_timeout_and_context_survives(lib):
+    """Failure detection without a GPU fault: one warp of every CTA of the
+    FP32 rollout waits, with a 1 ms limit, on an mbarrier that nothing arrives
+    on; the wait runs out, the kernel records the timeout, that warp issues no
+    copies and the kernel finishes.  The host reads GPMPPI_ERR_TIMEOUT from
+    mppi_device_status (which clears it), and with the hook off and the default
+    limit back the same controller steps normally, with parity against the
+    oracle."""
+    import torch
+    sc = S.scenario("small", precision=0, K=64, N=100, T=3)
+    g, ctrl = make_ctrl(lib, sc)
+    assert lib.mppi_rollout_kind(ctrl) == lib.GPMPPI_KERNEL_FP32
+    dev = torch.device("cuda")
+    U = torch.tensor(sc.U0, dtype=torch.float32, device=dev)
+    U_new = torch.empty_like(U)
+    lib.mppi_set_wait_limit(ctrl, 1_000_000, expire_first=True)
+    lib.mppi_set_iteration(ctrl, 0)
+    lib.mppi_step(ctrl, sc.x0, U, U_new)
+    with pytest.raises(lib.GpmppiError) as ei:
+        lib.mppi_device_status(ctrl)
+    assert ei.value.code == lib.GPMPPI_ERR_TIMEOUT
+    lib.mppi_device_status(ctrl)                 # the status word was cleared
+    lib.mppi_set_wait_limit(ctrl, 2_000_000_000, expire_first=False)
+    U2, w2, c2 = gpu_step(lib, ctrl, sc, sc.x0, sc.U0, it=0)
+    check_step(sc, _oracle(sc), sc.U0, U2, w2, c2)

@@ -67,7 +67,7 @@ def _table(s_gpu, s_ref, sf2):
     return row
 
 
-@pytest.mark.parametrize("N", [500, 2048])
+@pytest.mark.parametrize("N", [500, 1024, 2048])
 def test_variance_error_per_element(lib, N):
     rows = {}
     for precision in (0, 2, 1):
