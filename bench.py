@@ -260,18 +260,25 @@ class ClockSampler:
 
 def committed_traffic(kernel="rollout_fp32", workload=WORKLOAD):
     """DRAM bytes per launch from the committed ncu summary of this kernel and
-    workload, if it was taken on the current kernel source (the summary
-    records the source's sha256); else None."""
+    workload, if it was taken on the current sources: the summary records the
+    sha256 of the kernel's .cu file and of every other source it names, and
+    each must match the file as it is now; else None."""
     try:
         txt = open(os.path.join(PROFILES, f"{kernel}_{workload}_ncu.md")).read()
-        sha = hashlib.sha256(open(os.path.join(CSRC, f"{kernel}.cu"), "rb").read()).hexdigest()
     except OSError:
         return None
-    m_sha = re.search(rf"{kernel}\.cu sha256:\s*([0-9a-f]{{64}})", txt)
-    m_tr = re.search(r"dram bytes per launch \(full workload\):\s*([0-9.eE+]+)", txt)
-    if not m_sha or not m_tr or m_sha.group(1) != sha:
+    shas = dict(re.findall(r"^([A-Za-z0-9_.]+\.(?:cu|cuh)) sha256:\s*([0-9a-f]{64})", txt, re.M))
+    if f"{kernel}.cu" not in shas:
         return None
-    return float(m_tr.group(1))
+    for name, want in shas.items():
+        try:
+            have = hashlib.sha256(open(os.path.join(CSRC, name), "rb").read()).hexdigest()
+        except OSError:
+            return None
+        if have != want:
+            return None
+    m_tr = re.search(r"dram bytes per launch \(full workload\):\s*([0-9.eE+]+)", txt)
+    return float(m_tr.group(1)) if m_tr else None
 
 
 # ---------------------------------------------------------------------------

@@ -222,19 +222,28 @@ __global__ void __launch_bounds__(GTHREADS, 1) k_gram_tc(const GramArgs g) {
             const uint32_t use = (uint32_t)(c / GSTAGES);
             const int q0 = q_begin + c * GQ + 8 * h;
             float av[8], aw[8], b0[8], b1[8];
+            // the adjoints and the rows of b are loaded independently (all 32
+            // loads in flight at once); a query whose adjoints are both zero
+            // (padding samples, whose b may be anything) is then selected away
+            float4 qb[8];
+            float bi[8];
 #pragma unroll
             for (int e = 0; e < 8; ++e) {
                 const int q = q0 + e;
-                float4 qb = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (q < q_end) qb = __ldg(g.qbar + q);
-                // a query whose adjoints are both zero (padding samples) adds nothing
-                const bool live = (qb.z != 0.0f) || (qb.w != 0.0f);
-                const float* row = g.Bq + (size_t)(live ? q : 0) * g.Np;
-                const float bi = (live && in_i) ? __ldg(row + I0 + r) : 0.0f;
-                av[e] = bi * qb.z;
-                aw[e] = bi * qb.w;
-                b0[e] = (live && in_j0) ? __ldg(row + J0 + r) : 0.0f;
-                b1[e] = (live && in_j1) ? __ldg(row + J1 + r) : 0.0f;
+                const bool in = q < q_end;
+                const float* row = g.Bq + (size_t)(in ? q : q_begin) * g.Np;
+                qb[e] = in ? __ldg(g.qbar + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+                bi[e] = (in && in_i) ? __ldg(row + I0 + r) : 0.0f;
+                b0[e] = (in && in_j0) ? __ldg(row + J0 + r) : 0.0f;
+                b1[e] = (in && in_j1) ? __ldg(row + J1 + r) : 0.0f;
+            }
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const bool live = (qb[e].z != 0.0f) || (qb[e].w != 0.0f);
+                av[e] = live ? bi[e] * qb[e].z : 0.0f;
+                aw[e] = live ? bi[e] * qb[e].w : 0.0f;
+                b0[e] = live ? b0[e] : 0.0f;
+                b1[e] = live ? b1[e] : 0.0f;
             }
             uint32_t vh[4], vl[4], wh[4], wl[4], h0[4], l0[4], h1[4], l1[4];
 #pragma unroll
