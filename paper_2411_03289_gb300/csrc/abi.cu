@@ -514,7 +514,6 @@ int mppi_create(const gpmppi_params* p, const float* obstacles, int32_t O, const
             c->mm.Blo = g.mma_lo[c->fmt];
             c->mm.xa = g.mma_xa;
             c->mm.nblocks = g.NpM / 128;
-            c->mm.nchunks = g.NpM / 16;
             const double r = (double)g.sf2[0] / (g.mma_cB > 0.0f ? (double)g.mma_cB : 1.0);
             c->mm.qscale = (float)(r * r);
             c->mm.scene_smem = 1;

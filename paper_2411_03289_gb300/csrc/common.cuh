@@ -206,7 +206,6 @@ struct MmaArgs {
     const uint16_t* Blo;
     const float* xa;        // training inputs and alpha in pair layout (GpDevice::mma_xa)
     int nblocks;            // NpM / 128
-    int nchunks;            // NpM / 16
     float qscale;           // (sf2 / cB)^2: |L^-1 k*|^2 = qscale * |V'|^2
     int stages;             // shared-memory pipeline depth (2..6)
     int rps;                // producer threads per sample (2, 4, 8): 128, 64, 32 samples per CTA

@@ -277,21 +277,25 @@ __global__ void k_absmax(const double* __restrict__ Xm, size_t n, unsigned long 
     atomicMax(out, (unsigned long long)__double_as_longlong(m));
 }
 
-// Tensor-core tiles: element (i = 128 b + r, j = 16 c + 8 sl + e) of cB L^-1 goes
-// to piece (c, b) at ((c * NB + b) * 2 + sl) * 1024 + r * 8 + e, so one 16-point
-// chunk holds the 4 KiB pieces of all blocks contiguously; hi = round(v),
-// lo = round(v - hi).
+// Tensor-core tiles of the streaming rollout.  The factor's rows (output
+// columns of V) are grouped in pairs of 128-row blocks (NP = ceil(NB / 2)
+// pairs of 256 rows; the rows past NpM of an odd NB's last pair are zero) and
+// its columns (training points) in stages of 32.  Piece (c, p) holds element
+// (i = 256 p + r, j = 32 c + 8 sl + e) of cB L^-1 at
+// ((c * NP + p) * 4 + sl) * 2048 + r * 8 + e, so one stage holds the 16 KiB
+// pieces of all pairs contiguously, each as four 8-point slabs of 256 rows;
+// hi = round(v), lo = round(v - hi).
 __global__ void k_pack_mma(const double* __restrict__ Xm, int N, int NpM, int fmt, double cB,
                            uint16_t* __restrict__ hi, uint16_t* __restrict__ lo) {
     const size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-    const size_t total = (size_t)NpM * NpM;
+    const int NP = (NpM / 128 + 1) / 2;
+    const size_t total = (size_t)(NpM / 32) * NP * 8192;
     if (idx >= total) return;
-    const int NB = NpM / 128;
-    const size_t piece = idx / 2048;
-    const int w = (int)(idx % 2048);
-    const int c = (int)(piece / NB), b = (int)(piece % NB);
-    const int sl = w / 1024, r = (w / 8) % 128, e = w % 8;
-    const int i = 128 * b + r, j = 16 * c + 8 * sl + e;
+    const size_t piece = idx / 8192;
+    const int w = (int)(idx % 8192);
+    const int c = (int)(piece / NP), p = (int)(piece % NP);
+    const int sl = w / 2048, r = (w / 8) % 256, e = w % 8;
+    const int i = 256 * p + r, j = 32 * c + 8 * sl + e;
     double v = 0.0;
     if (i < N && j < N && j <= i) v = cB * Xm[(size_t)i * N + j];
     if (fmt == 0) {
@@ -441,7 +445,8 @@ int build_mma_tiles(GpDevice& g, int fmt) {
         // largest power of two with cB * max|L^-1| <= 2^14 (16-bit range, room for the sums)
         g.mma_cB = (float)std::ldexp(1.0, (int)std::floor(std::log2(16384.0 / (mx > 0 ? mx : 1.0))));
     }
-    const size_t n = (size_t)g.NpM * g.NpM;
+    // 32-point stages x pairs of 128-row blocks x 256 rows x 32 points
+    const size_t n = (size_t)(g.NpM / 32) * (size_t)((g.NpM / 128 + 1) / 2) * 8192;
     GPM_CUDA(cudaMalloc(&g.mma_hi[fmt], n * sizeof(uint16_t)));
     GPM_CUDA(cudaMalloc(&g.mma_lo[fmt], n * sizeof(uint16_t)));
     k_pack_mma<<<(unsigned)((n + 255) / 256), 256>>>(g.Linv64[0], N, g.NpM, fmt, (double)g.mma_cB,

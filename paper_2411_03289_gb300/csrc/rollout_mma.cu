@@ -16,15 +16,20 @@
 // chunk instead of three, which keeps the variance near FP32 accuracy at
 // N = 2048, at the price of output passes half as wide.
 //
-// CTA = 128 samples (the MMA M), 256 threads: thread t serves sample t % 128
-// and half h = t / 128 of every shared loop.  The output columns of V are
-// processed in passes of up to 512 columns (one TMEM allocation), or of 256
-// with the low column set in the other half, 128 columns per MMA block; the
-// reduction dimension in chunks of 16 training points through a ring of
-// shared-memory stages.  Per chunk the threads compute the kernel-row tile
-// (exp2 on the SFU), one thread fetches the pre-arranged L^-T tiles with bulk
-// copies and issues 3 MMAs per active block (blocks entirely above the
-// triangle are skipped) and commits them to the stage's mbarrier.  At the end
+// CTA = 128 samples (the MMA M), 256 producer threads: thread t serves
+// sample t % 128 and half h = t / 128 of every shared loop.  The output
+// columns of V are processed in passes of up to 512 columns (one TMEM
+// allocation), or of 256 with the low column set in the other half.  The
+// factor's 128-column blocks go to the tensor cores in pairs (MMA N = 256;
+// a pair whose lower block has passed its last stage, the diagonal of the
+// triangle, runs its upper block alone, N = 128).  The reduction dimension streams in stages of 32
+// training points (two MMA K-steps) through a ring of shared-memory stages:
+// per stage the producers compute the kernel-row tile (exp2 on the SFU), one
+// thread fetches the pre-arranged L^-T pieces of the active pairs with one
+// bulk copy per part, and one warp issues 3 MMAs per pair and K-step and
+// commits them to the stage's mbarrier.  Stages of 32 points halve the
+// handshakes per MMA against 16-point ones: the issuing warp's per-stage
+// bookkeeping, not the tensor pipe, bounded the 16-point design.  At the end
 // of a pass each thread reads its sample's TMEM row (both column sets, added,
 // with mm.lo_set) and sums the squares.
 #include <cuda_bf16.h>
@@ -42,15 +47,18 @@ namespace {
 constexpr int MT = 128;               // samples per CTA (the MMA M)
 constexpr int NPROD = 256;            // producer threads (warps 0-7): two per sample
 constexpr int THREADS = NPROD + 64;   // + warp 8 (MMA issuer) + warp 9 (tile loader)
-constexpr int KC = 16;                // training points per chunk (one MMA K-step)
-constexpr int BLK = 128;              // output columns per MMA block (MMA N)
-constexpr int BLOCKS_PER_PASS = 4;    // 512 TMEM columns (2 blocks per column set with mm.lo_set)
+constexpr int KCS = 32;               // training points per stage (two MMA K-steps of 16)
+constexpr int BLK = 128;              // output columns per block of L^-T
+constexpr int PAIR = 2 * BLK;         // output columns per MMA (a pair of blocks, MMA N = 256)
 constexpr int LO_COL = 256;           // first TMEM column of the low set
 constexpr int NSTAGE = 6;             // maximum pipeline depth (fewer when the training set is large)
-constexpr int A_PART = MT * KC * 2;                         // 4 KiB
-constexpr int B_PART = BLK * KC * 2;                        // 4 KiB
-// a stage: the A tile (hi, lo), then up to bpp B pieces hi, then bpp lo
-__host__ __device__ constexpr int stage_bytes(int bpp) { return 2 * A_PART + bpp * 2 * B_PART; }
+constexpr int A_PART = MT * KCS * 2;                        // 8 KiB: kernel-row tile, one part
+constexpr int P_PART = PAIR * KCS * 2;                      // 16 KiB: factor pair piece, one part
+// a stage: the A tile (hi, lo), then up to ppp pair pieces hi, then ppp lo
+// (ppp = pairs per pass: a pass fills the 512 TMEM columns, two pairs, or
+// one pair per column set with mm.lo_set)
+__host__ __device__ constexpr int stage_bytes(int ppp) { return 2 * A_PART + ppp * 2 * P_PART; }
+__host__ __device__ constexpr int pairs_per_pass(int lo_set) { return lo_set ? 1 : 2; }
 constexpr uint64_t kWaitNs = 2000000000ull;
 
 // Shared-memory layout for a given pipeline depth and padded training-set size.
@@ -58,9 +66,9 @@ struct MLayout {
     int bars, tslot, abort_flag, qh, mh, ep, om, xs, al, seg, il2, obs, total;
 };
 
-__host__ __device__ inline MLayout mma_layout(int nstage, int NpM, int S, int O, int bpp) {
+__host__ __device__ inline MLayout mma_layout(int nstage, int NpM, int S, int O, int ppp) {
     MLayout L;
-    L.bars = nstage * stage_bytes(bpp);                     // a_full, b_full, empty [NSTAGE] + pass_done, tmem_free, x_res
+    L.bars = nstage * stage_bytes(ppp);                     // a_full, b_full, empty [NSTAGE] + pass_done, tmem_free, x_res
     L.tslot = L.bars + 8 * (3 * NSTAGE + 3);
     L.abort_flag = L.tslot + 4;
     L.qh = ((L.abort_flag + 4 + 15) / 16) * 16;  // 2 x 128 floats
@@ -77,9 +85,9 @@ __host__ __device__ inline MLayout mma_layout(int nstage, int NpM, int S, int O,
 }
 
 // deepest pipeline that fits (0 if none)
-inline int mma_stages(int NpM, int S, int O, int optin, int bpp) {
+inline int mma_stages(int NpM, int S, int O, int optin, int ppp) {
     for (int s = NSTAGE; s >= 2; --s)
-        if (mma_layout(s, NpM, S, O, bpp).total <= optin) return s;
+        if (mma_layout(s, NpM, S, O, ppp).total <= optin) return s;
     return 0;
 }
 
@@ -110,11 +118,13 @@ __device__ __forceinline__ void split2(float a, float b, uint32_t* hi, uint32_t*
     }
 }
 
-// Bounded wait that also gives up at once when another role has aborted.
+// Bounded wait that gives up at once when another role has aborted.  The
+// flag is read only once the phase is found incomplete: a phase that did
+// complete is safe to use, and the fast path stays one instruction.
 __device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
                                               unsigned int* err) {
-    if (*abort_flag) return false;
     if (tc::mbar_try_wait(bar, parity)) return true;
+    if (*abort_flag) return false;
     const uint64_t t0 = tc::global_ns();
     while (!tc::mbar_try_wait(bar, parity)) {
         if (*abort_flag) return false;
@@ -155,12 +165,13 @@ template <int FMT, int R, bool TRACE>
 __device__ __forceinline__ void rollout_mma_body(const RolloutArgs& a, const MmaArgs& mm, int tile,
                                                  unsigned char* sm, uint32_t tmem_given) {
     constexpr int MTC = NPROD / R;
-    constexpr int KPT = KC / R;
+    constexpr int KPT = KCS / R;
     const int nstage = mm.stages;
     const int Ssm = mm.scene_smem ? a.S : 0, Osm = mm.scene_smem ? a.O : 0;
-    const int bpp = mm.lo_set ? BLOCKS_PER_PASS / 2 : BLOCKS_PER_PASS;   // output blocks per pass
-    const int STAGE = stage_bytes(bpp);
-    const MLayout L = mma_layout(nstage, mm.nblocks * BLK, Ssm, Osm, bpp);
+    const int ppp = pairs_per_pass(mm.lo_set);  // block pairs per pass
+    const int bpp = 2 * ppp;                    // output blocks per pass
+    const int STAGE = stage_bytes(ppp);
+    const MLayout L = mma_layout(nstage, mm.nblocks * BLK, Ssm, Osm, ppp);
     uint64_t* a_full = reinterpret_cast<uint64_t*>(sm + L.bars);
     uint64_t* b_full = a_full + NSTAGE;
     uint64_t* empty = b_full + NSTAGE;
@@ -176,7 +187,8 @@ __device__ __forceinline__ void rollout_mma_body(const RolloutArgs& a, const Mma
     float* obs_s = reinterpret_cast<float*>(sm + L.obs);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int NB = mm.nblocks;                 // 64-column blocks of L^-T
+    const int NB = mm.nblocks;                 // 128-column blocks of L^-T
+    const int NP = (NB + 1) / 2;               // block pairs (the last one half empty for odd NB)
     const int npass = (NB + bpp - 1) / bpp;
 
     if (tid == 0) {
@@ -227,65 +239,86 @@ __device__ __forceinline__ void rollout_mma_body(const RolloutArgs& a, const Mma
         // one loader thread; the issuer is a converged warp whose elected lane
         // issues the MMAs (its operand arithmetic stays warp-uniform)
         if (!issuer && lane != 0) return;
-        const uint32_t idesc = tc::idesc_f16(FMT, MT, BLK);
-        // base descriptors of stage 0's A tile (128 rows) and B pieces (128 rows);
-        // stage and block offsets are multiples of 16 bytes inside shared memory
+        const uint32_t idesc2 = tc::idesc_f16(FMT, MT, PAIR);   // a block pair
+        const uint32_t idesc1 = tc::idesc_f16(FMT, MT, BLK);    // one block of a pair
+        // base descriptors of stage 0's A tile (128 rows, slabs MT * 16 bytes
+        // apart) and pair pieces (256 rows, slabs PAIR * 16 bytes apart); stage,
+        // K-step and pair offsets are multiples of 16 bytes inside shared memory
         const uint64_t dA0 = tc::smem_desc(tc::smem_addr(sm), MT * 16, 128);
-        const uint64_t dB0 = tc::smem_desc(tc::smem_addr(sm), BLK * 16, 128);
-        uint32_t n = 0, pc = 0;
+        const uint64_t dB0 = tc::smem_desc(tc::smem_addr(sm), PAIR * 16, 128);
+        int st = 0;                  // ring position: stage and the parity of its current use
+        uint32_t ph = 0;
+        bool wrapped = false;
+        uint32_t pc = 0;
         for (int k = 0; k < a.T; ++k) {
             for (int g = 0; g < npass; ++g, ++pc) {
                 const int b0 = g * bpp;
                 const int b1 = min(NB, b0 + bpp);
-                const int nchunk = 8 * b1;               // block b needs chunks 0 .. 8b+7
+                const int p0 = b0 >> 1, p1 = (b1 + 1) >> 1;
+                const int nchunk = 4 * b1;               // block b needs stages 0 .. 4b+3
                 if (issuer && pc > 0) {
                     wait_or_abort(tmem_free, (pc - 1) & 1u, abort_flag, a.err);
                     __syncwarp();
                     tc::fence_after_sync();
                 }
-                for (int c = 0; c < nchunk; ++c, ++n) {
-                    const int st = (int)(n % (uint32_t)nstage);
-                    const uint32_t use = n / (uint32_t)nstage;
+                for (int c = 0; c < nchunk; ++c) {
                     unsigned char* stage = sm + st * STAGE;
+                    // blocks active at stage c: [ba, b1), ba = max(b0, c / 4)
+                    const int ba = max(b0, c >> 2);
+                    const int pa = ba >> 1;
                     if (!issuer) {
-                        // tile loader: wait until the stage's previous MMAs are done
-                        if (n >= (uint32_t)nstage && !wait_or_abort(empty + st, (use - 1) & 1u, abort_flag, a.err))
+                        // tile loader: wait until the stage's previous MMAs are done;
+                        // the active pairs' pieces are contiguous in the tile
+                        // arrays, one copy per part
+                        if (wrapped && !wait_or_abort(empty + st, ph ^ 1u, abort_flag, a.err)) {
+                            if (++st == nstage) { st = 0; ph ^= 1u; wrapped = true; }
                             continue;
-                        // active blocks at chunk c are a suffix [ba, b1) of the pass
-                        // (block b needs chunks c < 8b + 8); their pieces are
-                        // contiguous in the tile arrays, one copy per part
-                        int ba = b0;
-                        while (ba < b1 && c >= 8 * ba + 8) ++ba;
-                        const uint32_t bytes = (uint32_t)((b1 - ba) * B_PART);
-                        tc::mbar_expect_tx(b_full + st, 2u * bytes);
-                        const size_t off = ((size_t)c * NB + ba) * (B_PART / 2);
-                        unsigned char* dst = stage + 2 * A_PART + (ba - b0) * B_PART;
-                        bulk_copy(dst, mm.Bhi + off, bytes, b_full + st);
-                        bulk_copy(dst + bpp * B_PART, mm.Blo + off, bytes, b_full + st);
-                    } else {
-                        bool ok = wait_or_abort(a_full + st, use & 1u, abort_flag, a.err);
-                        ok = ok && wait_or_abort(b_full + st, use & 1u, abort_flag, a.err);
-                        if (!__all_sync(0xffffffffu, ok)) continue;
-                        tc::fence_after_sync();
-                        // descriptors by adds on precomputed bases: rebuilding them per
-                        // MMA makes the single issuing thread the bottleneck
-                        const uint64_t dAh = dA0 + (uint64_t)((st * STAGE) >> 4);
-                        const uint64_t dAl = dAh + (uint64_t)(A_PART >> 4);
-                        int ba = b0;                               // first block active at chunk c
-                        while (ba < b1 && c >= 8 * ba + 8) ++ba;
-                        for (int b = ba; b < b1; ++b) {
-                            const uint64_t dBh = dB0 + (uint64_t)((st * STAGE + 2 * A_PART + (b - b0) * B_PART) >> 4);
-                            const uint64_t dBl = dBh + (uint64_t)((bpp * B_PART) >> 4);
-                            const uint32_t d = taddr + (uint32_t)((b - b0) * BLK);
-                            if (mm.lo_set)
-                                tc::mma3_split2_elect(d, d + (uint32_t)LO_COL, dAh, dAl, dBh, dBl, idesc,
-                                                      c > 0 ? 1u : 0u);
-                            else
-                                tc::mma3_split_elect(d, dAh, dAl, dBh, dBl, idesc, c > 0 ? 1u : 0u);
                         }
-                        tc::mma_commit_elect(empty + st);
-                        if (c == nchunk - 1) tc::mma_commit_elect(pass_done);
+                        const uint32_t bytes = (uint32_t)((p1 - pa) * P_PART);
+                        tc::mbar_expect_tx(b_full + st, 2u * bytes);
+                        const size_t off = ((size_t)c * NP + pa) * (P_PART / 2);
+                        unsigned char* dst = stage + 2 * A_PART + (pa - p0) * P_PART;
+                        bulk_copy(dst, mm.Bhi + off, bytes, b_full + st);
+                        bulk_copy(dst + ppp * P_PART, mm.Blo + off, bytes, b_full + st);
+                    } else {
+                        bool ok = wait_or_abort(a_full + st, ph, abort_flag, a.err);
+                        ok = ok && wait_or_abort(b_full + st, ph, abort_flag, a.err);
+                        if (__all_sync(0xffffffffu, ok)) {
+                            tc::fence_after_sync();
+                            // descriptors by adds on precomputed bases: rebuilding them per
+                            // MMA makes the single issuing thread the bottleneck
+                            const uint64_t dAh = dA0 + (uint64_t)((st * STAGE) >> 4);
+                            const uint64_t dAl = dAh + (uint64_t)(A_PART >> 4);
+                            for (int p = pa; p < p1; ++p) {
+                                // both blocks of the pair (N = 256), else the upper one
+                                // (its lower block is done) or the lower one (no upper
+                                // block: odd NB) with N = 128
+                                const bool lower = 2 * p >= ba, upper = 2 * p + 1 < NB;
+                                const int row0 = lower ? 0 : BLK;
+                                const uint32_t id = (lower && upper) ? idesc2 : idesc1;
+                                const uint64_t dBh = dB0 + (uint64_t)((st * STAGE + 2 * A_PART + (p - p0) * P_PART +
+                                                                       row0 * 16) >> 4);
+                                const uint64_t dBl = dBh + (uint64_t)((ppp * P_PART) >> 4);
+                                const uint32_t d = taddr + (uint32_t)(2 * (p - p0) * BLK + row0);
+#pragma unroll
+                                for (int j = 0; j < 2; ++j) {
+                                    // K-step j: A slabs 2j, 2j+1 (MT * 32 bytes on), pair slabs
+                                    // 2j, 2j+1 (PAIR * 32 bytes on)
+                                    const uint64_t ja = (uint64_t)((j * MT * 32) >> 4);
+                                    const uint64_t jb = (uint64_t)((j * PAIR * 32) >> 4);
+                                    const uint32_t acc = (c > 0 || j > 0) ? 1u : 0u;
+                                    if (mm.lo_set)
+                                        tc::mma3_split2_elect(d, d + (uint32_t)LO_COL, dAh + ja, dAl + ja, dBh + jb,
+                                                              dBl + jb, id, acc);
+                                    else
+                                        tc::mma3_split_elect(d, dAh + ja, dAl + ja, dBh + jb, dBl + jb, id, acc);
+                                }
+                            }
+                            tc::mma_commit_elect(empty + st);
+                            if (c == nchunk - 1) tc::mma_commit_elect(pass_done);
+                        }
                     }
+                    if (++st == nstage) { st = 0; ph ^= 1u; wrapped = true; }
                 }
             }
         }
@@ -322,7 +355,10 @@ __device__ __forceinline__ void rollout_mma_body(const RolloutArgs& a, const Mma
     float S00 = 0, S01 = 0, S02 = 0, S03 = 0, S04 = 0, S11 = 0, S12 = 0, S13 = 0, S14 = 0,
           S22 = 0, S23 = 0, S24 = 0, S33 = 0, S34 = 0, S44 = 0;
     float cost = 0.0f, disc = 1.0f;
-    uint32_t n = 0, pc = 0;
+    uint32_t n = 0, pc = 0;          // stages produced, passes done
+    int st = 0;                      // ring position: stage and the parity of its current use
+    uint32_t ph = 0;
+    bool wrapped = false;
 
     for (int k = 0; k < a.T; ++k) {
         // ---------------- P1: noise, clamp, query (both halves) ------------
@@ -342,15 +378,13 @@ __device__ __forceinline__ void rollout_mma_body(const RolloutArgs& a, const Mma
         for (int g = 0; g < npass; ++g, ++pc) {
             const int b1 = min(NB, (g + 1) * bpp);
             const int b0 = g * bpp;
-            const int nchunk = 8 * b1;
+            const int nchunk = 4 * b1;
             const bool last_pass = (g == npass - 1);
             for (int c = 0; c < nchunk; ++c, ++n) {
-                const int st = (int)(n % (uint32_t)nstage);
-                const uint32_t use = n / (uint32_t)nstage;
                 unsigned char* stage = sm + st * STAGE;
-                // this thread's KPT training points of the chunk, two at a time
+                // this thread's KPT training points of the stage, two at a time
                 // (packed f32x2 arithmetic on the pair layout)
-                const int pb = (c * KC + u * KPT) / 2;
+                const int pb = (c * KCS + u * KPT) / 2;
                 float av[KPT];
 #pragma unroll
                 for (int q = 0; q < KPT / 2; ++q) {
@@ -367,7 +401,7 @@ __device__ __forceinline__ void rollout_mma_body(const RolloutArgs& a, const Mma
                     av[2 * q + 1] = ex2_ftz(-t1);
                 }
                 if (last_pass) {
-                    // the chunk's mean terms as packed partial sums, then one
+                    // the stage's mean terms as packed partial sums, then one
                     // compensated addition per output
                     uint64_t pv = 0ull, pw = 0ull;
 #pragma unroll
@@ -387,26 +421,30 @@ __device__ __forceinline__ void rollout_mma_body(const RolloutArgs& a, const Mma
 #pragma unroll
                 for (int q = 0; q < KPT / 2; ++q) split2<FMT>(av[2 * q], av[2 * q + 1], &hw[q], &lw[q]);
                 // the stage is free once the MMAs that last read it completed
-                if (n >= (uint32_t)nstage) wait_or_abort(empty + st, (use - 1) & 1u, abort_flag, a.err);
+                if (wrapped) wait_or_abort(empty + st, ph ^ 1u, abort_flag, a.err);
                 {
-                    // slab (u KPT) / 8, byte offset ((u KPT) % 8) * 2 within the row
+                    // points u KPT .. u KPT + KPT - 1 of the stage: slab (u KPT) / 8
+                    // on, byte offset ((u KPT) % 8) * 2 within the sample's row
                     const int sl = (u * KPT) / 8, off = ((u * KPT) % 8) * 2;
-                    unsigned char* ph = stage + sl * MT * 16 + m * 16 + off;
-                    unsigned char* pl = ph + A_PART;
-                    if (KPT == 8) {
-                        *reinterpret_cast<uint4*>(ph) = make_uint4(hw[0], hw[1 % (KPT / 2)], hw[2 % (KPT / 2)], hw[3 % (KPT / 2)]);
-                        *reinterpret_cast<uint4*>(pl) = make_uint4(lw[0], lw[1 % (KPT / 2)], lw[2 % (KPT / 2)], lw[3 % (KPT / 2)]);
-                    } else if (KPT == 4) {
-                        *reinterpret_cast<uint2*>(ph) = make_uint2(hw[0], hw[1 % (KPT / 2)]);
-                        *reinterpret_cast<uint2*>(pl) = make_uint2(lw[0], lw[1 % (KPT / 2)]);
+                    unsigned char* ph_ = stage + sl * MT * 16 + m * 16 + off;
+                    unsigned char* pl_ = ph_ + A_PART;
+                    if (KPT >= 8) {
+#pragma unroll
+                        for (int gq = 0; gq < KPT / 8; ++gq) {
+                            *reinterpret_cast<uint4*>(ph_ + gq * MT * 16) =
+                                make_uint4(hw[4 * gq], hw[4 * gq + 1], hw[4 * gq + 2], hw[4 * gq + 3]);
+                            *reinterpret_cast<uint4*>(pl_ + gq * MT * 16) =
+                                make_uint4(lw[4 * gq], lw[4 * gq + 1], lw[4 * gq + 2], lw[4 * gq + 3]);
+                        }
                     } else {
-                        *reinterpret_cast<uint32_t*>(ph) = hw[0];
-                        *reinterpret_cast<uint32_t*>(pl) = lw[0];
+                        *reinterpret_cast<uint2*>(ph_) = make_uint2(hw[0], hw[1 % (KPT / 2)]);
+                        *reinterpret_cast<uint2*>(pl_) = make_uint2(lw[0], lw[1 % (KPT / 2)]);
                     }
                 }
                 tc::fence_proxy_async();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(a_full + st);
+                if (++st == nstage) { st = 0; ph ^= 1u; wrapped = true; }
             }
             // pass end: every MMA of the pass has landed in TMEM
             bool ok = wait_or_abort(pass_done, pc & 1u, abort_flag, a.err);
@@ -621,8 +659,8 @@ __device__ void inval_item_barriers(const RolloutArgs& a, const MmaArgs& mm, int
         for (int i = 0; i < f32r::WARPS * a.stages; ++i) mbar_inval(bars + i);
         return;
     }
-    const int bpp = mm.lo_set ? BLOCKS_PER_PASS / 2 : BLOCKS_PER_PASS;
-    const MLayout L = mma_layout(mm.stages, mm.nblocks * BLK, mm.scene_smem ? a.S : 0, mm.scene_smem ? a.O : 0, bpp);
+    const MLayout L = mma_layout(mm.stages, mm.nblocks * BLK, mm.scene_smem ? a.S : 0, mm.scene_smem ? a.O : 0,
+                                 pairs_per_pass(mm.lo_set));
     uint64_t* a_full = reinterpret_cast<uint64_t*>(sm + L.bars);
     for (int i = 0; i < mm.stages; ++i) {
         mbar_inval(a_full + i);
@@ -726,7 +764,7 @@ int launch_rollout_persistent(const RolloutArgs* args, const MmaArgs* mms, const
 }
 
 int rollout_mma_stages(int NpM, int S, int O, int smem_optin, int lo_set) {
-    return mma_stages(NpM, S, O, smem_optin, lo_set ? BLOCKS_PER_PASS / 2 : BLOCKS_PER_PASS);
+    return mma_stages(NpM, S, O, smem_optin, pairs_per_pass(lo_set));
 }
 
 int launch_rollout_mma(const RolloutArgs& a, const MmaArgs& mm, int fmt, bool trace, cudaStream_t st) {
@@ -734,7 +772,7 @@ int launch_rollout_mma(const RolloutArgs& a, const MmaArgs& mm, int fmt, bool tr
     if (nstage < 2 || nstage > NSTAGE) return fail(GPMPPI_ERR_INVALID_ARG, "rollout: bad MMA pipeline depth");
     if (mm.rps != 2 && mm.rps != 4 && mm.rps != 8) return fail(GPMPPI_ERR_INVALID_ARG, "rollout: bad threads per sample");
     const int smem = mma_layout(nstage, mm.nblocks * BLK, mm.scene_smem ? a.S : 0, mm.scene_smem ? a.O : 0,
-                                mm.lo_set ? BLOCKS_PER_PASS / 2 : BLOCKS_PER_PASS).total;
+                                pairs_per_pass(mm.lo_set)).total;
     const int mtc = NPROD / mm.rps;
     const int grid = (a.K + mtc - 1) / mtc;
 #define GPM_LAUNCH_MMA(F, RR, TR)                                                                 \
@@ -766,7 +804,7 @@ namespace gpm {
 
 int rollout_mma_smem(const MmaArgs& mm, int S, int O) {
     return mma_layout(mm.stages, mm.nblocks * BLK, mm.scene_smem ? S : 0, mm.scene_smem ? O : 0,
-                      mm.lo_set ? BLOCKS_PER_PASS / 2 : BLOCKS_PER_PASS).total;
+                      pairs_per_pass(mm.lo_set)).total;
 }
 
 }  // namespace gpm
