@@ -607,23 +607,20 @@ def run_ours(args):
     gp.mppi_set_profiling(ctrl, False)
 
     # ---- end to end through the ABI with host buffers -----------------------
+    # mppi_step_host: U in from pinned host memory, the step, U_new back to the
+    # host, one call that returns once U_new is there (the controller needs
+    # U_new[0] on the host)
     U_host = torch.tensor(sc.U0, dtype=torch.float32).pin_memory()
     out_host = torch.empty_like(U_host).pin_memory()
     for _ in range(3):
-        U.copy_(U_host, non_blocking=True)
-        gp.mppi_step(ctrl, x0, U, U_new, w, c)
-        out_host.copy_(U_new, non_blocking=True)
-        torch.cuda.synchronize()
+        gp.mppi_step_host(ctrl, x0, U_host, out_host, stream=stream)
     barrier()
     e2e_s = 0.0
     for i in range(args.steps):
         flush.fill_(float(i))                # same cold-L2 condition as the device-timed loop
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        U.copy_(U_host, non_blocking=True)
-        gp.mppi_step(ctrl, x0, U, U_new, w, c)
-        out_host.copy_(U_new, non_blocking=True)
-        torch.cuda.synchronize()             # the controller needs U_new[0] on the host
+        gp.mppi_step_host(ctrl, x0, U_host, out_host, stream=stream)
         e2e_s += time.perf_counter() - t0
     (e2e_s,) = slowest_rank(e2e_s)
     h2d = U_host.numel() * 4 + 5 * 4

@@ -161,6 +161,21 @@ int mppi_create(const gpmppi_params* p, const float* obstacles, int32_t O, const
 int mppi_step(gpmppi_ctrl c, const float state[5], const float* U_nom, float* U_new,
               float* weights, float* costs, void* stream);
 
+/* The same iteration with every array on the host, as a receding-horizon
+ * controller calls it (Alg. 1 once per control period): copies U_nom in,
+ * runs mppi_step on the controller's own staging buffers, copies the results
+ * out and returns once they are on the host (the stream is synchronised).
+ *   state    host, 5 floats
+ *   U_nom    host, T x 2 floats (pinned memory makes the copy asynchronous)
+ *   U_new    host, T x 2 floats (output)
+ *   weights  host, K floats (output) or NULL
+ *   costs    host, K floats (output) or NULL
+ * The staging buffers (2 T x 2 floats, plus K floats once weights are asked
+ * for) are allocated by the first call and freed with the controller.
+ * Errors: as mppi_step; INVALID_ARG for device pointers; OOM; CUDA. */
+int mppi_step_host(gpmppi_ctrl c, const float state[5], const float* U_nom, float* U_new,
+                   float* weights, float* costs, void* stream);
+
 /* The rollout of mppi_step for the current iteration (Alg. 1 Step 1),
  * recording every sample's trajectory: the mean and covariance of Eq. 6 and
  * Eq. 10 and the stage costs and margins of Eq. 11-16 (does not update U and

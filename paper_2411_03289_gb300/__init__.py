@@ -37,7 +37,7 @@ GPMPPI_KERNEL_TC_CLUSTER = 2
 GPMPPI_KERNEL_ENSEMBLE = 3
 
 # names every build of the library exports (checked by the CPU test suite)
-EXPORTS = ("gp_fit", "gp_destroy", "gp_factors", "gp_predict", "mppi_create", "mppi_step",
+EXPORTS = ("gp_fit", "gp_destroy", "gp_factors", "gp_predict", "mppi_create", "mppi_step", "mppi_step_host",
            "mppi_rollout_trace", "mppi_set_iteration", "mppi_get_iteration", "mppi_nominal_sxy",
            "mppi_destroy", "mppi_rollout_kind", "mppi_set_wait_limit", "mppi_set_profiling", "mppi_last_profile", "mppi_device_status", "mppi_grad",
            "mppi_create_ensemble", "mppi_set_terrain_weights", "terrain_weights",
@@ -92,6 +92,7 @@ def load():
         "gp_predict": [vp, vp, i32, vp, vp, vp],
         "mppi_create": [vp, vp, i32, vp, i32, vp, ctypes.POINTER(vp)],
         "mppi_step": [vp, vp, vp, vp, vp, vp, vp],
+        "mppi_step_host": [vp, vp, vp, vp, vp, vp, vp],
         "mppi_rollout_trace": [vp, vp, vp, vp, vp, vp, vp, vp, vp],
         "mppi_set_iteration": [vp, u64],
         "mppi_get_iteration": [vp, ctypes.POINTER(u64)],
@@ -172,6 +173,29 @@ def _dptr(t, dtype=None, numel=None, name="array"):
 
 def _f32(x):
     return np.ascontiguousarray(np.asarray(x, dtype=np.float32))
+
+
+def _hptr(t, numel, name, writable=False):
+    """Data pointer of a contiguous float32 host array: a CPU tensor (pinned
+    or not) or a numpy array (None -> NULL)."""
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        if t.dtype != np.float32 or not t.flags["C_CONTIGUOUS"]:
+            raise ValueError(f"{name} must be a C-contiguous float32 array")
+        if writable and not t.flags["WRITEABLE"]:
+            raise ValueError(f"{name} must be writable")
+        if t.size < numel:
+            raise ValueError(f"{name} needs at least {numel} elements")
+        return ctypes.c_void_p(t.ctypes.data)
+    import torch
+    if t.dtype != torch.float32:
+        raise ValueError(f"{name} must have dtype torch.float32")
+    if t.is_cuda or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous host tensor")
+    if t.numel() < numel:
+        raise ValueError(f"{name} needs at least {numel} elements")
+    return ctypes.c_void_p(t.data_ptr())
 
 
 def make_hyper(h) -> Hyper:
@@ -327,6 +351,16 @@ def mppi_step(ctrl: Ctrl, state, U_nom, U_new, weights=None, costs=None, stream=
                             _dptr(U_new, numel=2 * ctrl.T, name="U_new"),
                             _dptr(weights, numel=ctrl.K, name="weights"),
                             _dptr(costs, numel=ctrl.K, name="costs"), _stream(stream)))
+
+
+def mppi_step_host(ctrl: Ctrl, state, U_nom, U_new, weights=None, costs=None, stream=None):
+    """mppi_step with every array on the host; returns once the outputs are there."""
+    st = _f32(state).reshape(5)
+    _check(load().mppi_step_host(ctrl.handle, st.ctypes.data_as(ctypes.c_void_p),
+                                 _hptr(U_nom, 2 * ctrl.T, "U_nom"),
+                                 _hptr(U_new, 2 * ctrl.T, "U_new", writable=True),
+                                 _hptr(weights, ctrl.K, "weights", writable=True),
+                                 _hptr(costs, ctrl.K, "costs", writable=True), _stream(stream)))
 
 
 def mppi_rollout_trace(ctrl: Ctrl, state, U_nom, mu=None, sigma=None, stage=None, margins=None,

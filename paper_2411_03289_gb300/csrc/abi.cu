@@ -51,6 +51,23 @@ int check_dev_ptr(const void* p, const char* name, bool nullable) {
     return GPMPPI_OK;
 }
 
+// A host array argument: not NULL unless nullable, and not device memory.
+int check_host_ptr(const void* p, const char* name, bool nullable) {
+    if (p == nullptr) {
+        if (nullable) return GPMPPI_OK;
+        return fail(GPMPPI_ERR_INVALID_ARG, std::string(name) + " must not be NULL");
+    }
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return GPMPPI_OK;                    // unknown to CUDA: ordinary host memory
+    }
+    if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged)
+        return fail(GPMPPI_ERR_INVALID_ARG, std::string(name) + " must be host memory");
+    return GPMPPI_OK;
+}
+
 }  // namespace gpm
 
 using namespace gpm;
@@ -121,6 +138,8 @@ void free_ctrl(gpmppi_ctrl c) {
     cudaFree(c->seg);
     cudaFree(c->seg_il2);
     cudaFree(c->costs);
+    cudaFree(c->hs_U);
+    cudaFree(c->hs_w);
     cudaFree(c->u_tilde);
     cudaFree(c->partial);
     cudaFree(c->counter);
@@ -619,6 +638,31 @@ int mppi_step(gpmppi_ctrl c, const float state[5], const float* U_nom, float* U_
         c->profiled = true;
     }
     c->it++;
+    return GPMPPI_OK;
+}
+
+int mppi_step_host(gpmppi_ctrl c, const float state[5], const float* U_nom, float* U_new, float* weights,
+                   float* costs, void* stream) {
+    if (!valid_ctrl(c)) return fail(GPMPPI_ERR_INVALID_ARG, "mppi_step_host: invalid handle");
+    int rc;
+    if ((rc = check_ctrl_device(c))) return rc;
+    if ((rc = check_state(state))) return rc;
+    if ((rc = check_host_ptr(U_nom, "mppi_step_host: U_nom", false))) return rc;
+    if ((rc = check_host_ptr(U_new, "mppi_step_host: U_new", false))) return rc;
+    if ((rc = check_host_ptr(weights, "mppi_step_host: weights", true))) return rc;
+    if ((rc = check_host_ptr(costs, "mppi_step_host: costs", true))) return rc;
+    const size_t ub = sizeof(float) * 2 * (size_t)c->p.T, kb = sizeof(float) * (size_t)c->p.K;
+    if (!c->hs_U) GPM_CUDA(cudaMalloc(&c->hs_U, 2 * ub));
+    if (weights && !c->hs_w) GPM_CUDA(cudaMalloc(&c->hs_w, kb));
+    cudaStream_t st = (cudaStream_t)stream;
+    float* d_nom = c->hs_U;
+    float* d_new = c->hs_U + 2 * (size_t)c->p.T;
+    GPM_CUDA(cudaMemcpyAsync(d_nom, U_nom, ub, cudaMemcpyHostToDevice, st));
+    if ((rc = mppi_step(c, state, d_nom, d_new, weights ? c->hs_w : nullptr, nullptr, st))) return rc;
+    GPM_CUDA(cudaMemcpyAsync(U_new, d_new, ub, cudaMemcpyDeviceToHost, st));
+    if (weights) GPM_CUDA(cudaMemcpyAsync(weights, c->hs_w, kb, cudaMemcpyDeviceToHost, st));
+    if (costs) GPM_CUDA(cudaMemcpyAsync(costs, c->costs, kb, cudaMemcpyDeviceToHost, st));
+    GPM_CUDA(cudaStreamSynchronize(st));
     return GPMPPI_OK;
 }
 

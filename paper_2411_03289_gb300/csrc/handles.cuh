@@ -28,6 +28,8 @@ struct gpmppi_ctrl_s {
     float4* seg = nullptr;
     float* seg_il2 = nullptr;
     float* costs = nullptr;       // K, used when the caller passes no costs array
+    float* hs_U = nullptr;        // mppi_step_host staging: U_nom then U_new (2 x T x 2)
+    float* hs_w = nullptr;        // mppi_step_host staging: weights (K)
     float2* u_tilde = nullptr;    // T x K
     float* partial = nullptr;     // n_upd x T x 2 update partials, then n_upd x 2 block statistics
     unsigned int* counter = nullptr;
