@@ -99,7 +99,7 @@ def alu_roof(achieved, peaks, kernel, traffic, note_extra=""):
             "kernel": kernel, "traffic": traffic, "peak_note": note + note_extra}
 
 
-PRECISIONS = {"fp32": 0, "bf16split": 1, "fp16split": 2}
+PRECISIONS = {"fp32": 0, "bf16split": 1, "fp16split": 2, "bf16split3": 3}
 
 
 def measured_tensor_peak():
@@ -666,7 +666,7 @@ def run_ours(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_ms / args.steps,
         "p50_ms": statistics.median(step_ms), "p90_ms": sorted(step_ms)[int(0.9 * (len(step_ms) - 1))],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": {0: "f32", 1: "f32+bf16split", 2: "f32+f16split"}[P.precision],
+        "dtype": {0: "f32", 1: "f32+bf16split", 2: "f32+f16split", 3: "f32+bf16split3"}[P.precision],
         "data": "synthetic (seeded GP training set, obstacles and figure-eight path)",
         "config": describe(sc) if not terrain else {
             **describe(sc), "workload": f"{sc.name}: K={P.K} T={P.T} three terrain GPs of N={sc.terrains[0][0].shape[0]} "
@@ -949,7 +949,7 @@ def run_batched(args):
         "metric": METRIC, "value": value, "unit": "sample-steps/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "p50_ms": statistics.median(step_ms),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": {0: "f32", 1: "f32+bf16split", 2: "f32+f16split"}[prec],
+        "dtype": {0: "f32", 1: "f32+bf16split", 2: "f32+f16split", 3: "f32+bf16split3"}[prec],
         "data": "synthetic (64 seeded controllers)",
         "config": {"workload": f"cfg5: {len(scs)} controllers, K {min(s.params.K for s in scs)}..{max(s.params.K for s in scs)}, "
                                f"T {min(s.params.T for s in scs)}..{max(s.params.T for s in scs)}, "

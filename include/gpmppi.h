@@ -55,6 +55,8 @@ extern "C" {
 #define GPMPPI_FP32 0         /* FP32 on the CUDA cores                                   */
 #define GPMPPI_BF16_SPLIT 1   /* tensor cores: BF16 hi/lo operands, 3 products, FP32 sums */
 #define GPMPPI_FP16_SPLIT 2   /* tensor cores: FP16 hi/lo operands, 3 products, FP32 sums */
+#define GPMPPI_BF16_SPLIT3 3  /* tensor cores: BF16 hi/mid/lo operands, 6 products, FP32 sums
+                                 (the streaming rollout at every N; 24 operand bits)     */
 
 /* limits of this library */
 #define GPMPPI_MAX_N 4096         /* GP training points      */
@@ -95,7 +97,8 @@ typedef struct gpmppi_params {
     float v_desired;         /* v_desired of Eq. 11                                 */
     uint64_t seed;           /* Philox key                                          */
     int32_t variance_mode;   /* GPMPPI_VAR_*                                        */
-    int32_t precision;       /* GPMPPI_FP32, GPMPPI_BF16_SPLIT or GPMPPI_FP16_SPLIT */
+    int32_t precision;       /* GPMPPI_FP32, GPMPPI_BF16_SPLIT, GPMPPI_FP16_SPLIT or
+                                GPMPPI_BF16_SPLIT3                                  */
     float goal[2];           /* goal position of the Eq. 12 goal terms              */
     float goal_radius;       /* terminal term: penalty when |mu_XY(T) - goal| > this */
     float P_goal;            /* penalty multiplying the terminal indicator          */

@@ -31,6 +31,7 @@ GPMPPI_VAR_NOMINAL = 1
 GPMPPI_FP32 = 0
 GPMPPI_BF16_SPLIT = 1
 GPMPPI_FP16_SPLIT = 2
+GPMPPI_BF16_SPLIT3 = 3
 GPMPPI_KERNEL_FP32 = 0
 GPMPPI_KERNEL_TC_STREAM = 1
 GPMPPI_KERNEL_TC_CLUSTER = 2

@@ -114,11 +114,12 @@ void free_gp(gpmppi_gp h) {
     cudaFree(g.Linv64[0]);
     cudaFree(g.alpha64[0]);
     cudaFree(g.alpha64[1]);
-    for (int f = 0; f < 2; ++f) {
+    for (int f = 0; f < 3; ++f) {
         cudaFree(g.mma_hi[f]);
         cudaFree(g.mma_lo[f]);
-        cudaFree(g.cl_tiles[f]);
     }
+    cudaFree(g.mma_mid);
+    for (int f = 0; f < 2; ++f) cudaFree(g.cl_tiles[f]);
     cudaFree(g.cl_xa);
     cudaFree(g.mma_xa);
     cudaFree(g.Wt);
@@ -182,7 +183,8 @@ int validate_params(const gpmppi_params& p) {
     if (p.goal_radius < 0.0f) return bad("goal_radius must be >= 0");
     if (p.variance_mode != GPMPPI_VAR_PER_SAMPLE && p.variance_mode != GPMPPI_VAR_NOMINAL)
         return bad("unknown variance_mode");
-    if (p.precision != GPMPPI_FP32 && p.precision != GPMPPI_BF16_SPLIT && p.precision != GPMPPI_FP16_SPLIT)
+    if (p.precision != GPMPPI_FP32 && p.precision != GPMPPI_BF16_SPLIT && p.precision != GPMPPI_FP16_SPLIT &&
+        p.precision != GPMPPI_BF16_SPLIT3)
         return bad("unknown precision");
     return GPMPPI_OK;
 }
@@ -523,7 +525,7 @@ int mppi_create(const gpmppi_params* p, const float* obstacles, int32_t O, const
             return rc;
         }
         if (p->precision != GPMPPI_FP32) {
-            c->fmt = (p->precision == GPMPPI_FP16_SPLIT) ? 0 : 1;
+            c->fmt = (p->precision == GPMPPI_FP16_SPLIT) ? 0 : (p->precision == GPMPPI_BF16_SPLIT ? 1 : 2);
             if ((rc = build_mma_tiles(gp->g, c->fmt))) {
                 free_ctrl(c);
                 return rc;
@@ -531,6 +533,8 @@ int mppi_create(const gpmppi_params* p, const float* obstacles, int32_t O, const
             const GpDevice& g = gp->g;
             c->mm.Bhi = g.mma_hi[c->fmt];
             c->mm.Blo = g.mma_lo[c->fmt];
+            c->mm.Bmid = c->fmt == 2 ? g.mma_mid : nullptr;
+            c->mm.parts = c->fmt == 2 ? 3 : 2;
             c->mm.xa = g.mma_xa;
             c->mm.nblocks = g.NpM / 128;
             const double r = (double)g.sf2[0] / (g.mma_cB > 0.0f ? (double)g.mma_cB : 1.0);
@@ -542,11 +546,14 @@ int mppi_create(const gpmppi_params* p, const float* obstacles, int32_t O, const
             // the two small products get their own column set (N / 16 MMAs on
             // the large accumulator), which keeps the variance error near
             // 1e-5 sf2 at N = 2048 at the cost of output passes half as wide.
-            c->mm.lo_set = g.N > kLoSetMinN ? 1 : 0;
-            c->mm.stages = rollout_mma_stages(g.NpM, c->S, O, layout_limit, c->mm.lo_set);
+            // The three-term BF16 split always keeps its five small products
+            // apart (its stages would not fit shared memory with 512-column
+            // passes).
+            c->mm.lo_set = (g.N > kLoSetMinN || c->fmt == 2) ? 1 : 0;
+            c->mm.stages = rollout_mma_stages(g.NpM, c->S, O, layout_limit, c->mm.lo_set, c->mm.parts);
             if (c->mm.stages < 3) {
                 // keep the pipeline deep; read the scene from global memory instead
-                const int st_noscene = rollout_mma_stages(g.NpM, 0, 0, layout_limit, c->mm.lo_set);
+                const int st_noscene = rollout_mma_stages(g.NpM, 0, 0, layout_limit, c->mm.lo_set, c->mm.parts);
                 if (st_noscene > c->mm.stages) {
                     c->mm.stages = st_noscene;
                     c->mm.scene_smem = 0;
@@ -562,9 +569,10 @@ int mppi_create(const gpmppi_params* p, const float* obstacles, int32_t O, const
                 free_ctrl(c);
                 return fail(GPMPPI_ERR_UNSUPPORTED, "mppi_create: tensor-core rollout does not fit shared memory");
             }
-            // N <= 512: the cluster rollout keeps the factor resident in shared memory
+            // N <= 512: the cluster rollout keeps the factor resident in shared
+            // memory (two-part formats only)
             const char* no_cl = std::getenv("GPMPPI_NO_CLUSTER");
-            if (g.N > 0 && g.N <= 512 && !(no_cl && no_cl[0] == '1')) {
+            if (c->fmt < 2 && g.N > 0 && g.N <= 512 && !(no_cl && no_cl[0] == '1')) {
                 if ((rc = build_cl_tiles(gp->g, c->fmt))) {
                     free_ctrl(c);
                     return rc;

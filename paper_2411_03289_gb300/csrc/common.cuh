@@ -117,10 +117,12 @@ struct GpDevice {
     // FP64 factors kept for export: Linv64[o] N x N, alpha64[o] N
     double* Linv64[2] = {nullptr, nullptr};
     double* alpha64[2] = {nullptr, nullptr};
-    // tensor-core tiles of L^-T per 16-bit format (0 = FP16, 1 = BF16), built
-    // on first use by a controller; NpM = N rounded up to 128
-    uint16_t* mma_hi[2] = {nullptr, nullptr};
-    uint16_t* mma_lo[2] = {nullptr, nullptr};
+    // tensor-core tiles of L^-T per operand format (0 = FP16 hi/lo, 1 = BF16
+    // hi/lo, 2 = BF16 hi/mid/lo), built on first use by a controller; NpM = N
+    // rounded up to 128
+    uint16_t* mma_hi[3] = {nullptr, nullptr, nullptr};
+    uint16_t* mma_lo[3] = {nullptr, nullptr, nullptr};
+    uint16_t* mma_mid = nullptr;   // the middle part of format 2
     float mma_cB = 0.0f;
     int NpM = 0;
     // the streaming rollout's training inputs and alpha in pair layout (NpM x 4
@@ -204,8 +206,10 @@ struct RolloutArgs {
 struct MmaArgs {
     const uint16_t* Bhi;
     const uint16_t* Blo;
+    const uint16_t* Bmid;   // format 2 (BF16 hi/mid/lo) only, else null
     const float* xa;        // training inputs and alpha in pair layout (GpDevice::mma_xa)
     int nblocks;            // NpM / 128
+    int parts;              // operand parts: 2 (hi, lo) or 3 (hi, mid, lo)
     float qscale;           // (sf2 / cB)^2: |L^-1 k*|^2 = qscale * |V'|^2
     int stages;             // shared-memory pipeline depth (2..6)
     int rps;                // producer threads per sample (2, 4, 8): 128, 64, 32 samples per CTA
@@ -362,7 +366,7 @@ int launch_noise(uint64_t seed, int K, int T, uint64_t it, float sv, float sw, f
 int launch_nominal(const RolloutArgs& a, float* sxy_out, cudaStream_t st);
 int rollout_fp32_smem_bytes(int Np, int mtp, int stages);
 int launch_rollout_mma(const RolloutArgs& a, const MmaArgs& mm, int fmt, bool trace, cudaStream_t st);
-int rollout_mma_stages(int NpM, int S, int O, int smem_optin, int lo_set);
+int rollout_mma_stages(int NpM, int S, int O, int smem_optin, int lo_set, int parts);
 int build_mma_tiles(GpDevice& g, int fmt);
 int build_cl_tiles(GpDevice& g, int fmt);
 int cl_smem_bytes(const ClArgs& cl, int S, int O);

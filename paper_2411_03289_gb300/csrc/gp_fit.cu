@@ -283,10 +283,12 @@ __global__ void k_absmax(const double* __restrict__ Xm, size_t n, unsigned long 
 // its columns (training points) in stages of 32.  Piece (c, p) holds element
 // (i = 256 p + r, j = 32 c + 8 sl + e) of cB L^-1 at
 // ((c * NP + p) * 4 + sl) * 2048 + r * 8 + e, so one stage holds the 16 KiB
-// pieces of all pairs contiguously, each as four 8-point slabs of 256 rows;
-// hi = round(v), lo = round(v - hi).
+// pieces of all pairs contiguously, each as four 8-point slabs of 256 rows.
+// Formats 0 (FP16) and 1 (BF16): hi = round(v), lo = round(v - hi); format 2
+// (BF16, three parts): hi = round(v), mid = round(v - hi), lo = round(v - hi -
+// mid), the residuals exact in double.
 __global__ void k_pack_mma(const double* __restrict__ Xm, int N, int NpM, int fmt, double cB,
-                           uint16_t* __restrict__ hi, uint16_t* __restrict__ lo) {
+                           uint16_t* __restrict__ hi, uint16_t* __restrict__ lo, uint16_t* __restrict__ mid) {
     const size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     const int NP = (NpM / 128 + 1) / 2;
     const size_t total = (size_t)(NpM / 32) * NP * 8192;
@@ -302,10 +304,17 @@ __global__ void k_pack_mma(const double* __restrict__ Xm, int N, int NpM, int fm
         const __half h = __double2half(v);
         hi[idx] = __half_as_ushort(h);
         lo[idx] = __half_as_ushort(__double2half(v - (double)__half2float(h)));
-    } else {
+    } else if (fmt == 1) {
         const __nv_bfloat16 h = __double2bfloat16(v);
         hi[idx] = __bfloat16_as_ushort(h);
         lo[idx] = __bfloat16_as_ushort(__double2bfloat16(v - (double)__bfloat162float(h)));
+    } else {
+        const __nv_bfloat16 h = __double2bfloat16(v);
+        const double r1 = v - (double)__bfloat162float(h);
+        const __nv_bfloat16 m = __double2bfloat16(r1);
+        hi[idx] = __bfloat16_as_ushort(h);
+        mid[idx] = __bfloat16_as_ushort(m);
+        lo[idx] = __bfloat16_as_ushort(__double2bfloat16(r1 - (double)__bfloat162float(m)));
     }
 }
 
@@ -449,8 +458,9 @@ int build_mma_tiles(GpDevice& g, int fmt) {
     const size_t n = (size_t)(g.NpM / 32) * (size_t)((g.NpM / 128 + 1) / 2) * 8192;
     GPM_CUDA(cudaMalloc(&g.mma_hi[fmt], n * sizeof(uint16_t)));
     GPM_CUDA(cudaMalloc(&g.mma_lo[fmt], n * sizeof(uint16_t)));
+    if (fmt == 2) GPM_CUDA(cudaMalloc(&g.mma_mid, n * sizeof(uint16_t)));
     k_pack_mma<<<(unsigned)((n + 255) / 256), 256>>>(g.Linv64[0], N, g.NpM, fmt, (double)g.mma_cB,
-                                                      g.mma_hi[fmt], g.mma_lo[fmt]);
+                                                      g.mma_hi[fmt], g.mma_lo[fmt], g.mma_mid);
     GPM_CUDA(cudaGetLastError());
     if (!g.mma_xa) {
         // the streaming rollout's training inputs and alpha in pair layout

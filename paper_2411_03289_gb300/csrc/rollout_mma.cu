@@ -54,10 +54,11 @@ constexpr int LO_COL = 256;           // first TMEM column of the low set
 constexpr int NSTAGE = 6;             // maximum pipeline depth (fewer when the training set is large)
 constexpr int A_PART = MT * KCS * 2;                        // 8 KiB: kernel-row tile, one part
 constexpr int P_PART = PAIR * KCS * 2;                      // 16 KiB: factor pair piece, one part
-// a stage: the A tile (hi, lo), then up to ppp pair pieces hi, then ppp lo
-// (ppp = pairs per pass: a pass fills the 512 TMEM columns, two pairs, or
-// one pair per column set with mm.lo_set)
-__host__ __device__ constexpr int stage_bytes(int ppp) { return 2 * A_PART + ppp * 2 * P_PART; }
+// a stage: the A tile parts (hi, lo[, mid]), then up to ppp pair pieces hi,
+// then ppp lo[, then ppp mid] (ppp = pairs per pass: a pass fills the 512
+// TMEM columns, two pairs, or one pair per column set with mm.lo_set; parts =
+// 2, or 3 for the three-term BF16 split)
+__host__ __device__ constexpr int stage_bytes(int ppp, int parts) { return parts * (A_PART + ppp * P_PART); }
 __host__ __device__ constexpr int pairs_per_pass(int lo_set) { return lo_set ? 1 : 2; }
 constexpr uint64_t kWaitNs = 2000000000ull;
 
@@ -66,9 +67,9 @@ struct MLayout {
     int bars, tslot, abort_flag, qh, mh, ep, om, xs, al, seg, il2, obs, total;
 };
 
-__host__ __device__ inline MLayout mma_layout(int nstage, int NpM, int S, int O, int ppp) {
+__host__ __device__ inline MLayout mma_layout(int nstage, int NpM, int S, int O, int ppp, int parts) {
     MLayout L;
-    L.bars = nstage * stage_bytes(ppp);                     // a_full, b_full, empty [NSTAGE] + pass_done, tmem_free, x_res
+    L.bars = nstage * stage_bytes(ppp, parts);                     // a_full, b_full, empty [NSTAGE] + pass_done, tmem_free, x_res
     L.tslot = L.bars + 8 * (3 * NSTAGE + 3);
     L.abort_flag = L.tslot + 4;
     L.qh = ((L.abort_flag + 4 + 15) / 16) * 16;  // 2 x 128 floats
@@ -85,9 +86,9 @@ __host__ __device__ inline MLayout mma_layout(int nstage, int NpM, int S, int O,
 }
 
 // deepest pipeline that fits (0 if none)
-inline int mma_stages(int NpM, int S, int O, int optin, int ppp) {
+inline int mma_stages(int NpM, int S, int O, int optin, int ppp, int parts) {
     for (int s = NSTAGE; s >= 2; --s)
-        if (mma_layout(s, NpM, S, O, ppp).total <= optin) return s;
+        if (mma_layout(s, NpM, S, O, ppp, parts).total <= optin) return s;
     return 0;
 }
 
@@ -116,6 +117,21 @@ __device__ __forceinline__ void split2(float a, float b, uint32_t* hi, uint32_t*
         const __nv_bfloat162 l = __floats2bfloat162_rn(ra, rb);
         *lo = *reinterpret_cast<const uint32_t*>(&l);
     }
+}
+
+// Three-term BF16 split of two values: hi = rn(a), mid = rn(a - hi), lo =
+// rn(a - hi - mid), 8 + 8 + 8 significant bits; each residual is exact (one
+// mixed-precision fma with the BF16 part taken as is).
+__device__ __forceinline__ void split3(float a, float b, uint32_t* hi, uint32_t* mid, uint32_t* lo) {
+    float ra, rb, sa, sb;
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    *hi = *reinterpret_cast<const uint32_t*>(&h);
+    tc::split_resid<1>(*hi, a, b, ra, rb);
+    const __nv_bfloat162 m = __floats2bfloat162_rn(ra, rb);
+    *mid = *reinterpret_cast<const uint32_t*>(&m);
+    tc::split_resid<1>(*mid, ra, rb, sa, sb);
+    const __nv_bfloat162 l = __floats2bfloat162_rn(sa, sb);
+    *lo = *reinterpret_cast<const uint32_t*>(&l);
 }
 
 // Bounded wait that gives up at once when another role has aborted.  The
@@ -166,12 +182,13 @@ __device__ __forceinline__ void rollout_mma_body(const RolloutArgs& a, const Mma
                                                  unsigned char* sm, uint32_t tmem_given) {
     constexpr int MTC = NPROD / R;
     constexpr int KPT = KCS / R;
+    constexpr int NPARTS = FMT == 2 ? 3 : 2;    // operand parts: hi, lo (, mid)
     const int nstage = mm.stages;
     const int Ssm = mm.scene_smem ? a.S : 0, Osm = mm.scene_smem ? a.O : 0;
     const int ppp = pairs_per_pass(mm.lo_set);  // block pairs per pass
     const int bpp = 2 * ppp;                    // output blocks per pass
-    const int STAGE = stage_bytes(ppp);
-    const MLayout L = mma_layout(nstage, mm.nblocks * BLK, Ssm, Osm, ppp);
+    const int STAGE = stage_bytes(ppp, NPARTS);
+    const MLayout L = mma_layout(nstage, mm.nblocks * BLK, Ssm, Osm, ppp, NPARTS);
     uint64_t* a_full = reinterpret_cast<uint64_t*>(sm + L.bars);
     uint64_t* b_full = a_full + NSTAGE;
     uint64_t* empty = b_full + NSTAGE;
@@ -239,8 +256,9 @@ __device__ __forceinline__ void rollout_mma_body(const RolloutArgs& a, const Mma
         // one loader thread; the issuer is a converged warp whose elected lane
         // issues the MMAs (its operand arithmetic stays warp-uniform)
         if (!issuer && lane != 0) return;
-        const uint32_t idesc2 = tc::idesc_f16(FMT, MT, PAIR);   // a block pair
-        const uint32_t idesc1 = tc::idesc_f16(FMT, MT, BLK);    // one block of a pair
+        constexpr int TYPE = FMT == 0 ? 0 : 1;                  // FP16 or BF16 operands
+        const uint32_t idesc2 = tc::idesc_f16(TYPE, MT, PAIR);  // a block pair
+        const uint32_t idesc1 = tc::idesc_f16(TYPE, MT, BLK);   // one block of a pair
         // base descriptors of stage 0's A tile (128 rows, slabs MT * 16 bytes
         // apart) and pair pieces (256 rows, slabs PAIR * 16 bytes apart); stage,
         // K-step and pair offsets are multiples of 16 bytes inside shared memory
@@ -275,11 +293,12 @@ __device__ __forceinline__ void rollout_mma_body(const RolloutArgs& a, const Mma
                             continue;
                         }
                         const uint32_t bytes = (uint32_t)((p1 - pa) * P_PART);
-                        tc::mbar_expect_tx(b_full + st, 2u * bytes);
+                        tc::mbar_expect_tx(b_full + st, (uint32_t)NPARTS * bytes);
                         const size_t off = ((size_t)c * NP + pa) * (P_PART / 2);
-                        unsigned char* dst = stage + 2 * A_PART + (pa - p0) * P_PART;
+                        unsigned char* dst = stage + NPARTS * A_PART + (pa - p0) * P_PART;
                         bulk_copy(dst, mm.Bhi + off, bytes, b_full + st);
                         bulk_copy(dst + ppp * P_PART, mm.Blo + off, bytes, b_full + st);
+                        if (NPARTS == 3) bulk_copy(dst + 2 * ppp * P_PART, mm.Bmid + off, bytes, b_full + st);
                     } else {
                         bool ok = wait_or_abort(a_full + st, ph, abort_flag, a.err);
                         ok = ok && wait_or_abort(b_full + st, ph, abort_flag, a.err);
@@ -296,7 +315,7 @@ __device__ __forceinline__ void rollout_mma_body(const RolloutArgs& a, const Mma
                                 const bool lower = 2 * p >= ba, upper = 2 * p + 1 < NB;
                                 const int row0 = lower ? 0 : BLK;
                                 const uint32_t id = (lower && upper) ? idesc2 : idesc1;
-                                const uint64_t dBh = dB0 + (uint64_t)((st * STAGE + 2 * A_PART + (p - p0) * P_PART +
+                                const uint64_t dBh = dB0 + (uint64_t)((st * STAGE + NPARTS * A_PART + (p - p0) * P_PART +
                                                                        row0 * 16) >> 4);
                                 const uint64_t dBl = dBh + (uint64_t)((ppp * P_PART) >> 4);
                                 const uint32_t d = taddr + (uint32_t)(2 * (p - p0) * BLK + row0);
@@ -307,7 +326,12 @@ __device__ __forceinline__ void rollout_mma_body(const RolloutArgs& a, const Mma
                                     const uint64_t ja = (uint64_t)((j * MT * 32) >> 4);
                                     const uint64_t jb = (uint64_t)((j * PAIR * 32) >> 4);
                                     const uint32_t acc = (c > 0 || j > 0) ? 1u : 0u;
-                                    if (mm.lo_set)
+                                    if (NPARTS == 3)
+                                        tc::mma6_split3_elect(d, d + (uint32_t)LO_COL, dAh + ja,
+                                                              dAh + ja + (uint64_t)((2 * A_PART) >> 4), dAl + ja,
+                                                              dBh + jb, dBh + jb + (uint64_t)((2 * ppp * P_PART) >> 4),
+                                                              dBl + jb, id, acc);
+                                    else if (mm.lo_set)
                                         tc::mma3_split2_elect(d, d + (uint32_t)LO_COL, dAh + ja, dAl + ja, dBh + jb,
                                                               dBl + jb, id, acc);
                                     else
@@ -417,9 +441,14 @@ __device__ __forceinline__ void rollout_mma_body(const RolloutArgs& a, const Mma
                     kahan_add(mv, cv, pv0 + pv1);
                     kahan_add(mw, cw, pw0 + pw1);
                 }
-                uint32_t hw[KPT / 2], lw[KPT / 2];
+                uint32_t hw[KPT / 2], lw[KPT / 2], mw[NPARTS == 3 ? KPT / 2 : 1];
 #pragma unroll
-                for (int q = 0; q < KPT / 2; ++q) split2<FMT>(av[2 * q], av[2 * q + 1], &hw[q], &lw[q]);
+                for (int q = 0; q < KPT / 2; ++q) {
+                    if constexpr (NPARTS == 3)
+                        split3(av[2 * q], av[2 * q + 1], &hw[q], &mw[q], &lw[q]);
+                    else
+                        split2<FMT>(av[2 * q], av[2 * q + 1], &hw[q], &lw[q]);
+                }
                 // the stage is free once the MMAs that last read it completed
                 if (wrapped) wait_or_abort(empty + st, ph ^ 1u, abort_flag, a.err);
                 {
@@ -435,10 +464,15 @@ __device__ __forceinline__ void rollout_mma_body(const RolloutArgs& a, const Mma
                                 make_uint4(hw[4 * gq], hw[4 * gq + 1], hw[4 * gq + 2], hw[4 * gq + 3]);
                             *reinterpret_cast<uint4*>(pl_ + gq * MT * 16) =
                                 make_uint4(lw[4 * gq], lw[4 * gq + 1], lw[4 * gq + 2], lw[4 * gq + 3]);
+                            if constexpr (NPARTS == 3)
+                                *reinterpret_cast<uint4*>(ph_ + 2 * A_PART + gq * MT * 16) =
+                                    make_uint4(mw[4 * gq], mw[4 * gq + 1], mw[4 * gq + 2], mw[4 * gq + 3]);
                         }
                     } else {
                         *reinterpret_cast<uint2*>(ph_) = make_uint2(hw[0], hw[1 % (KPT / 2)]);
                         *reinterpret_cast<uint2*>(pl_) = make_uint2(lw[0], lw[1 % (KPT / 2)]);
+                        if constexpr (NPARTS == 3)
+                            *reinterpret_cast<uint2*>(ph_ + 2 * A_PART) = make_uint2(mw[0], mw[1 % (KPT / 2)]);
                     }
                 }
                 tc::fence_proxy_async();
@@ -660,7 +694,7 @@ __device__ void inval_item_barriers(const RolloutArgs& a, const MmaArgs& mm, int
         return;
     }
     const MLayout L = mma_layout(mm.stages, mm.nblocks * BLK, mm.scene_smem ? a.S : 0, mm.scene_smem ? a.O : 0,
-                                 pairs_per_pass(mm.lo_set));
+                                 pairs_per_pass(mm.lo_set), mm.parts);
     uint64_t* a_full = reinterpret_cast<uint64_t*>(sm + L.bars);
     for (int i = 0; i < mm.stages; ++i) {
         mbar_inval(a_full + i);
@@ -733,10 +767,14 @@ __global__ void __launch_bounds__(THREADS, 1)
                 if (it.w == 2) persistent_mma_item<0, 2>(a, mm, it.y, sm, taddr);
                 else if (it.w == 4) persistent_mma_item<0, 4>(a, mm, it.y, sm, taddr);
                 else persistent_mma_item<0, 8>(a, mm, it.y, sm, taddr);
-            } else {
+            } else if (it.z == 2) {
                 if (it.w == 2) persistent_mma_item<1, 2>(a, mm, it.y, sm, taddr);
                 else if (it.w == 4) persistent_mma_item<1, 4>(a, mm, it.y, sm, taddr);
                 else persistent_mma_item<1, 8>(a, mm, it.y, sm, taddr);
+            } else {
+                if (it.w == 2) persistent_mma_item<2, 2>(a, mm, it.y, sm, taddr);
+                else if (it.w == 4) persistent_mma_item<2, 4>(a, mm, it.y, sm, taddr);
+                else persistent_mma_item<2, 8>(a, mm, it.y, sm, taddr);
             }
         }
         // every role of this CTA is done with the item (TMEM reads included)
@@ -763,16 +801,18 @@ int launch_rollout_persistent(const RolloutArgs* args, const MmaArgs* mms, const
     return GPMPPI_OK;
 }
 
-int rollout_mma_stages(int NpM, int S, int O, int smem_optin, int lo_set) {
-    return mma_stages(NpM, S, O, smem_optin, pairs_per_pass(lo_set));
+int rollout_mma_stages(int NpM, int S, int O, int smem_optin, int lo_set, int parts) {
+    return mma_stages(NpM, S, O, smem_optin, pairs_per_pass(lo_set), parts);
 }
 
 int launch_rollout_mma(const RolloutArgs& a, const MmaArgs& mm, int fmt, bool trace, cudaStream_t st) {
     const int nstage = mm.stages;
     if (nstage < 2 || nstage > NSTAGE) return fail(GPMPPI_ERR_INVALID_ARG, "rollout: bad MMA pipeline depth");
     if (mm.rps != 2 && mm.rps != 4 && mm.rps != 8) return fail(GPMPPI_ERR_INVALID_ARG, "rollout: bad threads per sample");
+    if ((fmt == 2) != (mm.parts == 3) || (fmt == 2 && !mm.lo_set))
+        return fail(GPMPPI_ERR_INVALID_ARG, "rollout: operand parts do not match the format");
     const int smem = mma_layout(nstage, mm.nblocks * BLK, mm.scene_smem ? a.S : 0, mm.scene_smem ? a.O : 0,
-                                pairs_per_pass(mm.lo_set)).total;
+                                pairs_per_pass(mm.lo_set), mm.parts).total;
     const int mtc = NPROD / mm.rps;
     const int grid = (a.K + mtc - 1) / mtc;
 #define GPM_LAUNCH_MMA(F, RR, TR)                                                                 \
@@ -789,8 +829,10 @@ int launch_rollout_mma(const RolloutArgs& a, const MmaArgs& mm, int fmt, bool tr
     } while (0)
     if (fmt == 0) {
         if (trace) GPM_LAUNCH_MMA_R(0, true); else GPM_LAUNCH_MMA_R(0, false);
-    } else {
+    } else if (fmt == 1) {
         if (trace) GPM_LAUNCH_MMA_R(1, true); else GPM_LAUNCH_MMA_R(1, false);
+    } else {
+        if (trace) GPM_LAUNCH_MMA_R(2, true); else GPM_LAUNCH_MMA_R(2, false);
     }
 #undef GPM_LAUNCH_MMA_R
 #undef GPM_LAUNCH_MMA
@@ -804,7 +846,7 @@ namespace gpm {
 
 int rollout_mma_smem(const MmaArgs& mm, int S, int O) {
     return mma_layout(mm.stages, mm.nblocks * BLK, mm.scene_smem ? S : 0, mm.scene_smem ? O : 0,
-                      pairs_per_pass(mm.lo_set)).total;
+                      pairs_per_pass(mm.lo_set), mm.parts).total;
 }
 
 }  // namespace gpm

@@ -104,6 +104,29 @@ __device__ __forceinline__ void mma3_split2_elect(uint32_t d_main, uint32_t d_lo
         : "memory");
 }
 
+// The six products of the three-term split (hi + mid + lo, 8 bits each) that
+// carry 24 bits: A_hi B_hi into d_main (accumulating only if acc0 != 0);
+// A_hi B_mid, A_mid B_hi, A_hi B_lo, A_lo B_hi and A_mid B_mid into d_lo (the
+// first accumulating only if acc0 != 0).  The dropped products are below
+// 2^-24 of the main one.  Warp-collective, one elected lane issues them.
+__device__ __forceinline__ void mma6_split3_elect(uint32_t d_main, uint32_t d_lo, uint64_t a_hi, uint64_t a_mid,
+                                                  uint64_t a_lo, uint64_t b_hi, uint64_t b_mid, uint64_t b_lo,
+                                                  uint32_t idesc, uint32_t acc0) {
+    asm volatile(
+        "{\n\t.reg .pred e, p0, p1;\n\t"
+        "elect.sync _|e, 0xffffffff;\n\t"
+        "setp.ne.b32 p0, %9, 0;\n\t"
+        "setp.ne.b32 p1, 1, 0;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %2, %5, %8, p0;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%1], %2, %6, %8, p0;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%1], %3, %5, %8, p1;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%1], %2, %7, %8, p1;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%1], %4, %5, %8, p1;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%1], %3, %6, %8, p1;\n\t}" ::"r"(d_main), "r"(d_lo),
+        "l"(a_hi), "l"(a_mid), "l"(a_lo), "l"(b_hi), "l"(b_mid), "l"(b_lo), "r"(idesc), "r"(acc0)
+        : "memory");
+}
+
 // Warp-collective commit: the whole (converged) warp executes it and one lane,
 // chosen by elect.sync, issues it.
 __device__ __forceinline__ void mma_commit_elect(uint64_t* bar) {

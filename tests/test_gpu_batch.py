@@ -17,6 +17,7 @@ SPECS = [  # (K, T, N, O, path, precision, seed)
     (129, 4, 0, 0, "eight", 2, 14),
     (260, 6, 140, 5, "sine", 1, 15),
     (200, 8, 90, 4, "eight", 0, 16),
+    (190, 6, 260, 5, "sine", 3, 17),
 ]
 
 

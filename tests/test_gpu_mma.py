@@ -44,7 +44,7 @@ def _sc(name, precision, **kw):
     return S.scenario(name, precision=precision, **kw)
 
 
-@pytest.mark.parametrize("precision", [2, 1])
+@pytest.mark.parametrize("precision", [2, 1, 3])
 @pytest.mark.parametrize("name,kw", [("small", {}), ("cfg1", {}), ("small", dict(N=0)),
                                      ("small", dict(K=130, N=200)), ("small", dict(K=1, T=2))])
 def test_mma_rollout_parity(lib, precision, name, kw):
@@ -68,7 +68,7 @@ def test_variance_error_per_precision(lib, N):
     variance contraction: the GP variance s(0) (the v-v entry of Sigma after
     the first step is exactly s(0)), means, covariances, margins, costs."""
     errs = {}
-    for precision in (0, 2, 1):
+    for precision in (0, 2, 1, 3):
         sc = _sc("cfg2", precision, K=384, N=N, T=20)
         g, ctrl = make_ctrl(lib, sc)
         fits = O.gp_fit(sc.X, sc.Y, sc.hyper)
@@ -84,10 +84,12 @@ def test_variance_error_per_precision(lib, N):
         info["err_var_over_sf2"] = var_err
         errs[precision] = info
         print(f"N={N} precision {precision}: {info}")
-    # FP32 and the FP16 split stay inside the declared GP-variance tolerance
-    # (1e-4 sf2) and pass every parity check above; the BF16 split is reported
+    # FP32, the FP16 split and the three-term BF16 split stay inside the
+    # declared GP-variance tolerance (1e-4 sf2) and pass every parity check
+    # above; the two-term BF16 split is reported
     assert errs[0]["err_var_over_sf2"] <= 1e-4
     assert errs[2]["err_var_over_sf2"] <= 1e-4
+    assert errs[3]["err_var_over_sf2"] <= 1e-4
     assert errs[1]["err_var_over_sf2"] <= 1e-3
 
 
