@@ -141,6 +141,10 @@ void free_ctrl(gpmppi_ctrl c) {
     cudaFree(c->costs);
     cudaFree(c->hs_U);
     cudaFree(c->hs_w);
+    cudaFree(c->ens_hi);
+    cudaFree(c->ens_lo);
+    cudaFree(c->ens_mid);
+    cudaFree(c->ens_xa);
     cudaFree(c->u_tilde);
     cudaFree(c->partial);
     cudaFree(c->counter);
@@ -538,7 +542,16 @@ int mppi_create(const gpmppi_params* p, const float* obstacles, int32_t O, const
             c->mm.xa = g.mma_xa;
             c->mm.nblocks = g.NpM / 128;
             const double r = (double)g.sf2[0] / (g.mma_cB > 0.0f ? (double)g.mma_cB : 1.0);
-            c->mm.qscale = (float)(r * r);
+            // the single GP: one terrain of weight 1 over every block
+            MmaTerrains& tr = c->mm.tr;
+            tr = MmaTerrains{};
+            tr.M = 1;
+            tr.blk0[0] = 0;
+            tr.blk0[1] = c->mm.nblocks;
+            tr.qscale[0] = (float)(r * r);
+            tr.sf2[0] = g.sf2[0];
+            tr.w[0] = 1.0f;
+            for (int d = 0; d < 4; ++d) tr.zscale[0][d] = g.zscale[0][d];
             c->mm.scene_smem = 1;
             // The tensor core rounds its FP32 accumulator at every MMA, so the
             // variance error grows with the MMAs per output column (3 N / 16
@@ -550,10 +563,10 @@ int mppi_create(const gpmppi_params* p, const float* obstacles, int32_t O, const
             // apart (its stages would not fit shared memory with 512-column
             // passes).
             c->mm.lo_set = (g.N > kLoSetMinN || c->fmt == 2) ? 1 : 0;
-            c->mm.stages = rollout_mma_stages(g.NpM, c->S, O, layout_limit, c->mm.lo_set, c->mm.parts);
+            c->mm.stages = rollout_mma_stages(g.NpM, c->S, O, layout_limit, c->mm.lo_set, c->mm.parts, 1);
             if (c->mm.stages < 3) {
                 // keep the pipeline deep; read the scene from global memory instead
-                const int st_noscene = rollout_mma_stages(g.NpM, 0, 0, layout_limit, c->mm.lo_set, c->mm.parts);
+                const int st_noscene = rollout_mma_stages(g.NpM, 0, 0, layout_limit, c->mm.lo_set, c->mm.parts, 1);
                 if (st_noscene > c->mm.stages) {
                     c->mm.stages = st_noscene;
                     c->mm.scene_smem = 0;
@@ -587,7 +600,7 @@ int mppi_create(const gpmppi_params* p, const float* obstacles, int32_t O, const
                     cl.base[r] = gp->g.cl_base[r];
                     cl.bytes[r] = gp->g.cl_bytes[r];
                 }
-                cl.qscale = c->mm.qscale;
+                cl.qscale = c->mm.tr.qscale[0];
                 cl.scene_smem = 1;
                 if (cl_smem_bytes(cl, c->S, O) > smem_optin) cl.scene_smem = 0;
                 c->cl = cl_smem_bytes(cl, c->S, O) <= smem_optin && cl_schedulable(cl, c->S, O, dev);
@@ -615,7 +628,7 @@ int mppi_step(gpmppi_ctrl c, const float state[5], const float* U_nom, float* U_
     RolloutArgs a = make_rollout_args(c, state, U_nom);
     if (costs) a.costs = costs;
     if (c->profiling) GPM_CUDA(cudaEventRecord(c->ev[0], st));
-    if (c->ens)
+    if (c->ens && c->fmt < 0)
         rc = launch_rollout_ens(make_ens_args(c, a), false, st);
     else if (c->cl)
         rc = launch_rollout_cl(a, c->cla, c->fmt, false, st);
@@ -692,7 +705,7 @@ int mppi_rollout_trace(gpmppi_ctrl c, const float state[5], const float* U_nom, 
     a.tr_sig = sigma;
     a.tr_stage = stage;
     a.tr_margin = margins;
-    if (c->ens) return launch_rollout_ens(make_ens_args(c, a), true, (cudaStream_t)stream);
+    if (c->ens && c->fmt < 0) return launch_rollout_ens(make_ens_args(c, a), true, (cudaStream_t)stream);
     if (c->cl) return launch_rollout_cl(a, c->cla, c->fmt, true, (cudaStream_t)stream);
     if (c->fmt >= 0) return launch_rollout_mma(a, c->mm, c->fmt, true, (cudaStream_t)stream);
     return launch_rollout_fp32(a, &c->tmW, true, (cudaStream_t)stream);
@@ -715,17 +728,16 @@ int mppi_create_ensemble(const gpmppi_params* p, const float* obstacles, int32_t
         if (!is_finite(weights[i])) return fail(GPMPPI_ERR_NONFINITE, "mppi_create_ensemble: non-finite weight");
     }
     // M = 1 with weight 1 is the single-GP controller (any precision);
-    // everything else runs the FP32 ensemble rollout
+    // everything else runs an ensemble rollout: the FP32 one, or in the split
+    // precisions the streaming tensor-core rollout over the GPs' stacked factors
     const bool ens = M > 1 || weights[0] != 1.0f;
-    if (ens && p->precision != GPMPPI_FP32)
-        return fail(GPMPPI_ERR_UNSUPPORTED, "mppi_create_ensemble: the ensemble rollout runs in FP32");
     if (ens && p->variance_mode != GPMPPI_VAR_PER_SAMPLE)
         return fail(GPMPPI_ERR_UNSUPPORTED, "mppi_create_ensemble: needs the per-sample variance mode");
     int npmax = 0, optin = 0, dev = 0, rc;
     for (int i = 0; i < M; ++i) npmax = gps[i]->g.Np > npmax ? gps[i]->g.Np : npmax;
     if ((rc = current_device(&dev))) return rc;
     GPM_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    if (ens && ens_smem_bytes(npmax) > optin)
+    if (ens && p->precision == GPMPPI_FP32 && ens_smem_bytes(npmax) > optin)
         return fail(GPMPPI_ERR_UNSUPPORTED, "mppi_create_ensemble: GPs too large for the ensemble rollout");
     gpmppi_ctrl c = nullptr;
     if ((rc = mppi_create(p, obstacles, O, path, P, gps[0], &c))) return rc;
@@ -735,6 +747,42 @@ int mppi_create_ensemble(const gpmppi_params* p, const float* obstacles, int32_t
         c->tgp[i] = gps[i];
         c->tw[i] = weights[i];
         if (i > 0) gps[i]->g.n_controllers++;
+    }
+    if (ens && c->fmt >= 0) {
+        // the streaming rollout over the stacked factors (not the cluster kernel)
+        GpDevice* gd[kMaxTerrains];
+        bool lo = c->fmt == 2;
+        for (int i = 0; i < M; ++i) {
+            gd[i] = &gps[i]->g;
+            lo = lo || gps[i]->g.N > kLoSetMinN;
+        }
+        MmaArgs& mm = c->mm;
+        if ((rc = build_mma_ensemble(gd, M, c->fmt, mm.tr, &c->ens_hi, &c->ens_lo, &c->ens_mid, &c->ens_xa))) {
+            mppi_destroy(c);
+            return rc;
+        }
+        for (int i = 0; i < M; ++i) mm.tr.w[i] = weights[i];
+        mm.Bhi = c->ens_hi;
+        mm.Blo = c->ens_lo;
+        mm.Bmid = c->ens_mid;
+        mm.xa = c->ens_xa;
+        mm.nblocks = mm.tr.blk0[M];
+        mm.lo_set = lo ? 1 : 0;
+        mm.scene_smem = 1;
+        const int NpT = mm.nblocks * 128;
+        mm.stages = rollout_mma_stages(NpT, c->S, O, optin - 64, mm.lo_set, mm.parts, M);
+        if (mm.stages < 3) {
+            const int st_noscene = rollout_mma_stages(NpT, 0, 0, optin - 64, mm.lo_set, mm.parts, M);
+            if (st_noscene > mm.stages) {
+                mm.stages = st_noscene;
+                mm.scene_smem = 0;
+            }
+        }
+        c->cl = false;
+        if (mm.stages == 0) {
+            mppi_destroy(c);
+            return fail(GPMPPI_ERR_UNSUPPORTED, "mppi_create_ensemble: the GPs' training sets do not fit shared memory");
+        }
     }
     *out = c;
     return GPMPPI_OK;
@@ -749,6 +797,8 @@ int mppi_set_terrain_weights(gpmppi_ctrl c, const float* weights, int32_t M) {
         return fail(GPMPPI_ERR_UNSUPPORTED,
                     "mppi_set_terrain_weights: a single-GP controller keeps weight 1 (create it with weight != 1)");
     for (int i = 0; i < M; ++i) c->tw[i] = weights[i];
+    if (c->ens && c->fmt >= 0)
+        for (int i = 0; i < M; ++i) c->mm.tr.w[i] = weights[i];
     return GPMPPI_OK;
 }
 
@@ -909,7 +959,7 @@ int mppi_set_wait_limit(gpmppi_ctrl c, uint64_t ns, int32_t expire_first) {
 int mppi_rollout_kind(gpmppi_ctrl c, int32_t* kind) {
     if (!valid_ctrl(c)) return fail(GPMPPI_ERR_INVALID_ARG, "mppi_rollout_kind: invalid handle");
     if (!kind) return fail(GPMPPI_ERR_INVALID_ARG, "mppi_rollout_kind: kind is NULL");
-    *kind = c->ens ? GPMPPI_KERNEL_ENSEMBLE
+    *kind = (c->ens && c->fmt < 0) ? GPMPPI_KERNEL_ENSEMBLE
                    : (c->cl ? GPMPPI_KERNEL_TC_CLUSTER : (c->fmt >= 0 ? GPMPPI_KERNEL_TC_STREAM : GPMPPI_KERNEL_FP32));
     return GPMPPI_OK;
 }

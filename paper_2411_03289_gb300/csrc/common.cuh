@@ -199,18 +199,34 @@ struct RolloutArgs {
     const unsigned long long* it_dev;
 };
 
-// Tensor-core variance contraction: L^-T (scaled by cB, a power of two) split
-// into hi and lo 16-bit parts, stored as 4 KiB pieces of 128 output columns x
-// 16 training points in the slab-major operand layout, piece (chunk c, block
-// b) at element offset (c * nblocks + b) * 2048.
+constexpr int kMaxTerrains = 8;
+
+// The GPs of a tensor-core rollout: M = 1 is the single GP, M > 1 the terrain
+// ensemble of Eq. 3 (mean sum_t w_t m_t, variance sum_t w_t^2 var_t).  The
+// factors are stacked block-diagonally: terrain t owns the 128-column blocks
+// [blk0[t], blk0[t+1]) of the output and the training points 128 blk0[t] ..
+// 128 blk0[t+1] - 1; with M > 1 every terrain's block count is even, so no
+// pair of blocks straddles two terrains.
+struct MmaTerrains {
+    int M;
+    int blk0[kMaxTerrains + 1];
+    float qscale[kMaxTerrains];     // (sf2_t / cB_t)^2: |L_t^-1 k*|^2 = qscale_t |V'_t|^2
+    float sf2[kMaxTerrains];        // signal variance
+    float w[kMaxTerrains];          // mixing weight (1 for the single GP)
+    float zscale[kMaxTerrains][4];  // query scaling (the GP's inverse lengthscales)
+};
+
+// Tensor-core variance contraction: cB L^-T (cB a power of two per GP) split
+// into 16-bit parts, packed by k_pack_mma as 16 KiB pair pieces (256 output
+// columns x 32 training points, slab-major operand layout).
 struct MmaArgs {
     const uint16_t* Bhi;
     const uint16_t* Blo;
     const uint16_t* Bmid;   // format 2 (BF16 hi/mid/lo) only, else null
     const float* xa;        // training inputs and alpha in pair layout (GpDevice::mma_xa)
-    int nblocks;            // NpM / 128
+    int nblocks;            // 128-column blocks of all GPs together (tr.blk0[tr.M])
     int parts;              // operand parts: 2 (hi, lo) or 3 (hi, mid, lo)
-    float qscale;           // (sf2 / cB)^2: |L^-1 k*|^2 = qscale * |V'|^2
+    MmaTerrains tr;         // per-GP ranges and constants
     int stages;             // shared-memory pipeline depth (2..6)
     int rps;                // producer threads per sample (2, 4, 8): 128, 64, 32 samples per CTA
     int scene_smem;         // lane segments and obstacles staged in shared memory
@@ -267,8 +283,6 @@ struct TerrainGp {
     float zscale[4];
     float w;                // ensemble weight w_i
 };
-
-constexpr int kMaxTerrains = 8;
 
 struct EnsArgs {
     RolloutArgs r;          // scene, controls, constants (the GP fields of r are unused)
@@ -366,9 +380,14 @@ int launch_noise(uint64_t seed, int K, int T, uint64_t it, float sv, float sw, f
 int launch_nominal(const RolloutArgs& a, float* sxy_out, cudaStream_t st);
 int rollout_fp32_smem_bytes(int Np, int mtp, int stages);
 int launch_rollout_mma(const RolloutArgs& a, const MmaArgs& mm, int fmt, bool trace, cudaStream_t st);
-int rollout_mma_stages(int NpM, int S, int O, int smem_optin, int lo_set, int parts);
+int rollout_mma_stages(int NpM, int S, int O, int smem_optin, int lo_set, int parts, int M);
 int build_mma_tiles(GpDevice& g, int fmt);
 int build_cl_tiles(GpDevice& g, int fmt);
+// The M GPs of a terrain ensemble as one block-diagonal factor for the
+// streaming tensor-core rollout: fills tr (ranges, scales, weights 1) and
+// allocates the stacked tiles and training set (caller frees them).
+int build_mma_ensemble(GpDevice* const* gs, int M, int fmt, MmaTerrains& tr, uint16_t** hi, uint16_t** lo,
+                       uint16_t** mid, float** xa);
 int cl_smem_bytes(const ClArgs& cl, int S, int O);
 bool cl_schedulable(const ClArgs& cl, int S, int O, int device);
 int launch_rollout_cl(const RolloutArgs& a, const ClArgs& cl, int fmt, bool trace, cudaStream_t st);

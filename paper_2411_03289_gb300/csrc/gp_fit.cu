@@ -286,16 +286,20 @@ __global__ void k_absmax(const double* __restrict__ Xm, size_t n, unsigned long 
 // pieces of all pairs contiguously, each as four 8-point slabs of 256 rows.
 // Formats 0 (FP16) and 1 (BF16): hi = round(v), lo = round(v - hi); format 2
 // (BF16, three parts): hi = round(v), mid = round(v - hi), lo = round(v - hi -
-// mid), the residuals exact in double.
-__global__ void k_pack_mma(const double* __restrict__ Xm, int N, int NpM, int fmt, double cB,
-                           uint16_t* __restrict__ hi, uint16_t* __restrict__ lo, uint16_t* __restrict__ mid) {
-    const size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+// mid), the residuals exact in double.  A GP of a terrain ensemble goes to the
+// diagonal block of a stacked factor: its piece (c, p) lands at (c + c_off,
+// p + p_off) of a grid NP_out pairs wide (a single GP: 0, 0, its own NP).
+__global__ void k_pack_mma(const double* __restrict__ Xm, int N, int NpM, int fmt, double cB, int c_off,
+                           int p_off, int NP_out, uint16_t* __restrict__ hi, uint16_t* __restrict__ lo,
+                           uint16_t* __restrict__ mid) {
+    const size_t idx0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     const int NP = (NpM / 128 + 1) / 2;
     const size_t total = (size_t)(NpM / 32) * NP * 8192;
-    if (idx >= total) return;
-    const size_t piece = idx / 8192;
-    const int w = (int)(idx % 8192);
+    if (idx0 >= total) return;
+    const size_t piece = idx0 / 8192;
+    const int w = (int)(idx0 % 8192);
     const int c = (int)(piece / NP), p = (int)(piece % NP);
+    const size_t idx = ((size_t)(c + c_off) * NP_out + (p + p_off)) * 8192 + w;
     const int sl = w / 2048, r = (w / 8) % 256, e = w % 8;
     const int i = 256 * p + r, j = 32 * c + 8 * sl + e;
     double v = 0.0;
@@ -370,22 +374,27 @@ __global__ void k_pack_cl(const double* __restrict__ Xm, int N, int NS, int fmt,
 // 2p and 2p + 1, x[2p] = (x0, x0', x1, x1'), x[2p + 1] = (x2, x2', x3, x3') and
 // a[p] = (a_v, a_v', a_w, a_w') (primes: point 2p + 1); rows j >= N get a far
 // point (exp2 underflows to exactly 0) and alpha 0
+// Training inputs and alpha of one GP in pair layout: point j (j < npc; far
+// away with alpha 0 past N) at position J0 + j of an array of NpT points (a
+// single GP: J0 = 0, NpT = npc; J0 even).
 __global__ void k_pack_xa(const float* __restrict__ Xs, const float* __restrict__ alpha, int N, int npc,
-                          float* __restrict__ out) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= npc) return;
+                          int J0, int NpT, float* __restrict__ out) {
+    const int j0 = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j0 >= npc) return;
+    const int j = j0;
     float4 x = make_float4(1.0e4f, 1.0e4f, 1.0e4f, 1.0e4f);
     float2 al = make_float2(0.0f, 0.0f);
     if (j < N) {
         x = reinterpret_cast<const float4*>(Xs)[j];
         al = reinterpret_cast<const float2*>(alpha)[j];
     }
-    float* xp = out + 8 * (j >> 1) + (j & 1);
+    const int J = J0 + j;
+    float* xp = out + 8 * (J >> 1) + (J & 1);
     xp[0] = x.x;
     xp[2] = x.y;
     xp[4] = x.z;
     xp[6] = x.w;
-    float* ap = out + 4 * npc + 4 * (j >> 1) + (j & 1);
+    float* ap = out + 4 * NpT + 4 * (J >> 1) + (J & 1);
     ap[0] = al.x;
     ap[2] = al.y;
 }
@@ -424,7 +433,7 @@ int build_cl_tiles(GpDevice& g, int fmt) {
     if (!g.cl_xa) {
         e = cudaMalloc(&g.cl_xa, sizeof(float) * 6 * (size_t)NpC);
         if (e == cudaSuccess) {
-            k_pack_xa<<<(NpC + 127) / 128, 128>>>(g.Xs[0], g.alpha, g.N, NpC, g.cl_xa);
+            k_pack_xa<<<(NpC + 127) / 128, 128>>>(g.Xs[0], g.alpha, g.N, NpC, 0, NpC, g.cl_xa);
             e = cudaGetLastError();
         }
         if (e == cudaSuccess) e = cudaDeviceSynchronize();
@@ -459,13 +468,63 @@ int build_mma_tiles(GpDevice& g, int fmt) {
     GPM_CUDA(cudaMalloc(&g.mma_hi[fmt], n * sizeof(uint16_t)));
     GPM_CUDA(cudaMalloc(&g.mma_lo[fmt], n * sizeof(uint16_t)));
     if (fmt == 2) GPM_CUDA(cudaMalloc(&g.mma_mid, n * sizeof(uint16_t)));
-    k_pack_mma<<<(unsigned)((n + 255) / 256), 256>>>(g.Linv64[0], N, g.NpM, fmt, (double)g.mma_cB,
-                                                      g.mma_hi[fmt], g.mma_lo[fmt], g.mma_mid);
+    k_pack_mma<<<(unsigned)((n + 255) / 256), 256>>>(g.Linv64[0], N, g.NpM, fmt, (double)g.mma_cB, 0, 0,
+                                                      (g.NpM / 128 + 1) / 2, g.mma_hi[fmt], g.mma_lo[fmt],
+                                                      g.mma_mid);
     GPM_CUDA(cudaGetLastError());
     if (!g.mma_xa) {
         // the streaming rollout's training inputs and alpha in pair layout
         GPM_CUDA(cudaMalloc(&g.mma_xa, sizeof(float) * 6 * (size_t)g.NpM));
-        k_pack_xa<<<(g.NpM + 127) / 128, 128>>>(g.Xs[0], g.alpha, g.N, g.NpM, g.mma_xa);
+        k_pack_xa<<<(g.NpM + 127) / 128, 128>>>(g.Xs[0], g.alpha, g.N, g.NpM, 0, g.NpM, g.mma_xa);
+        GPM_CUDA(cudaGetLastError());
+    }
+    GPM_CUDA(cudaDeviceSynchronize());
+    return GPMPPI_OK;
+}
+
+int build_mma_ensemble(GpDevice* const* gs, int M, int fmt, MmaTerrains& tr, uint16_t** hi, uint16_t** lo,
+                       uint16_t** mid, float** xa) {
+    *hi = *lo = *mid = nullptr;
+    *xa = nullptr;
+    tr = MmaTerrains{};
+    tr.M = M;
+    int nb = 0;
+    for (int t = 0; t < M; ++t) {
+        GpDevice& g = *gs[t];
+        int rc = build_mma_tiles(g, fmt);             // the GP's cB (and its own tiles)
+        if (rc) return rc;
+        // an even number of blocks per GP: no block pair straddles two GPs
+        const int nbt = g.N == 0 ? 0 : 2 * ((g.NpM / 128 + 1) / 2);
+        tr.blk0[t] = nb;
+        nb += nbt;
+        const double r = (double)g.sf2[0] / (g.mma_cB > 0.0f ? (double)g.mma_cB : 1.0);
+        tr.qscale[t] = (float)(r * r);
+        tr.sf2[t] = g.sf2[0];
+        tr.w[t] = 1.0f;
+        for (int d = 0; d < 4; ++d) tr.zscale[t][d] = g.zscale[0][d];
+    }
+    tr.blk0[M] = nb;
+    if (nb == 0) return GPMPPI_OK;
+    const int NpT = nb * 128, NP = nb / 2;
+    const size_t n = (size_t)(NpT / 32) * NP * 8192;
+    GPM_CUDA(cudaMalloc(hi, n * sizeof(uint16_t)));
+    GPM_CUDA(cudaMalloc(lo, n * sizeof(uint16_t)));
+    GPM_CUDA(cudaMemset(*hi, 0, n * sizeof(uint16_t)));
+    GPM_CUDA(cudaMemset(*lo, 0, n * sizeof(uint16_t)));
+    if (fmt == 2) {
+        GPM_CUDA(cudaMalloc(mid, n * sizeof(uint16_t)));
+        GPM_CUDA(cudaMemset(*mid, 0, n * sizeof(uint16_t)));
+    }
+    GPM_CUDA(cudaMalloc(xa, sizeof(float) * 6 * (size_t)NpT));
+    for (int t = 0; t < M; ++t) {
+        const GpDevice& g = *gs[t];
+        const int nbt = tr.blk0[t + 1] - tr.blk0[t];
+        if (nbt == 0) continue;
+        const size_t nt = (size_t)(nbt * 4) * (nbt / 2) * 8192;
+        k_pack_mma<<<(unsigned)((nt + 255) / 256), 256>>>(g.Linv64[0], g.N, nbt * 128, fmt, (double)g.mma_cB,
+                                                           4 * tr.blk0[t], tr.blk0[t] / 2, NP, *hi, *lo, *mid);
+        GPM_CUDA(cudaGetLastError());
+        k_pack_xa<<<(nbt * 128 + 127) / 128, 128>>>(g.Xs[0], g.alpha, g.N, nbt * 128, 128 * tr.blk0[t], NpT, *xa);
         GPM_CUDA(cudaGetLastError());
     }
     GPM_CUDA(cudaDeviceSynchronize());

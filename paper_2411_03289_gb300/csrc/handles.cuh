@@ -30,6 +30,12 @@ struct gpmppi_ctrl_s {
     float* costs = nullptr;       // K, used when the caller passes no costs array
     float* hs_U = nullptr;        // mppi_step_host staging: U_nom then U_new (2 x T x 2)
     float* hs_w = nullptr;        // mppi_step_host staging: weights (K)
+    // a terrain ensemble on the tensor cores: the stacked factor tiles and
+    // training set of its GPs (owned by the controller)
+    uint16_t* ens_hi = nullptr;
+    uint16_t* ens_lo = nullptr;
+    uint16_t* ens_mid = nullptr;
+    float* ens_xa = nullptr;
     float2* u_tilde = nullptr;    // T x K
     float* partial = nullptr;     // n_upd x T x 2 update partials, then n_upd x 2 block statistics
     unsigned int* counter = nullptr;

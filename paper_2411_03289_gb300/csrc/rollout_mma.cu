@@ -67,14 +67,14 @@ struct MLayout {
     int bars, tslot, abort_flag, qh, mh, ep, om, xs, al, seg, il2, obs, total;
 };
 
-__host__ __device__ inline MLayout mma_layout(int nstage, int NpM, int S, int O, int ppp, int parts) {
+__host__ __device__ inline MLayout mma_layout(int nstage, int NpM, int S, int O, int ppp, int parts, int M) {
     MLayout L;
     L.bars = nstage * stage_bytes(ppp, parts);                     // a_full, b_full, empty [NSTAGE] + pass_done, tmem_free, x_res
     L.tslot = L.bars + 8 * (3 * NSTAGE + 3);
     L.abort_flag = L.tslot + 4;
-    L.qh = ((L.abort_flag + 4 + 15) / 16) * 16;  // 2 x 128 floats
-    L.mh = L.qh + 2 * MT * 4;                    // 2 x 128 float2
-    L.ep = L.mh + 2 * MT * 8;                    // 2 x 128 floats
+    L.qh = ((L.abort_flag + 4 + 15) / 16) * 16;  // M x 2 x 128 floats: |V|^2 halves per GP
+    L.mh = L.qh + M * 2 * MT * 4;                // M x 2 x 128 float2: mean partials per GP
+    L.ep = L.mh + M * 2 * MT * 8;                // 2 x 128 floats
     L.om = L.ep + 2 * MT * 4;                    // 2 x 128 floats
     L.xs = ((L.om + 2 * MT * 4 + 127) / 128) * 128;   // NpM x 4 floats: scaled inputs, pair layout
     L.al = L.xs + NpM * 16;                      // NpM x 2 floats: alpha, pair layout
@@ -86,9 +86,9 @@ __host__ __device__ inline MLayout mma_layout(int nstage, int NpM, int S, int O,
 }
 
 // deepest pipeline that fits (0 if none)
-inline int mma_stages(int NpM, int S, int O, int optin, int ppp, int parts) {
+inline int mma_stages(int NpM, int S, int O, int optin, int ppp, int parts, int M) {
     for (int s = NSTAGE; s >= 2; --s)
-        if (mma_layout(s, NpM, S, O, ppp, parts).total <= optin) return s;
+        if (mma_layout(s, NpM, S, O, ppp, parts, M).total <= optin) return s;
     return 0;
 }
 
@@ -188,7 +188,7 @@ __device__ __forceinline__ void rollout_mma_body(const RolloutArgs& a, const Mma
     const int ppp = pairs_per_pass(mm.lo_set);  // block pairs per pass
     const int bpp = 2 * ppp;                    // output blocks per pass
     const int STAGE = stage_bytes(ppp, NPARTS);
-    const MLayout L = mma_layout(nstage, mm.nblocks * BLK, Ssm, Osm, ppp, NPARTS);
+    const MLayout L = mma_layout(nstage, mm.nblocks * BLK, Ssm, Osm, ppp, NPARTS, mm.tr.M);
     uint64_t* a_full = reinterpret_cast<uint64_t*>(sm + L.bars);
     uint64_t* b_full = a_full + NSTAGE;
     uint64_t* empty = b_full + NSTAGE;
@@ -206,7 +206,7 @@ __device__ __forceinline__ void rollout_mma_body(const RolloutArgs& a, const Mma
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int NB = mm.nblocks;                 // 128-column blocks of L^-T
     const int NP = (NB + 1) / 2;               // block pairs (the last one half empty for odd NB)
-    const int npass = (NB + bpp - 1) / bpp;
+    const MmaTerrains& TR = mm.tr;             // the GPs' block ranges (one range for a single GP)
 
     if (tid == 0) {
         for (int i = 0; i < nstage; ++i) {
@@ -269,17 +269,22 @@ __device__ __forceinline__ void rollout_mma_body(const RolloutArgs& a, const Mma
         bool wrapped = false;
         uint32_t pc = 0;
         for (int k = 0; k < a.T; ++k) {
-            for (int g = 0; g < npass; ++g, ++pc) {
-                const int b0 = g * bpp;
-                const int b1 = min(NB, b0 + bpp);
+          for (int t = 0; t < TR.M; ++t) {
+            // GP t: its blocks [tb0, tb1) in passes of bpp blocks; its stages
+            // start at c0 (its first training point), block b needs stages
+            // c0 .. 4b+3 (the factor is block-diagonal)
+            const int tb0 = TR.blk0[t], tb1 = TR.blk0[t + 1];
+            const int c0 = 4 * tb0;
+            for (int b0 = tb0; b0 < tb1; b0 += bpp, ++pc) {
+                const int b1 = min(tb1, b0 + bpp);
                 const int p0 = b0 >> 1, p1 = (b1 + 1) >> 1;
-                const int nchunk = 4 * b1;               // block b needs stages 0 .. 4b+3
+                const int nchunk = 4 * b1;
                 if (issuer && pc > 0) {
                     wait_or_abort(tmem_free, (pc - 1) & 1u, abort_flag, a.err);
                     __syncwarp();
                     tc::fence_after_sync();
                 }
-                for (int c = 0; c < nchunk; ++c) {
+                for (int c = c0; c < nchunk; ++c) {
                     unsigned char* stage = sm + st * STAGE;
                     // blocks active at stage c: [ba, b1), ba = max(b0, c / 4)
                     const int ba = max(b0, c >> 2);
@@ -312,7 +317,7 @@ __device__ __forceinline__ void rollout_mma_body(const RolloutArgs& a, const Mma
                                 // both blocks of the pair (N = 256), else the upper one
                                 // (its lower block is done) or the lower one (no upper
                                 // block: odd NB) with N = 128
-                                const bool lower = 2 * p >= ba, upper = 2 * p + 1 < NB;
+                                const bool lower = 2 * p >= ba, upper = 2 * p + 1 < b1;
                                 const int row0 = lower ? 0 : BLK;
                                 const uint32_t id = (lower && upper) ? idesc2 : idesc1;
                                 const uint64_t dBh = dB0 + (uint64_t)((st * STAGE + NPARTS * A_PART + (p - p0) * P_PART +
@@ -325,7 +330,7 @@ __device__ __forceinline__ void rollout_mma_body(const RolloutArgs& a, const Mma
                                     // 2j, 2j+1 (PAIR * 32 bytes on)
                                     const uint64_t ja = (uint64_t)((j * MT * 32) >> 4);
                                     const uint64_t jb = (uint64_t)((j * PAIR * 32) >> 4);
-                                    const uint32_t acc = (c > 0 || j > 0) ? 1u : 0u;
+                                    const uint32_t acc = (c > c0 || j > 0) ? 1u : 0u;
                                     if (NPARTS == 3)
                                         tc::mma6_split3_elect(d, d + (uint32_t)LO_COL, dAh + ja,
                                                               dAh + ja + (uint64_t)((2 * A_PART) >> 4), dAl + ja,
@@ -345,6 +350,7 @@ __device__ __forceinline__ void rollout_mma_body(const RolloutArgs& a, const Mma
                     if (++st == nstage) { st = 0; ph ^= 1u; wrapped = true; }
                 }
             }
+          }
         }
         return;
     }
@@ -392,19 +398,22 @@ __device__ __forceinline__ void rollout_mma_body(const RolloutArgs& a, const Mma
         ut.x = fminf(fmaxf(__ldg(a.U + 2 * k) + e.x, a.umin0), a.umax0);
         ut.y = fminf(fmaxf(__ldg(a.U + 2 * k + 1) + e.y, a.umin1), a.umax1);
         if (u == 0 && active) a.u_tilde[(size_t)k * a.K + s_me] = ut;
-        const float z0 = mu3 * a.zscale[0], z1 = mu4 * a.zscale[1];
-        const float z2 = ut.x * a.zscale[2], z3 = ut.y * a.zscale[3];
-        const uint64_t zz0 = tc::f2pack(z0, z0), zz1 = tc::f2pack(z1, z1);
-        const uint64_t zz2 = tc::f2pack(z2, z2), zz3 = tc::f2pack(z3, z3);
-
         // ---------------- P2/P3: kernel-row tiles for the tensor cores ------
-        float qpart = 0.0f, mv = 0.0f, mw = 0.0f, cv = 0.0f, cw = 0.0f;
-        for (int g = 0; g < npass; ++g, ++pc) {
-            const int b1 = min(NB, (g + 1) * bpp);
-            const int b0 = g * bpp;
+        for (int t = 0; t < TR.M; ++t) {
+          // GP t: the query scaled by its inverse lengthscales, its blocks
+          // [tb0, tb1) and stages from c0 on
+          const float z0 = mu3 * TR.zscale[t][0], z1 = mu4 * TR.zscale[t][1];
+          const float z2 = ut.x * TR.zscale[t][2], z3 = ut.y * TR.zscale[t][3];
+          const uint64_t zz0 = tc::f2pack(z0, z0), zz1 = tc::f2pack(z1, z1);
+          const uint64_t zz2 = tc::f2pack(z2, z2), zz3 = tc::f2pack(z3, z3);
+          const int tb0 = TR.blk0[t], tb1 = TR.blk0[t + 1];
+          const int c0 = 4 * tb0;
+          float qpart = 0.0f, mv = 0.0f, mw = 0.0f, cv = 0.0f, cw = 0.0f;
+          for (int b0 = tb0; b0 < tb1; b0 += bpp, ++pc) {
+            const int b1 = min(tb1, b0 + bpp);
             const int nchunk = 4 * b1;
-            const bool last_pass = (g == npass - 1);
-            for (int c = 0; c < nchunk; ++c, ++n) {
+            const bool last_pass = (b1 == tb1);
+            for (int c = c0; c < nchunk; ++c, ++n) {
                 unsigned char* stage = sm + st * STAGE;
                 // this thread's KPT training points of the stage, two at a time
                 // (packed f32x2 arithmetic on the pair layout)
@@ -522,20 +531,28 @@ __device__ __forceinline__ void rollout_mma_body(const RolloutArgs& a, const Mma
             tc::fence_before_sync();
             __syncwarp();
             if (lane == 0) mbar_arrive(tmem_free);
+          }
+          qh[(2 * t + hr) * MT + mr] = qpart;
+          mh[(t * R + u) * MTC + m] = make_float2(mv + cv, mw + cw);
         }
-        qh[hr * MT + mr] = qpart;
-        mh[u * MTC + m] = make_float2(mv + cv, mw + cw);
         producers_sync();
-        const float q = (qh[m] + qh[MT + m]) * mm.qscale;
-        float2 msum = mh[m];
+        // Eq. 3: mean sum_t w_t m_t and variance sum_t w_t^2 var_t (a single
+        // GP has w = 1: the same arithmetic as without the sums)
+        float mean_v = 0.0f, mean_w = 0.0f, s = 0.0f;
+        for (int t = 0; t < TR.M; ++t) {
+            const float q = (qh[2 * t * MT + m] + qh[(2 * t + 1) * MT + m]) * TR.qscale[t];
+            float2 msum = mh[t * R * MTC + m];
 #pragma unroll
-        for (int i = 1; i < R; ++i) {
-            const float2 mi = mh[i * MTC + m];
-            msum.x += mi.x;
-            msum.y += mi.y;
+            for (int i = 1; i < R; ++i) {
+                const float2 mi = mh[(t * R + i) * MTC + m];
+                msum.x += mi.x;
+                msum.y += mi.y;
+            }
+            const float wsf = TR.w[t] * TR.sf2[t];
+            mean_v += wsf * msum.x;
+            mean_w += wsf * msum.y;
+            s += TR.w[t] * TR.w[t] * fmaxf(0.0f, TR.sf2[t] - q);
         }
-        const float mean_v = a.sf2 * msum.x, mean_w = a.sf2 * msum.y;
-        const float s = fmaxf(0.0f, a.sf2 - q);
         // ---------------- P4: dynamics, covariance, obstacles ---------------
         float sn, cs;
         sincosf(mu2, &sn, &cs);
@@ -694,7 +711,7 @@ __device__ void inval_item_barriers(const RolloutArgs& a, const MmaArgs& mm, int
         return;
     }
     const MLayout L = mma_layout(mm.stages, mm.nblocks * BLK, mm.scene_smem ? a.S : 0, mm.scene_smem ? a.O : 0,
-                                 pairs_per_pass(mm.lo_set), mm.parts);
+                                 pairs_per_pass(mm.lo_set), mm.parts, mm.tr.M);
     uint64_t* a_full = reinterpret_cast<uint64_t*>(sm + L.bars);
     for (int i = 0; i < mm.stages; ++i) {
         mbar_inval(a_full + i);
@@ -801,8 +818,8 @@ int launch_rollout_persistent(const RolloutArgs* args, const MmaArgs* mms, const
     return GPMPPI_OK;
 }
 
-int rollout_mma_stages(int NpM, int S, int O, int smem_optin, int lo_set, int parts) {
-    return mma_stages(NpM, S, O, smem_optin, pairs_per_pass(lo_set), parts);
+int rollout_mma_stages(int NpM, int S, int O, int smem_optin, int lo_set, int parts, int M) {
+    return mma_stages(NpM, S, O, smem_optin, pairs_per_pass(lo_set), parts, M);
 }
 
 int launch_rollout_mma(const RolloutArgs& a, const MmaArgs& mm, int fmt, bool trace, cudaStream_t st) {
@@ -811,8 +828,10 @@ int launch_rollout_mma(const RolloutArgs& a, const MmaArgs& mm, int fmt, bool tr
     if (mm.rps != 2 && mm.rps != 4 && mm.rps != 8) return fail(GPMPPI_ERR_INVALID_ARG, "rollout: bad threads per sample");
     if ((fmt == 2) != (mm.parts == 3) || (fmt == 2 && !mm.lo_set))
         return fail(GPMPPI_ERR_INVALID_ARG, "rollout: operand parts do not match the format");
+    if (mm.tr.M < 1 || mm.tr.M > kMaxTerrains || mm.tr.blk0[0] != 0 || mm.tr.blk0[mm.tr.M] != mm.nblocks)
+        return fail(GPMPPI_ERR_INVALID_ARG, "rollout: bad GP block ranges");
     const int smem = mma_layout(nstage, mm.nblocks * BLK, mm.scene_smem ? a.S : 0, mm.scene_smem ? a.O : 0,
-                                pairs_per_pass(mm.lo_set), mm.parts).total;
+                                pairs_per_pass(mm.lo_set), mm.parts, mm.tr.M).total;
     const int mtc = NPROD / mm.rps;
     const int grid = (a.K + mtc - 1) / mtc;
 #define GPM_LAUNCH_MMA(F, RR, TR)                                                                 \
@@ -846,7 +865,7 @@ namespace gpm {
 
 int rollout_mma_smem(const MmaArgs& mm, int S, int O) {
     return mma_layout(mm.stages, mm.nblocks * BLK, mm.scene_smem ? S : 0, mm.scene_smem ? O : 0,
-                      pairs_per_pass(mm.lo_set), mm.parts).total;
+                      pairs_per_pass(mm.lo_set), mm.parts, mm.tr.M).total;
 }
 
 }  // namespace gpm

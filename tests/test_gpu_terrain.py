@@ -38,6 +38,46 @@ def test_ensemble_small_full_step_and_trace(lib, M):
     print(M, info_t, info)
 
 
+@pytest.mark.parametrize("precision,M,N", [(2, 2, 40), (2, 3, 300), (3, 3, 40), (2, 2, 800), (1, 2, 200)])
+def test_ensemble_split_precision_full_step_and_trace(lib, precision, M, N):
+    """The ensemble on the tensor cores: the GPs' factors stacked block-diagonally
+    through the streaming rollout (odd block counts padded, the second column
+    set beyond 768 points, the three-term BF16 split)."""
+    sc = S.terrain_scenario("small", M=M, N=N, precision=precision)
+    gps, ctrl = make_ctrl(lib, sc)
+    assert lib.mppi_rollout_kind(ctrl) == lib.GPMPPI_KERNEL_TC_STREAM
+    U = _U(sc)
+    ens = O.fit_scenario(sc)
+    ro = O.rollout(sc, ens, _x0(sc), U, 0)
+    tr = gpu_trace(lib, ctrl, sc, sc.x0, U, it=0)
+    info_t = check_trace(sc, ro, tr)
+    U_new, w, c = gpu_step(lib, ctrl, sc, sc.x0, U, it=0)
+    info = check_step(sc, ro, U, U_new, w, c)
+    np.testing.assert_allclose(tr["costs"], c, rtol=1e-6, atol=1e-6)
+    print(precision, M, N, info_t, info)
+
+
+def test_ensemble_split_weight_change_and_fp32_agreement(lib):
+    """New weights reach the tensor-core ensemble at the next step, and its
+    costs agree with the FP32 ensemble's."""
+    sc2 = S.terrain_scenario("small", M=3, N=60, precision=2)
+    sc0 = S.terrain_scenario("small", M=3, N=60, precision=0)
+    _, c2 = make_ctrl(lib, sc2)
+    _, c0 = make_ctrl(lib, sc0)
+    U = _U(sc2, 3)
+    for w in (None, (0.2, 0.5, 0.3)):
+        if w is not None:
+            lib.mppi_set_terrain_weights(c2, w)
+            lib.mppi_set_terrain_weights(c0, w)
+            sc2 = sc2.replace(terrain_w=tuple(float(x) for x in np.float32(w)))
+        Ua, wa, ca = gpu_step(lib, c2, sc2, sc2.x0, U, it=6)
+        Ub, wb, cb = gpu_step(lib, c0, sc0, sc0.x0, U, it=6)
+        np.testing.assert_allclose(ca, cb, rtol=2e-5, atol=2e-5)
+        assert np.max(np.abs(Ua - Ub)) <= TOL_U
+        ro = O.rollout(sc2, O.fit_scenario(sc2), _x0(sc2), U, 6)
+        check_step(sc2, ro, U, Ua, wa, ca)
+
+
 def test_ensemble_one_hot_equals_single_gp(lib):
     import torch
     sc = S.terrain_scenario("small", M=3, N=40, w=(0.0, 1.0, 0.0))
@@ -85,9 +125,10 @@ def test_ensemble_weight_update_loop(lib):
     check_step(sc2, ro, U, U_new, wt, c)
 
 
-def test_ensemble_cfg2_three_terrains_sampled(lib):
+@pytest.mark.parametrize("precision", [0, 2])
+def test_ensemble_cfg2_three_terrains_sampled(lib, precision):
     """K=4096, T=50, three terrains of N=500: sampled rows recomputed by the oracle."""
-    sc = S.terrain_scenario("cfg2", M=3)
+    sc = S.terrain_scenario("cfg2", M=3, precision=precision)
     P = sc.params
     gps, ctrl = make_ctrl(lib, sc)
     tr = gpu_trace(lib, ctrl, sc, sc.x0, sc.U0, it=1)
@@ -100,7 +141,7 @@ def test_ensemble_cfg2_three_terrains_sampled(lib):
     U_new, w, c = gpu_step(lib, ctrl, sc, sc.x0, sc.U0, it=1)
     np.testing.assert_allclose(c, tr["costs"], rtol=1e-6, atol=1e-6)
     assert abs(w.sum() - 1.0) <= 1e-5
-    print("cfg2 terrain3", info)
+    print("cfg2 terrain3 precision", precision, info)
 
 
 def _goal_scenario(precision=0, **kw):
@@ -165,7 +206,7 @@ def test_ensemble_rejections(lib):
     sc = S.terrain_scenario("small", M=2, N=20)
     gps = [lib.gp_fit(X, Y, h) for X, Y, h in sc.terrains]
     P = sc.params
-    for field, val in (("precision", 2), ("variance_mode", 1)):
+    for field, val in (("variance_mode", 1),):
         P2 = P.__class__(**{**P.__dict__, field: val})
         with pytest.raises(lib.GpmppiError) as ei:
             lib.mppi_create_ensemble(P2, sc.obstacles, sc.path, gps, sc.terrain_w)
