@@ -466,36 +466,59 @@ def fp32_path(args, gp, S, dev, flush, stream, barrier, peaks=None):
             "roofline": roof}
 
 
-def cfg3_leg(args, gp, S, dev, flush, stream, barrier):
-    """Secondary leg: the K=16384, T=100, N=2048, 64-obstacle workload on the
-    streaming tensor-core rollout (FP16 split), a few timed mppi_steps."""
+def _tc_leg(args, gp, dev, flush, stream, barrier, sc, ctrl, flops, profile_key, steps):
+    """A few timed mppi_steps of a tensor-core workload: the leg's entry of the
+    bench line (throughput, latency, kernel times, tensor roofline)."""
     import numpy as np
     import torch
-    sc = S.scenario("cfg3", seed=1, precision=PRECISIONS["fp16split"])
     P = sc.params
-    g = gp.gp_fit(sc.X, sc.Y, sc.hyper)
-    ctrl = gp.mppi_create(P, sc.obstacles, sc.path, g)
     U = torch.tensor(sc.U0, dtype=torch.float32, device=dev)
     U_new = torch.empty_like(U)
     w = torch.empty(P.K, dtype=torch.float32, device=dev)
     c = torch.empty_like(w)
     gp.mppi_set_profiling(ctrl, True)
-    steps = max(5, args.steps // 40)
     step_ms, rollout_ms, update_ms, _, _ = timed_steps(gp, ctrl, sc.x0.astype(np.float32), U, U_new, w, c,
                                                        flush, stream, steps, 3, barrier)
-    S_seg = max(sc.path.shape[0] - 1, 1)
-    flops = rollout_flops_per_sample_step(sc.N, sc.obstacles.shape[0], S_seg) * P.K * P.T
     r_avg = sum(rollout_ms) / len(rollout_ms)
     ach = flops / (r_avg / 1e3) / 1e12
     peak, note = measured_tensor_peak()
     kind = gp.mppi_rollout_kind(ctrl)
-    return {"workload": describe(sc)["workload"], "value": P.K * P.T * steps / (sum(step_ms) / 1e3),
+    return {"value": P.K * P.T * steps / (sum(step_ms) / 1e3),
             "unit": "sample-steps/s", "steps": steps, "warmup": 3, "p50_ms": statistics.median(step_ms),
             "kernel_ms": {"rollout_avg": r_avg, "update_avg": sum(update_ms) / len(update_ms)},
             "roofline": {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                          "frac": ach / peak, "peak_note": note,
                          "kernel": "k_rollout_mma" if kind == gp.GPMPPI_KERNEL_TC_STREAM else str(kind),
-                         "traffic": committed_traffic("rollout_mma", "cfg3")}}
+                         "traffic": committed_traffic("rollout_mma", profile_key)}}
+
+
+def cfg3_leg(args, gp, S, dev, flush, stream, barrier, precision="fp16split"):
+    """Secondary leg: the K=16384, T=100, N=2048, 64-obstacle workload on the
+    streaming tensor-core rollout (FP16 split, or the three-term BF16 split),
+    a few timed mppi_steps."""
+    sc = S.scenario("cfg3", seed=1, precision=PRECISIONS[precision])
+    g = gp.gp_fit(sc.X, sc.Y, sc.hyper)
+    ctrl = gp.mppi_create(sc.params, sc.obstacles, sc.path, g)
+    S_seg = max(sc.path.shape[0] - 1, 1)
+    flops = rollout_flops_per_sample_step(sc.N, sc.obstacles.shape[0], S_seg) * sc.params.K * sc.params.T
+    leg = _tc_leg(args, gp, dev, flush, stream, barrier, sc, ctrl, flops,
+                  "cfg3" if precision == "fp16split" else f"cfg3-{precision}", max(5, args.steps // 40))
+    return {"workload": describe(sc)["workload"], **leg}
+
+
+def terrain_leg(args, gp, S, dev, flush, stream, barrier):
+    """Secondary leg: cfg2 with three terrain GPs of N = 500 mixed by Eq. 3, on
+    the streaming tensor-core rollout over the GPs' stacked factors (FP16
+    split), a few timed mppi_steps; flops summed over the GPs."""
+    sc = S.terrain_scenario("cfg2", M=3, seed=1, precision=PRECISIONS["fp16split"])
+    gps = [gp.gp_fit(X, Y, h) for X, Y, h in sc.terrains]
+    ctrl = gp.mppi_create_ensemble(sc.params, sc.obstacles, sc.path, gps, sc.terrain_w)
+    S_seg = max(sc.path.shape[0] - 1, 1)
+    flops = sum(rollout_flops_per_sample_step(X.shape[0], sc.obstacles.shape[0], S_seg)
+                for X, _, _ in sc.terrains) * sc.params.K * sc.params.T
+    leg = _tc_leg(args, gp, dev, flush, stream, barrier, sc, ctrl, flops, "cfg2-terrain3", max(10, args.steps // 5))
+    return {"workload": f"cfg2-terrain3: K={sc.params.K} T={sc.params.T} three terrain GPs of N=500 mixed by "
+                        f"Eq. 3 (w={sc.terrain_w}), fp16split", **leg}
 
 
 def cfg5_leg(args, gp, S, dev):
@@ -661,7 +684,9 @@ def run_ours(args):
     legs = {}
     if args.workload == WORKLOAD and not terrain and not args.no_legs:
         legs["cfg3"] = cfg3_leg(args, gp, S, dev, flush, stream, barrier)
+        legs["cfg3_bf16split3"] = cfg3_leg(args, gp, S, dev, flush, stream, barrier, "bf16split3")
         legs["cfg5"] = cfg5_leg(args, gp, S, dev)
+        legs["cfg2_terrain3"] = terrain_leg(args, gp, S, dev, flush, stream, barrier)
     if rank != 0:
         if ws > 1:
             torch.distributed.destroy_process_group()
