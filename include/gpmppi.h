@@ -206,7 +206,8 @@ int mppi_nominal_sxy(gpmppi_ctrl c, float* sxy, void* stream);
  * GPMPPI_KERNEL_FP32 (CUDA cores), GPMPPI_KERNEL_TC_STREAM (tensor cores,
  * factor tiles streamed per step), GPMPPI_KERNEL_TC_CLUSTER (tensor cores,
  * factor resident in a CTA cluster; split precisions with N <= 512 when the
- * cluster fits the device) or GPMPPI_KERNEL_ENSEMBLE (terrain ensemble). */
+ * cluster fits the device) or GPMPPI_KERNEL_ENSEMBLE (FP32 terrain ensemble;
+ * a terrain ensemble in the split precisions reports GPMPPI_KERNEL_TC_STREAM). */
 #define GPMPPI_KERNEL_FP32 0
 #define GPMPPI_KERNEL_TC_STREAM 1
 #define GPMPPI_KERNEL_TC_CLUSTER 2
@@ -237,10 +238,14 @@ int mppi_destroy(gpmppi_ctrl c);
  * handles; each terrain's two outputs must share hyper-parameters; the
  * controller keeps them alive as mppi_create does), weights: host, M floats
  * (any finite values; Eq. 4 keeps them on the simplex).  2 <= M <= 8, or
- * M = 1 (weight 1 gives the single-GP controller of mppi_create).  The
- * ensemble rollout runs in FP32 with per-sample variance
- * (GPMPPI_ERR_UNSUPPORTED for other precisions / modes); mppi_step and
- * mppi_rollout_trace use it, mppi_grad and the batch API reject it.
+ * M = 1 (weight 1 gives the single-GP controller of mppi_create).  Needs
+ * the per-sample variance mode (else GPMPPI_ERR_UNSUPPORTED).  In FP32 the
+ * ensemble rollout runs on the CUDA cores; in the split precisions the
+ * streaming tensor-core rollout runs over the GPs' factors stacked
+ * block-diagonally (each GP's block count rounded up to even; UNSUPPORTED
+ * when the GPs' training sets do not fit shared memory together).
+ * mppi_step and mppi_rollout_trace use it; mppi_grad rejects it; the batch
+ * API takes it in the split precisions only.
  * mppi_set_terrain_weights replaces the weights (host, M floats) for the
  * following steps, e.g. with the result of terrain_weights. */
 int mppi_create_ensemble(const gpmppi_params* p, const float* obstacles, int32_t O, const float* path,
@@ -336,7 +341,10 @@ int mppi_update_noalloc(const float* costs, const float* u_tilde, const float* U
  * (controller, sample tile) items from an atomic work queue - FP32 tiles and
  * FP16- or BF16-split tensor-core tiles alike, longest first - then one update
  * launch for all controllers.  Controllers whose own mppi_step would use the
- * cluster rollout (N <= 512) run the streaming tensor-core body here. */
+ * cluster rollout (N <= 512) run the streaming tensor-core body here; terrain
+ * ensembles in the split precisions are items like single-GP controllers
+ * (their weights as set on the controller when a step is enqueued); FP32
+ * terrain ensembles give GPMPPI_ERR_UNSUPPORTED. */
 int mppi_batch_create(const gpmppi_ctrl* ctrls, int32_t B, gpmppi_batch* out);
 int mppi_batch_buffers(gpmppi_batch b, int32_t i, float** state, float** U_nom, float** U_new,
                        float** weights, float** costs);

@@ -34,7 +34,8 @@ constexpr uint32_t kBatchMagic = 0x42415431u;   // "BAT1"
 int check_ctrl_handle(gpmppi_ctrl c) {
     if (!c || c->magic != kCtrlMagicValue || !c->gp || c->gp->magic != kGpMagicValue)
         return fail(GPMPPI_ERR_INVALID_ARG, "mppi_batch_create: invalid controller handle");
-    if (c->ens) return fail(GPMPPI_ERR_UNSUPPORTED, "mppi_batch_create: terrain ensembles are not batched");
+    if (c->ens && c->fmt < 0)
+        return fail(GPMPPI_ERR_UNSUPPORTED, "mppi_batch_create: FP32 terrain ensembles are not batched");
     return GPMPPI_OK;
 }
 
@@ -124,7 +125,31 @@ double tile_estimate(gpmppi_batch b, int i) {
     gpmppi_ctrl c = b->ctrls[i];
     const double T = c->p.T, np = c->gp->g.Np > 0 ? c->gp->g.Np : 1;
     if (c->fmt < 0) return T * np * np * c->mt / 128.0 * 8.0e-6;
-    return T * np * np * (c->mm.lo_set ? 1.5 : 1.0) * 1.0e-6;
+    double n2 = 0.0;                      // the GPs' triangles (one GP, or a terrain ensemble)
+    for (int t = 0; t < c->mm.tr.M; ++t) {
+        const double nt = 128.0 * (c->mm.tr.blk0[t + 1] - c->mm.tr.blk0[t]);
+        n2 += nt * nt;
+    }
+    return T * (n2 > 0.0 ? n2 : 1.0) * (c->mm.lo_set ? 1.5 : 1.0) * 1.0e-6;
+}
+
+// A terrain ensemble's weights may change between steps (mppi_set_terrain_weights
+// on its controller): the batch's copy of its launch arguments follows before
+// the next step (an ordered copy on the step's stream, outside any capture).
+int refresh_weights(gpmppi_batch b, cudaStream_t st) {
+    bool dirty = false;
+    for (int i = 0; i < b->B; ++i) {
+        gpmppi_ctrl c = b->ctrls[i];
+        if (!c->ens || c->fmt < 0) continue;
+        for (int t = 0; t < c->mm.tr.M; ++t)
+            if (b->h_mm[i].tr.w[t] != c->mm.tr.w[t]) {
+                b->h_mm[i].tr.w[t] = c->mm.tr.w[t];
+                dirty = true;
+            }
+    }
+    if (dirty)
+        GPM_CUDA(cudaMemcpyAsync(b->d_mm, b->h_mm.data(), sizeof(MmaArgs) * b->B, cudaMemcpyHostToDevice, st));
+    return GPMPPI_OK;
 }
 
 // the work queue: every controller's tiles, longest tile first
@@ -176,12 +201,14 @@ int enqueue_step(gpmppi_batch b, cudaStream_t st) {
 // Measured tile times per controller shape, kept for the process: a shape is
 // (precision, K, T, Np, lane segments, obstacles) and the value (threads per
 // sample, microseconds per tile).
-using ShapeKey = std::tuple<int, int, int, int, int, int>;
+using ShapeKey = std::tuple<int, int, int, int, int, int, int>;
 std::map<ShapeKey, std::pair<int, double>> g_tuned;
 std::mutex g_tuned_mu;
 
 ShapeKey shape_of(gpmppi_ctrl c) {
-    return ShapeKey(c->fmt, c->p.K, c->p.T, c->gp->g.Np, c->S, c->O);
+    // a terrain ensemble: its total block count and number of GPs
+    if (c->ens) return ShapeKey(c->fmt, c->p.K, c->p.T, 128 * c->mm.nblocks, c->S, c->O, c->mm.tr.M);
+    return ShapeKey(c->fmt, c->p.K, c->p.T, c->gp->g.Np, c->S, c->O, 1);
 }
 
 // time of one wave of tiles of controller i (at most one tile per SM) with
@@ -355,6 +382,8 @@ int mppi_batch_step(gpmppi_batch b, void* stream) {
     int dev = 0;
     GPM_CUDA(cudaGetDevice(&dev));
     if (dev != b->device) return fail(GPMPPI_ERR_INVALID_ARG, "mppi_batch_step: batch belongs to another device");
+    int rc;
+    if ((rc = refresh_weights(b, (cudaStream_t)stream))) return rc;
     return enqueue_step(b, (cudaStream_t)stream);
 }
 
@@ -362,6 +391,8 @@ int mppi_batch_graph(gpmppi_batch b, void* stream) {
     if (!valid_batch(b)) return fail(GPMPPI_ERR_INVALID_ARG, "mppi_batch_graph: invalid handle");
     if (!stream) return fail(GPMPPI_ERR_INVALID_ARG, "mppi_batch_graph: graph replay needs a created stream");
     cudaStream_t st = (cudaStream_t)stream;
+    int rc0;
+    if ((rc0 = refresh_weights(b, st))) return rc0;
     if (!b->gexec) {
         GPM_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
         const int rc = enqueue_step(b, st);

@@ -167,3 +167,60 @@ def test_batch_cfg5_shapes_sampled_rows_and_properties(lib):
         assert np.max(np.abs(U_new - U_chk)) <= TOL_U, f"controller {i}"
         layouts.append(lib.mppi_batch_layout(b, i))
     print("cfg5 layouts (threads per sample, us per tile):", layouts)
+
+
+def test_batch_with_terrain_ensembles(lib):
+    """Terrain ensembles (Eq. 3) in the split precisions are items of the
+    persistent launch: each matches its own mppi_step and the oracle, and a
+    weight change on its controller reaches the next batched step, direct
+    and graph-replayed."""
+    import torch
+    scs = [S.terrain_scenario("small", M=3, N=40, precision=2, K=150, T=6),
+           S.terrain_scenario("small", M=2, N=300, precision=3, K=90, T=5),
+           S.scenario("small", K=120, T=6, N=200, precision=2)]
+    ctrls = [make_ctrl(lib, sc)[1] for sc in scs]
+    b = lib.mppi_batch_create(ctrls)
+    Us = []
+    for i, sc in enumerate(scs):
+        U = np.tile([sc.params.v_desired, 0.0], (sc.params.T, 1))
+        U[:, 1] = 0.3 * np.sin(np.arange(sc.params.T) + i)
+        Us.append(U)
+        b.state[i].copy_(torch.tensor(sc.x0, dtype=torch.float32))
+        b.U_nom[i].copy_(torch.tensor(U, dtype=torch.float32))
+
+    def compare(it, oracle=False):
+        for i, sc in enumerate(scs):
+            Ud = torch.tensor(Us[i], dtype=torch.float32, device="cuda")
+            U1 = torch.empty_like(Ud)
+            w1 = torch.empty(sc.params.K, device="cuda")
+            c1 = torch.empty_like(w1)
+            lib.mppi_set_iteration(ctrls[i], it)
+            lib.mppi_step(ctrls[i], sc.x0, Ud, U1, w1, c1)
+            torch.cuda.synchronize()
+            assert lib.mppi_batch_get_iteration(b, i) == it + 1
+            assert np.max(np.abs(to_np(U1) - to_np(b.U_new[i]))) <= TOL_U
+            np.testing.assert_allclose(to_np(c1), to_np(b.costs[i]), rtol=1e-5, atol=1e-5)
+            if oracle:
+                x0 = sc.x0.astype(np.float32).astype(np.float64)
+                ro = O.rollout(sc, O.fit_scenario(sc), x0, Us[i], it)
+                check_step(sc, ro, Us[i], to_np(b.U_new[i]), to_np(b.weights[i]), to_np(b.costs[i]))
+
+    lib.mppi_batch_step(b)
+    torch.cuda.synchronize()
+    compare(0, oracle=True)
+    lib.mppi_set_terrain_weights(ctrls[0], [0.1, 0.2, 0.7])
+    scs[0] = scs[0].replace(terrain_w=tuple(float(x) for x in np.float32([0.1, 0.2, 0.7])))
+    lib.mppi_batch_step(b)
+    torch.cuda.synchronize()
+    compare(1, oracle=True)
+    lib.mppi_set_terrain_weights(ctrls[1], [0.6, 0.4])
+    scs[1] = scs[1].replace(terrain_w=tuple(float(x) for x in np.float32([0.6, 0.4])))
+    st = torch.cuda.Stream()
+    lib.mppi_batch_graph(b, st)
+    st.synchronize()
+    compare(2, oracle=True)
+    lib.mppi_set_terrain_weights(ctrls[0], [0.5, 0.3, 0.2])
+    scs[0] = scs[0].replace(terrain_w=tuple(float(x) for x in np.float32([0.5, 0.3, 0.2])))
+    lib.mppi_batch_graph(b, st)
+    st.synchronize()
+    compare(3)
