@@ -6,8 +6,12 @@
 // of the variance, V = K* L^-T with |V_m|^2 = |L^-1 k*_m|^2, moves to the
 // tensor cores.  Operands are split into a high and a low 16-bit part
 // (x = hi + lo, both FP16 or both BF16) and the three products hi*hi, hi*lo,
-// lo*hi are accumulated in FP32; the queries are scaled to a_j = k*_j / sf2
-// in [0, 1] and L^-T by a power of two cB so that both fit the 16-bit range.
+// lo*hi are accumulated in FP32 (or, for the three-term BF16 split, x = hi +
+// mid + lo and six products); the queries are scaled to a_j = k*_j / sf2 in
+// [0, 1] and L^-T by a power of two cB so that both fit the 16-bit range.
+// A terrain ensemble (Eq. 3) runs the same body over its GPs' factors stacked
+// block-diagonally (MmaTerrains): each GP's passes use its own query scaling
+// and stages, and the step mixes the GPs' means and variances.
 // The tensor core's FP32 accumulation rounds at every MMA relative to the
 // accumulator's magnitude, so its error grows with the number of MMAs that
 // add into one accumulator.  For large training sets (mm.lo_set) hi*hi goes
@@ -171,7 +175,7 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 
 // R producer threads per sample: a CTA owns MTC = 256 / R samples (rows
 // m >= MTC of the 128-row MMA tile are never written; their TMEM lanes are
-// not read) and each thread makes KPT = 16 / R points of every chunk.
+// not read) and each thread makes KPT = 32 / R points of every stage.
 // tmem_given: kTmemAlloc to allocate the 512 TMEM columns here (and free them
 // at the end), else the base of columns the caller holds (the persistent
 // batched kernel allocates once per CTA).
