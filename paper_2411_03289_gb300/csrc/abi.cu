@@ -678,12 +678,18 @@ int mppi_step_host(gpmppi_ctrl c, const float state[5], const float* U_nom, floa
     cudaStream_t st = (cudaStream_t)stream;
     float* d_nom = c->hs_U;
     float* d_new = c->hs_U + 2 * (size_t)c->p.T;
-    GPM_CUDA(cudaMemcpyAsync(d_nom, U_nom, ub, cudaMemcpyHostToDevice, st));
-    if ((rc = mppi_step(c, state, d_nom, d_new, weights ? c->hs_w : nullptr, nullptr, st))) return rc;
-    GPM_CUDA(cudaMemcpyAsync(U_new, d_new, ub, cudaMemcpyDeviceToHost, st));
-    if (weights) GPM_CUDA(cudaMemcpyAsync(weights, c->hs_w, kb, cudaMemcpyDeviceToHost, st));
-    if (costs) GPM_CUDA(cudaMemcpyAsync(costs, c->costs, kb, cudaMemcpyDeviceToHost, st));
-    GPM_CUDA(cudaStreamSynchronize(st));
+    // every exit waits for the copies it enqueued: the caller's host buffers
+    // may be released as soon as the call returns
+    cudaError_t e = cudaMemcpyAsync(d_nom, U_nom, ub, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "mppi_step_host: copy in");
+    rc = mppi_step(c, state, d_nom, d_new, weights ? c->hs_w : nullptr, nullptr, st);
+    if (!rc) e = cudaMemcpyAsync(U_new, d_new, ub, cudaMemcpyDeviceToHost, st);
+    if (!rc && e == cudaSuccess && weights) e = cudaMemcpyAsync(weights, c->hs_w, kb, cudaMemcpyDeviceToHost, st);
+    if (!rc && e == cudaSuccess && costs) e = cudaMemcpyAsync(costs, c->costs, kb, cudaMemcpyDeviceToHost, st);
+    const cudaError_t es = cudaStreamSynchronize(st);
+    if (rc) return rc;
+    if (e != cudaSuccess) return cuda_fail(e, "mppi_step_host: copy out");
+    if (es != cudaSuccess) return cuda_fail(es, "mppi_step_host: synchronise");
     return GPMPPI_OK;
 }
 
