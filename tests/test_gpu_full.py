@@ -47,13 +47,18 @@ def _cfg2_oracle(sc, U, it):
 
 
 # FP32 CUDA-core rollout (0), FP16 hi/lo split (2, the benchmarked default) and
-# BF16 hi/lo split (1) on the 4-CTA cluster tensor-core rollout
-@pytest.mark.parametrize("precision", [0, 2, 1])
+# BF16 hi/lo split (1) on the 4-CTA cluster tensor-core rollout; the three-term
+# BF16 split (3) on the streaming tensor-core rollout
+_KIND = {0: "GPMPPI_KERNEL_FP32", 1: "GPMPPI_KERNEL_TC_CLUSTER", 2: "GPMPPI_KERNEL_TC_CLUSTER",
+         3: "GPMPPI_KERNEL_TC_STREAM"}
+
+
+@pytest.mark.parametrize("precision", [0, 2, 1, 3])
 def test_cfg2_full_step(lib, precision):
     sc = S.scenario("cfg2", precision=precision)
     g, ctrl = make_ctrl(lib, sc)
     kind = lib.mppi_rollout_kind(ctrl)
-    assert kind == (lib.GPMPPI_KERNEL_FP32 if precision == 0 else lib.GPMPPI_KERNEL_TC_CLUSTER)
+    assert kind == getattr(lib, _KIND[precision])
     U_new, w, c = gpu_step(lib, ctrl, sc, sc.x0, sc.U0, it=0)
     ro = _cfg2_oracle(sc, sc.U0, 0)
     info = check_step(sc, ro, sc.U0, U_new, w, c)
@@ -61,7 +66,7 @@ def test_cfg2_full_step(lib, precision):
     assert info["n_alt"] <= 0.01 * sc.params.K
 
 
-@pytest.mark.parametrize("precision", [0, 2, 1])
+@pytest.mark.parametrize("precision", [0, 2, 1, 3])
 def test_cfg2_sampled_trajectories(lib, precision):
     """Per-(sample, step) means, covariances, margins and costs at the full
     cfg2 size: rows from every one of the cluster kernel's 32 sample tiles
